@@ -1,0 +1,142 @@
+"""Pins of the input generator (eb_inputs): quadrature rule, closed forms and the paper's
+smallest-volume-fraction table (Sec. 3.4.1)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import eb_inputs as E
+from eb_inputs.geometry import _load
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def test_gauss_kronrod_exactness():
+    lib = _load()
+    for k in range(23):  # 15-point Kronrod: exact to degree 22
+        assert abs(lib.geo_gk15_panel_pow(k, 0) - 1.0 / (k + 1)) < 1e-15
+    for k in range(14):  # embedded 7-point Gauss: exact to degree 13
+        assert abs(lib.geo_gk15_panel_pow(k, 1) - 1.0 / (k + 1)) < 1e-15
+    assert abs(lib.geo_gk15_panel_pow(14, 1) - 1.0 / 15) > 1e-9  # and not beyond
+
+
+def test_splitmix64_published_values():
+    # first outputs of SplitMix64 seeded with 0
+    g = E.SplitMix64(0)
+    assert [g.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    g = E.SplitMix64(7)
+    seq = [g.next_double() for _ in range(5)]
+    assert np.array_equal(np.array(seq), E.uniform(7, 5))
+
+
+def test_full_cells_closed_form():
+    g = E.line_config(8)
+    assert np.all(g.flag == 1) and len(g.cut_cells) == 0
+    g = E.circle_config(16)
+    full = np.nonzero(g.flag == 1)[0][:5]
+    bp = g._basis_pow(4)
+    vals = g.cell_integrals(full, np.full(len(full), -1, np.int32), bp, g._terms_mono(2, 4))
+    expect = [np.prod([0.0 if q % 2 else 0.5 ** q / (q + 1) for q in m]) for m in E.monomials(2, 4)]
+    assert np.allclose(vals, np.array(expect)[None, :], atol=1e-16)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_circle_area_and_perimeter(N):
+    g = E.circle_config(N)
+    assert abs(g.kappa.sum() * g.h ** 2 - (1 - math.pi * 0.25 ** 2)) < 1e-13
+    assert abs(g.eb_mom[:, 0].sum() * g.h - 2 * math.pi * 0.25) < 1e-13
+    gi = E.circle_config(N, r=0.3, inside=True)
+    assert abs(gi.kappa.sum() * gi.h ** 2 - math.pi * 0.09) < 1e-13
+
+
+def test_sphere_volume_and_area():
+    g = E.sphere_inside_config(16)
+    assert abs(g.kappa.sum() * g.h ** 3 - 4 / 3 * math.pi * 0.45 ** 3) < 1e-13
+    assert abs(g.eb_mom[:, 0].sum() * g.h ** 2 - 4 * math.pi * 0.45 ** 2) < 1e-12
+    g = E.sphere_box_config(16)
+    assert abs(g.kappa.sum() * g.h ** 3 - (1 - 4 / 3 * math.pi * 0.35 ** 3)) < 1e-13
+
+
+def _divergence_residual(g):
+    """max over cut cells and monomials of |int_V d_d xi^p - int_dV xi^p n_d| (divergence theorem)."""
+    D, q = g.dim, g.qmax - 1
+    mons = E.monomials(D, q + 1)
+    idx = {m: i for i, m in enumerate(mons)}
+    fmons = E.monomials(D - 1, g.qmax)
+    fidx = {m: i for i, m in enumerate(fmons)}
+    vol_idx = {m: i for i, m in enumerate(E.monomials(D, g.qmax))}
+    worst = 0.0
+    for ci, c in enumerate(g.cut_cells[:200]):
+        ijk = []
+        r = int(c)
+        for d in range(D):
+            ijk.append(r % g.n[d]); r //= g.n[d]
+        for d in range(D):
+            for m in mons:
+                if m[d] == 0 or sum(m) > g.qmax:
+                    continue
+                lower = list(m); lower[d] -= 1
+                lhs = m[d] * g.vol_mom[ci, vol_idx[tuple(lower)]]
+                tang = tuple(m[k] for k in range(D) if k != d)
+                rhs = 0.0
+                for side in (0, 1):
+                    f = list(ijk)
+                    f[d] += side
+                    lin, s = 0, 1
+                    for k in range(D):
+                        lin += f[k] * s
+                        s *= g.n[k] + (k == d)
+                    ff = g.face_flag[d][lin]
+                    if ff == 0:
+                        continue
+                    if ff == 1:
+                        tm = np.prod([0.0 if e % 2 else 0.5 ** e / (e + 1) for e in tang])
+                    else:
+                        pos = np.searchsorted(g.cut_faces[d], lin)
+                        tm = g.face_mom[d][pos, fidx[tang]]
+                    rhs += (0.5 if side else -0.5) ** m[d] * (1 if side else -1) * tm
+                rhs += g.eb_nmom[ci, d, vol_idx[m]]
+                worst = max(worst, abs(lhs - rhs))
+    return worst
+
+
+def test_divergence_theorem_2d():
+    assert _divergence_residual(E.circle_config(32)) < 1e-14
+    assert _divergence_residual(E.multi_circle_config(64)) < 1e-14
+
+
+def test_divergence_theorem_3d():
+    assert _divergence_residual(E.sphere_box_config(16)) < 1e-13
+    assert _divergence_residual(E.sphere_inside_config(12)) < 1e-13
+
+
+@pytest.mark.parametrize("key,center,r", [("c0.5_r0.25", (0.5, 0.5), 0.25), ("c0.5_r0.255", (0.5, 0.5), 0.255),
+                                          ("c0.501_r0.25", (0.501, 0.501), 0.25),
+                                          ("c0.51-0.5_r0.25", (0.51, 0.5), 0.25)])
+def test_smallest_volume_fraction_table(key, center, r):
+    """The paper's table of smallest volume fractions (Sec. 3.4.1), two significant digits."""
+    for N, want in zip(GOLD["kappa_min"]["N"], GOLD["kappa_min"][key]):
+        got = E.circle_config(N, center=center, r=r).min_kappa()
+        assert float(f"{got:.1e}") == pytest.approx(want, rel=1e-9), (N, got, want)
+
+
+def test_multi_circle_clearance():
+    g = E.multi_circle_config(128, seed=1)
+    c, r = g.centers[:, :2], g.radii
+    for i in range(len(r)):
+        assert np.all(c[i] - r[i] >= 0.04 - 1e-12) and np.all(c[i] + r[i] <= 0.96 + 1e-12)
+        for j in range(i):
+            assert np.linalg.norm(c[i] - c[j]) - r[i] - r[j] >= 0.04 - 1e-12
+
+
+def test_manufactured_full_cell_average():
+    g = E.circle_config(16)
+    man = E.Manufactured(g, E.sin_product("config2d"))
+    avg = man.cell_avg()
+    c = 0  # cell (0,0) is full
+    x0, x1, h = 0.0, g.h, g.h
+    ex = (-(math.cos(2 * math.pi * x1) - math.cos(2 * math.pi * x0)) / (2 * math.pi * h)) * \
+         ((math.sin(3 * math.pi * x1) - math.sin(3 * math.pi * x0)) / (3 * math.pi * h))
+    assert abs(avg[c] - ex) < 1e-15
