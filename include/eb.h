@@ -1,0 +1,182 @@
+/*
+ * eb.h -- C ABI of the GB300 library for the higher-order cut-cell
+ * finite-volume Poisson discretisation of Devendran, Graves and Johansen
+ * (arXiv:1411.4283).
+ *
+ * The method (Sec. 2): on a Cartesian grid cut by an embedded boundary (EB),
+ * every face f carries a flux stencil s_f = W (A^T W)^+ F (Eq. "stencil
+ * equation solution"), the minimum-||W^-1 s|| solution of A^T s = F, where
+ * the rows of A are volume averages of the monomials (x - x0)^p, |p| <= Q,
+ * over the neighbouring volumes and face averages over the neighbouring
+ * boundary faces (Sec. 2.2.1), F_p is the integral over f of
+ * grad (x - x0)^p . n, and W is the distance weight of Sec. 2.4.  The
+ * Laplacian of a volume is its flux divergence (1/|V_v|) sum_f s_f^T Phi
+ * (Sec. 2.3); boundary values enter through a matrix B.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers unless the name ends in _host;
+ *     the caller owns them; the library never frees or retains them beyond
+ *     the call (eb_build_stencils copies what it needs).
+ *   - All calls are ordered on the given CUDA stream (NULL = legacy default
+ *     stream).  eb_build_stencils and eb_solve synchronise that stream to
+ *     read back small scalars (counts, status, residual norms); eb_apply and
+ *     eb_bc_rhs do not synchronise.
+ *   - Errors are returned as eb_status; nothing is thrown across the ABI.
+ *     eb_last_error_message() gives a human-readable reason for the last
+ *     failure on the calling thread.
+ *   - Cells are indexed c = x + nx*(y + ny*z); faces normal to d are indexed
+ *     x + (nx+[d==0])*(y + (ny+[d==1])*z), where the face with coordinate i_d
+ *     lies at x_d = i_d*h.  Global face ids: faces normal to 0, then 1, then
+ *     2, each block in that order; EB faces follow, id = n_grid_faces + cut
+ *     index.  Cut cells are listed in ascending cell index.
+ *   - Moments are in h-scaled coordinates xi = (x - centre)/h about the cell
+ *     centre (volumes, EB patches) or the face centre (grid faces), divided by
+ *     h^D (volumes) or h^(D-1) (faces), for the graded monomials of degree
+ *     <= moment_degree: degree 0, then for each degree q the exponents
+ *     (p0, p1, ...) with p0 from q down to 0, p1 from q - p0 down to 0, ....
+ *     Face moments use the face's tangential coordinates in ascending
+ *     dimension order.  EB normals point out of the fluid.
+ */
+#ifndef EB_GB300_H
+#define EB_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* eb_stream_t; /* = cudaStream_t */
+
+typedef enum {
+  EB_OK = 0,
+  EB_ERR_INVALID = 1,        /* malformed descriptor or argument */
+  EB_ERR_RANK_DEFICIENT = 2, /* some face's weighted LS system has rank < K (face ids recorded) */
+  EB_ERR_MULTIVALUED = 3,    /* geometry needs more than one volume per cell (unsupported) */
+  EB_ERR_NOT_CONVERGED = 4,  /* solve stopped at its iteration limit */
+  EB_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+  EB_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  EB_ERR_OOM = 7,            /* device allocation failed */
+  EB_ERR_CAPACITY = 8        /* a face needs more LS rows than the kernels support */
+} eb_status;
+
+enum { EB_F32 = 0, EB_F64 = 1 };
+enum { EB_DIRICHLET = 0, EB_NEUMANN = 1 };
+enum { EB_NBR_BOX = 0, EB_NBR_PATH = 1 };
+
+/* Geometry descriptor: the EB moment tables the paper takes from its
+ * geometry generator (Sec. 2.1: volume moments m^p_v, face moments m^p_f,
+ * normal-weighted EB moments m^p_{d,f}).  All pointers are device pointers. */
+typedef struct eb_geom {
+  int32_t dim;               /* 2 or 3 */
+  int32_t n[3];              /* cells per dimension (n[2] = 1 in 2D) */
+  double h;                  /* grid spacing */
+  int32_t moment_degree;     /* degree of the stored moment tables (>= order) */
+  const uint8_t* cell_flag;  /* [ncell]: 0 covered, 1 full, 2 cut */
+  int32_t n_cut;
+  const int32_t* cut_cell;   /* [n_cut] ascending cell indices */
+  const double* vol_mom;     /* [n_cut][K_D] volume moments */
+  const double* eb_mom;      /* [n_cut][K_D] EB-patch moments */
+  const double* eb_nmom;     /* [n_cut][dim][K_D] EB moments weighted by the normal component */
+  const uint8_t* eb_bc;      /* [n_cut] EB_DIRICHLET/EB_NEUMANN, or NULL = all Dirichlet */
+  const uint8_t* face_flag[3];  /* per direction [nface_d]: 0 covered, 1 full, 2 cut */
+  int32_t n_cutface[3];
+  const int32_t* cutface[3];    /* [n_cutface[d]] ascending face indices */
+  const double* face_mom[3];    /* [n_cutface[d]][K_{D-1}] tangential moments */
+} eb_geom;
+
+/* Discretisation parameters (Sec. 2.4).  Defaults: order 4, path radius 3
+ * (2 for order 2), box neighbourhoods, weight threshold 1/2, power 5. */
+typedef struct eb_params {
+  int32_t order;         /* Q: interpolant degree, 2 or 4 (P = Q + 1) */
+  int32_t path_radius;   /* R_n; <= 0 selects the paper's value for the order */
+  int32_t nbr_metric;    /* EB_NBR_BOX (default) or EB_NBR_PATH */
+  int32_t weighted;      /* 1: W_ii as in Sec. 2.4; 0: W = I (unstable control) */
+  double w_threshold;    /* 0.5 */
+  double w_power;        /* 5 */
+} eb_params;
+
+typedef struct eb_stencils eb_stencils; /* opaque, library-owned */
+
+typedef struct eb_build_info {
+  int64_t n_flux_faces;     /* open grid faces + EB faces */
+  int64_t n_unique_faces;   /* faces whose LS system was solved individually */
+  int64_t n_class_faces;    /* faces sharing a translation-invariant class stencil */
+  int32_t n_classes;        /* class stencils solved (includes the interior template) */
+  int32_t max_rows;         /* largest LS system (rows) */
+  int64_t n_irregular_rows; /* cells with their own operator row */
+  int32_t n_row_classes;    /* shared operator rows (wall classes and template) */
+  int64_t lsq_flops;        /* algorithmic FP64 flops of the LS solves */
+  double ms_classify, ms_gather, ms_lsq, ms_assemble; /* device time per phase */
+} eb_build_info;
+
+/* Build all flux stencils and the operator (Sec. 2.2-2.4).
+ * Rank-deficient systems return EB_ERR_RANK_DEFICIENT (no fallback); query
+ * the offending faces with eb_last_error_faces.  *out is NULL on failure. */
+eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_stencils** out, eb_build_info* info,
+                            eb_stream_t stream);
+
+/* y = L phi (kappa_weighted = 0) or kappa .* (L phi) (kappa_weighted = 1):
+ * the homogeneous part of the discrete Laplacian (boundary values zero;
+ * Sec. 2.3).  phi, y: [ncell] of dtype EB_F32 or EB_F64; covered cells of y
+ * are set to 0 and covered entries of phi are ignored.  Never synchronises. */
+eb_status eb_apply(const eb_stencils* st, const void* phi, void* y, int32_t dtype, int32_t kappa_weighted,
+                   eb_stream_t stream);
+
+/* Bg = B g, the boundary-data part of the Laplacian (FP64; kappa-weighted
+ * when kappa_weighted = 1).  g_eb: [n_cut] face averages on the EB faces
+ * (Dirichlet: <phi>_f; Neumann: <grad phi . n>_f); g_wall: values on the
+ * open wall faces in ascending global face id (eb_wall_faces lists them). */
+eb_status eb_bc_rhs(const eb_stencils* st, const double* g_eb, const double* g_wall, double* Bg,
+                    int32_t kappa_weighted, eb_stream_t stream);
+
+typedef struct eb_solve_opts {
+  int32_t mixed;          /* 1: FP32 BiCGStab inner solves + FP64 iterative refinement; 0: FP64 BiCGStab */
+  double inner_tol;       /* relative residual target of each inner solve (mixed), e.g. 1e-5 */
+  int32_t max_inner;      /* iteration cap per inner solve */
+  int32_t max_outer;      /* refinement sweeps (mixed) */
+  int32_t max_iters;      /* total iteration cap */
+  int32_t check_every;    /* host convergence check interval (iterations run as graphs in between) */
+} eb_solve_opts;
+
+typedef struct eb_solve_info {
+  int32_t iterations;     /* total Krylov iterations */
+  int32_t sweeps;         /* refinement sweeps (mixed) */
+  double rel_residual;    /* final ||rhs - kappa L phi||_2 / ||rhs||_2, FP64 */
+  double history[64];     /* FP64 relative residual after each sweep (mixed) or check (FP64) */
+  int32_t n_history;
+} eb_solve_info;
+
+/* Solve L phi = rho - B g to a relative residual tol (kappa-weighted system
+ * kappa L phi = kappa (rho - B g)).  rho: [ncell] cell averages of the
+ * source; phi: [ncell] initial guess on entry, solution on exit (FP64). */
+eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
+                   const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream);
+
+/* Error norms of Sec. 3.3 over the volumes: L_inf, L1 = sum |e||V| / sum|V|,
+ * L2 = (sum e^2 |V| / sum |V|)^(1/2).  err: [ncell] FP64 device; out_host[3]. */
+eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, eb_stream_t stream);
+
+/* Debug / parity: the flux stencil of a face (global face id).  Columns:
+ * volume -> cell index; boundary face -> -(1 + global face id).  Values are
+ * the h-scaled stencil s_hat (s = h^(D-2) s_hat), rows in canonical order
+ * (volumes ascending, wall faces ascending, EB faces ascending).  With
+ * cols_host == NULL only *n is written.  Synchronises the stream. */
+eb_status eb_stencil_query(const eb_stencils* st, int64_t face, int32_t* n, int64_t* cols_host, double* coef_host,
+                           int32_t cap, eb_stream_t stream);
+
+/* Open wall faces in ascending global face id (the g_wall order). */
+eb_status eb_wall_faces(const eb_stencils* st, int64_t* ids_host, int64_t cap, int64_t* n);
+
+/* Faces whose LS system was rank deficient in the last failed build. */
+eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n);
+
+void eb_stencils_destroy(eb_stencils* st);
+const char* eb_status_string(eb_status s);
+const char* eb_last_error_message(void);
+int32_t eb_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,283 @@
+"""GB300 library for the higher-order cut-cell finite-volume Poisson method
+(Devendran, Graves, Johansen, arXiv:1411.4283).
+
+Thin Python binding of the C ABI in ``include/eb.h``: argument marshalling
+only.  Every step of the method -- neighbourhoods, weighted least squares,
+operator assembly, apply, Krylov solve, error norms -- runs in the CUDA
+kernels of ``libeb_gb300.so``.  PyTorch provides device memory and streams.
+
+The library must be built (``paper_1411_4283_gb300.build.build()``); importing
+this package without it raises ImportError -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+EB_OK = 0
+EB_F32, EB_F64 = 0, 1
+EB_DIRICHLET, EB_NEUMANN = 0, 1
+EB_NBR_BOX, EB_NBR_PATH = 0, 1
+STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID", 2: "EB_ERR_RANK_DEFICIENT", 3: "EB_ERR_MULTIVALUED",
+          4: "EB_ERR_NOT_CONVERGED", 5: "EB_ERR_TIMEOUT", 6: "EB_ERR_CUDA", 7: "EB_ERR_OOM", 8: "EB_ERR_CAPACITY"}
+
+_vp = ctypes.c_void_p
+
+
+class EbGeom(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("h", ctypes.c_double),
+                ("moment_degree", ctypes.c_int32), ("cell_flag", _vp), ("n_cut", ctypes.c_int32),
+                ("cut_cell", _vp), ("vol_mom", _vp), ("eb_mom", _vp), ("eb_nmom", _vp), ("eb_bc", _vp),
+                ("face_flag", _vp * 3), ("n_cutface", ctypes.c_int32 * 3), ("cutface", _vp * 3),
+                ("face_mom", _vp * 3)]
+
+
+class EbParams(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("path_radius", ctypes.c_int32), ("nbr_metric", ctypes.c_int32),
+                ("weighted", ctypes.c_int32), ("w_threshold", ctypes.c_double), ("w_power", ctypes.c_double)]
+
+
+class EbBuildInfo(ctypes.Structure):
+    _fields_ = [("n_flux_faces", ctypes.c_int64), ("n_unique_faces", ctypes.c_int64),
+                ("n_class_faces", ctypes.c_int64), ("n_classes", ctypes.c_int32), ("max_rows", ctypes.c_int32),
+                ("n_irregular_rows", ctypes.c_int64), ("n_row_classes", ctypes.c_int32),
+                ("lsq_flops", ctypes.c_int64), ("ms_classify", ctypes.c_double), ("ms_gather", ctypes.c_double),
+                ("ms_lsq", ctypes.c_double), ("ms_assemble", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EbSolveOpts(ctypes.Structure):
+    _fields_ = [("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_inner", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+class EbSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "sweeps": self.sweeps, "rel_residual": self.rel_residual,
+                "history": [self.history[i] for i in range(self.n_history)]}
+
+
+class EbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libeb_gb300.so (raises ImportError when it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1411_4283_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "eb_build_stencils": (i32, [P(EbGeom), P(EbParams), P(_vp), P(EbBuildInfo), _vp]),
+        "eb_apply": (i32, [_vp, _vp, _vp, i32, i32, _vp]),
+        "eb_bc_rhs": (i32, [_vp, _vp, _vp, _vp, i32, _vp]),
+        "eb_solve": (i32, [_vp, _vp, _vp, _vp, dbl, P(EbSolveOpts), _vp, P(EbSolveInfo), _vp]),
+        "eb_norms": (i32, [_vp, _vp, P(dbl), _vp]),
+        "eb_stencil_query": (i32, [_vp, i64, P(i32), P(i64), P(dbl), i32, _vp]),
+        "eb_wall_faces": (i32, [_vp, P(i64), i64, P(i64)]),
+        "eb_last_error_faces": (i32, [P(i64), i32, P(i32)]),
+        "eb_stencils_destroy": (None, [_vp]),
+        "eb_status_string": (ctypes.c_char_p, [i32]),
+        "eb_last_error_message": (ctypes.c_char_p, []),
+        "eb_abi_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(code):
+    if code != EB_OK:
+        raise EbError(code, load().eb_last_error_message().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(a, dtype):
+    import torch
+    if isinstance(a, torch.Tensor):
+        return a.to(device="cuda", dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+class DeviceGeometry:
+    """Device copies of a geometry's moment tables, in the layout eb.h documents."""
+
+    def __init__(self, dim, n, h, moment_degree, cell_flag, cut_cell, vol_mom, eb_mom, eb_nmom, face_flag, cut_faces,
+                 face_mom, eb_bc=None):
+        import torch
+        self.dim = int(dim)
+        self.n = tuple(int(v) for v in n) + (1,) * (3 - len(n))
+        self.h = float(h)
+        self.moment_degree = int(moment_degree)
+        self.cell_flag = _dev(cell_flag, torch.uint8)
+        self.cut_cell = _dev(cut_cell, torch.int32)
+        self.vol_mom = _dev(vol_mom, torch.float64)
+        self.eb_mom = _dev(eb_mom, torch.float64)
+        self.eb_nmom = _dev(eb_nmom, torch.float64)
+        self.eb_bc = _dev(eb_bc, torch.uint8) if eb_bc is not None else None
+        self.face_flag = [_dev(f, torch.uint8) for f in face_flag]
+        self.cut_faces = [_dev(f, torch.int32) for f in cut_faces]
+        self.face_mom = [_dev(f, torch.float64) for f in face_mom]
+        self.n_cut = int(self.cut_cell.numel())
+
+    @classmethod
+    def from_geometry(cls, g, eb_bc=None):
+        """From an object with the eb_inputs.Geometry attributes (flag, cut_cells, vol_mom, ...)."""
+        return cls(g.dim, g.n[:g.dim], g.h, g.qmax, g.flag, g.cut_cells, g.vol_mom, g.eb_mom, g.eb_nmom, g.face_flag,
+                   g.cut_faces, g.face_mom, eb_bc)
+
+    def struct(self) -> EbGeom:
+        s = EbGeom()
+        s.dim = self.dim
+        for d in range(3):
+            s.n[d] = self.n[d]
+        s.h = self.h
+        s.moment_degree = self.moment_degree
+        s.cell_flag = _ptr(self.cell_flag)
+        s.n_cut = self.n_cut
+        s.cut_cell = _ptr(self.cut_cell)
+        s.vol_mom = _ptr(self.vol_mom)
+        s.eb_mom = _ptr(self.eb_mom)
+        s.eb_nmom = _ptr(self.eb_nmom)
+        s.eb_bc = _ptr(self.eb_bc)
+        for d in range(self.dim):
+            s.face_flag[d] = _ptr(self.face_flag[d])
+            s.n_cutface[d] = int(self.cut_faces[d].numel())
+            s.cutface[d] = _ptr(self.cut_faces[d])
+            s.face_mom[d] = _ptr(self.face_mom[d])
+        return s
+
+
+class Stencils:
+    """Owns an eb_stencils handle (freed by eb_stencils_destroy)."""
+
+    def __init__(self, handle, info: EbBuildInfo, geom: DeviceGeometry):
+        self.handle = handle
+        self.info = info.as_dict()
+        self.dim = geom.dim
+        self.n = geom.n
+        self.h = geom.h
+        self.ncell = int(np.prod(geom.n))
+        self.n_cut = geom.n_cut
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.eb_stencils_destroy(self.handle)
+            self.handle = None
+
+
+def eb_build_stencils(geom: DeviceGeometry, order=4, path_radius=0, nbr_metric=EB_NBR_BOX, weighted=True,
+                      w_threshold=0.5, w_power=5.0, stream=None) -> Stencils:
+    lib = load()
+    g = geom.struct()
+    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power)
+    h = ctypes.c_void_p()
+    info = EbBuildInfo()
+    _check(lib.eb_build_stencils(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h), ctypes.byref(info),
+                                 _stream(stream)))
+    return Stencils(h, info, geom)
+
+
+def eb_apply(st: Stencils, phi, y, kappa_weighted=True, stream=None):
+    import torch
+    dt = {torch.float32: EB_F32, torch.float64: EB_F64}[phi.dtype]
+    assert y.dtype == phi.dtype and phi.is_cuda and y.is_cuda and phi.is_contiguous() and y.is_contiguous()
+    assert phi.numel() == st.ncell and y.numel() == st.ncell
+    _check(load().eb_apply(st.handle, _ptr(phi), _ptr(y), dt, int(kappa_weighted), _stream(stream)))
+    return y
+
+
+def eb_wall_faces(st: Stencils) -> np.ndarray:
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib.eb_wall_faces(st.handle, None, 0, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), dtype=np.int64)
+    _check(lib.eb_wall_faces(st.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n.value,
+                             ctypes.byref(n)))
+    return out[:n.value]
+
+
+def eb_bc_rhs(st: Stencils, g_eb, g_wall, Bg, kappa_weighted=True, stream=None):
+    _check(load().eb_bc_rhs(st.handle, _ptr(g_eb), _ptr(g_wall), _ptr(Bg), int(kappa_weighted), _stream(stream)))
+    return Bg
+
+
+def eb_solve(st: Stencils, rho, g_eb, g_wall, phi, tol=1e-12, mixed=True, inner_tol=1e-5, max_inner=20000,
+             max_outer=40, max_iters=400000, stream=None, allow_not_converged=False) -> dict:
+    lib = load()
+    o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, 1)
+    info = EbSolveInfo()
+    code = lib.eb_solve(st.handle, _ptr(rho), _ptr(g_eb), _ptr(g_wall), tol, ctypes.byref(o), _ptr(phi),
+                        ctypes.byref(info), _stream(stream))
+    if not (allow_not_converged and code == 4):
+        _check(code)
+    d = info.as_dict()
+    d["status"] = STATUS.get(code, code)
+    return d
+
+
+def eb_norms(st: Stencils, err, stream=None) -> dict:
+    out = (ctypes.c_double * 3)()
+    _check(load().eb_norms(st.handle, _ptr(err), out, _stream(stream)))
+    return {"linf": out[0], "l1": out[1], "l2": out[2]}
+
+
+def eb_stencil_query(st: Stencils, face: int, stream=None):
+    """(cols, s_hat) of a face; cols: cell index (volume) or -(1 + face id) (boundary face)."""
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.eb_stencil_query(st.handle, int(face), ctypes.byref(n), None, None, 0, _stream(stream)))
+    cols = np.zeros(max(n.value, 1), dtype=np.int64)
+    vals = np.zeros(max(n.value, 1), dtype=np.float64)
+    _check(lib.eb_stencil_query(st.handle, int(face), ctypes.byref(n),
+                                cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value, _stream(stream)))
+    return cols[:n.value], vals[:n.value]
+
+
+def eb_last_error_faces() -> np.ndarray:
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.eb_last_error_faces(None, 0, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), dtype=np.int64)
+    _check(lib.eb_last_error_faces(out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n.value, ctypes.byref(n)))
+    return out[:n.value]
+
+
+__all__ = ["load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+           "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

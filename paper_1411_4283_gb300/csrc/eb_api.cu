@@ -1,0 +1,1163 @@
+// C ABI of the library (include/eb.h): host orchestration of the build,
+// apply and solve phases.  Every arithmetic step of the method runs in the
+// kernels of eb_build.cu, eb_apply.cu and eb_solve.cu; this file validates
+// arguments, allocates library-owned device memory and launches them.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "eb_apply.cuh"
+#include "eb_internal.cuh"
+#include "eb_scan.cuh"
+#include "eb_solve.cuh"
+#include "eb_tables.cuh"
+#include "eb_build.cuh"
+
+namespace eb {
+
+constexpr int LS_SMEM_PER_WARP = (int)sizeof(LsWarpSmem);
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+static thread_local std::vector<int64_t> g_bad_faces;
+
+void set_error(const std::string& msg) { g_err = msg; }
+eb_status cuda_status(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? EB_ERR_OOM : EB_ERR_CUDA;
+}
+
+std::vector<std::vector<int>> monomials(int dim, int q) {
+  std::vector<std::vector<int>> out;
+  for (int deg = 0; deg <= q; ++deg) {
+    if (dim == 1) { out.push_back({deg}); continue; }
+    if (dim == 2) {
+      for (int p0 = deg; p0 >= 0; --p0) out.push_back({p0, deg - p0});
+      continue;
+    }
+    for (int p0 = deg; p0 >= 0; --p0)
+      for (int p1 = deg - p0; p1 >= 0; --p1) out.push_back({p0, p1, deg - p0 - p1});
+  }
+  return out;
+}
+
+static double full1d(int q) { return (q & 1) ? 0.0 : pow(0.5, q) / (q + 1); }
+
+bool make_tables(int dim, int order, int mdeg, Tables* t) {
+  memset(t, 0, sizeof(*t));
+  auto mon = monomials(dim, order);
+  t->dim = dim;
+  t->K = (int)mon.size();
+  t->KS = (int)monomials(dim, mdeg).size();
+  t->KFS = dim > 1 ? (int)monomials(dim - 1, mdeg).size() : 1;
+  if (t->K > MAXK) return false;
+  std::map<std::vector<int>, int> idx;
+  for (int i = 0; i < t->K; ++i) {
+    idx[mon[i]] = i;
+    for (int d = 0; d < 3; ++d) t->mon[i][d] = d < dim ? (int8_t)mon[i][d] : 0;
+  }
+  for (int d = 0; d < dim; ++d) {
+    int e = 0;
+    for (int i = 0; i < t->K; ++i) {
+      for (int j = 0; j <= mon[i][d]; ++j) {
+        std::vector<int> q = mon[i];
+        q[d] = j;
+        if (e >= MAXSH) return false;
+        t->sh_out[d][e] = (uint8_t)i;
+        t->sh_in[d][e] = (uint8_t)idx[q];
+        t->sh_pw[d][e] = (uint8_t)(mon[i][d] - j);
+        double c = 1.0;
+        for (int k = 1; k <= j; ++k) c = c * (mon[i][d] - j + k) / k;  // C(p_d, j)
+        t->sh_c[d][e] = c;
+        ++e;
+      }
+    }
+    t->nsh[d] = e;
+    for (int i = 0; i < t->K; ++i) {
+      if (mon[i][d] == 0) { t->lower[d][i] = -1; continue; }
+      std::vector<int> q = mon[i];
+      q[d] -= 1;
+      t->lower[d][i] = (int8_t)idx[q];
+    }
+    // tangential monomials of faces normal to d
+    std::vector<std::vector<int>> fm = dim > 1 ? monomials(dim - 1, mdeg) : std::vector<std::vector<int>>{{}};
+    std::map<std::vector<int>, int> fidx;
+    for (size_t i = 0; i < fm.size(); ++i) fidx[fm[i]] = (int)i;
+    for (int i = 0; i < t->K; ++i) {
+      if (mon[i][d] != 0) { t->tang[d][i] = -1; t->full_face[d][i] = 0.0; continue; }
+      std::vector<int> pt;
+      double ff = 1.0;
+      for (int k = 0; k < dim; ++k)
+        if (k != d) { pt.push_back(mon[i][k]); ff *= full1d(mon[i][k]); }
+      t->tang[d][i] = dim > 1 ? (int16_t)fidx[pt] : 0;
+      t->full_face[d][i] = ff;
+    }
+  }
+  for (int i = 0; i < t->K; ++i) {
+    double f = 1.0;
+    for (int d = 0; d < dim; ++d) f *= full1d(mon[i][d]);
+    t->full_vol[i] = f;
+  }
+  return true;
+}
+
+static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+static eb_status dalloc(eb_stencils* st, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  st->allocs.push_back((void*)*p);
+  return EB_OK;
+}
+
+// temporary allocations freed at scope exit
+struct Tmp {
+  std::vector<void*> ptrs;
+  ~Tmp() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  eb_status get(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+    ptrs.push_back((void*)*p);
+    return EB_OK;
+  }
+};
+
+#define EB_TRY(x)                  \
+  do {                             \
+    eb_status _s = (x);            \
+    if (_s != EB_OK) return _s;    \
+  } while (0)
+
+// exclusive scan of in[0..n) into out[0..n); returns the total
+template <typename T>
+static eb_status scan(const T* in, int64_t n, int64_t* out, int64_t* total, cudaStream_t s, Tmp& tmp) {
+  int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  if (nb == 0) { *total = 0; return EB_OK; }
+  int64_t* sums;
+  int64_t* dtot;
+  EB_TRY(tmp.get(&sums, nb));
+  EB_TRY(tmp.get(&dtot, 1));
+  k_scan_block_sums<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, sums);
+  k_scan_single<<<1, SCAN_BLOCK, 0, s>>>(sums, nb, dtot);
+  k_scan_apply<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, sums, out);
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaMemcpyAsync(total, dtot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  return EB_OK;
+}
+
+// ------------------------------------------------------------------ small kernels
+
+__global__ void k_scatter_index(const int32_t* idx, int64_t n, int32_t* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[idx[i]] = (int32_t)i;
+}
+
+__global__ void k_kappa(int64_t ncell, const uint8_t* flag, const int32_t* cut_of, const double* vol_mom, int KS,
+                        double* kappa, double* invk) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double k = flag[c] == 0 ? 0.0 : (flag[c] == 1 ? 1.0 : vol_mom[(int64_t)cut_of[c] * KS]);
+  kappa[c] = k;
+  invk[c] = k > 0 ? 1.0 / k : 0.0;
+}
+
+__global__ void k_flag_list(const uint8_t* dil, const uint8_t* flag, int64_t ncell, int32_t* sel) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell) sel[c] = (dil[c] & 1) && flag[c] > 0;
+}
+
+__global__ void k_compact(const int32_t* sel, const int64_t* pos, int64_t n, int32_t* out, int32_t* map) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  if (sel[c]) {
+    out[pos[c]] = (int32_t)c;
+    if (map) map[c] = (int32_t)pos[c];
+  } else if (map) map[c] = -1;
+}
+
+__global__ void k_eb_slots(int64_t n_cut, int64_t base, int64_t n_grid, int64_t* slot_face, int32_t* eb_slot) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cut) return;
+  slot_face[base + i] = n_grid + i;
+  eb_slot[i] = (int32_t)(base + i);
+}
+
+// cell kind and row key: 0 covered, 1 template, 2 irregular.  rowkey: -2 unique, >= 0 class key
+__global__ void k_cell_kind(Dims dm, const uint8_t* flag, const int32_t* fs0, const int32_t* fs1, const int32_t* fs2,
+                            int64_t n_unique_slots, const int32_t* tmpl_slot, uint8_t* kind, int32_t* rowkey,
+                            int64_t* row_rep, int32_t* is_unique) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= dm.ncell) return;
+  is_unique[c] = 0;
+  if (flag[c] == 0) { kind[c] = 0; rowkey[c] = -1; return; }
+  int x[3];
+  x[0] = (int)(c % dm.n[0]);
+  int64_t r = c / dm.n[0];
+  x[1] = (int)(r % dm.n[1]);
+  x[2] = (int)(r / dm.n[1]);
+  const int32_t* fs[3] = {fs0, fs1, fs2};
+  bool uniq = flag[c] == 2, tmpl = flag[c] == 1;
+  for (int d = 0; d < dm.dim; ++d)
+    for (int side = 0; side < 2; ++side) {
+      int fx[3] = {x[0], x[1], x[2]};
+      if (side) fx[d] += 1;
+      int64_t m0 = dm.n[0] + (d == 0), m1 = dm.n[1] + (d == 1);
+      int64_t fl = (int64_t)fx[0] + m0 * ((int64_t)fx[1] + m1 * fx[2]);
+      int32_t sl = fs[d][fl];
+      if (sl < 0) { tmpl = false; continue; }
+      if (sl < n_unique_slots) uniq = true;
+      if (sl != tmpl_slot[d]) tmpl = false;
+    }
+  if (uniq) { kind[c] = 2; rowkey[c] = -2; is_unique[c] = 1; return; }
+  if (tmpl) { kind[c] = 1; rowkey[c] = 0; atomicMin((unsigned long long*)&row_rep[0], (unsigned long long)c); return; }
+  kind[c] = 2;
+  int M = dm.R + 3, key = 0;
+  for (int k = dm.dim - 1; k >= 0; --k) {
+    int lo = x[k] < M - 1 ? x[k] : M - 1;
+    int hi = dm.n[k] - 1 - x[k];
+    hi = hi < M - 1 ? hi : M - 1;
+    key = (key * M + lo) * M + hi;
+  }
+  key += 1;  // 0 is the template
+  rowkey[c] = key;
+  atomicMin((unsigned long long*)&row_rep[key], (unsigned long long)c);
+}
+
+__global__ void k_irr_list(int64_t ncell, const uint8_t* kind, const int64_t* pos, const int32_t* rowkey,
+                           const int32_t* key_row, const int64_t* upos, int64_t ubase, int32_t* irr_cell,
+                           int32_t* irr_row, int32_t* rep_of_row) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell || kind[c] != 2) return;
+  int64_t p = pos[c];
+  irr_cell[p] = (int32_t)c;
+  int32_t row;
+  if (rowkey[c] == -2) {
+    row = (int32_t)(ubase + upos[c]);
+    rep_of_row[row] = (int32_t)c;
+  } else row = key_row[rowkey[c]];
+  irr_row[p] = row;
+}
+
+__global__ void k_is_kind2(int64_t n, const uint8_t* kind, int32_t* sel) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) sel[c] = kind[c] == 2;
+}
+
+__global__ void k_wall_pos(int64_t nnz, const int64_t* bcol, int64_t n_grid, const int64_t* walls, int64_t nwall,
+                           int64_t* pos) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  int64_t c = bcol[k];
+  if (c >= n_grid) { pos[k] = -1; return; }
+  int64_t lo = 0, hi = nwall - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (walls[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  pos[k] = lo;
+}
+
+__global__ void k_diag_inv(int64_t ncell, const uint8_t* kind, const int32_t* irr_map_unused, const double* tmpl,
+                           int center, double* dinv64, float* dinv32) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double d = kind[c] == 1 ? tmpl[center] : 0.0;
+  double v = d != 0.0 ? 1.0 / d : 0.0;
+  dinv64[c] = v;
+  dinv32[c] = (float)v;
+}
+
+__global__ void k_diag_irr(int64_t n_irr, const int32_t* irr_cell, const int32_t* irr_row, const double* rows64,
+                           int64_t n_rows, int center, double* dinv64, float* dinv32) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_irr) return;
+  double d = rows64[(int64_t)center * n_rows + irr_row[t]];
+  double v = d != 0.0 ? 1.0 / d : 0.0;
+  dinv64[irr_cell[t]] = v;
+  dinv32[irr_cell[t]] = (float)v;
+}
+
+__global__ void k_gather_flags(const uint8_t* ff, const int64_t* ids, int64_t n, uint8_t* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ff[ids[i]];
+}
+
+__global__ void k_zero_f64(int64_t n, double* x) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.0;
+}
+
+}  // namespace eb
+
+using namespace eb;
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* eb_status_string(eb_status s) {
+  switch (s) {
+    case EB_OK: return "ok";
+    case EB_ERR_INVALID: return "invalid argument";
+    case EB_ERR_RANK_DEFICIENT: return "rank-deficient least-squares system";
+    case EB_ERR_MULTIVALUED: return "multi-valued cell";
+    case EB_ERR_NOT_CONVERGED: return "not converged";
+    case EB_ERR_TIMEOUT: return "timeout";
+    case EB_ERR_CUDA: return "CUDA error";
+    case EB_ERR_OOM: return "out of device memory";
+    case EB_ERR_CAPACITY: return "LS system larger than supported";
+  }
+  return "unknown";
+}
+
+const char* eb_last_error_message(void) { return g_err.c_str(); }
+int32_t eb_abi_version(void) { return 1; }
+
+void eb_stencils_destroy(eb_stencils* st) {
+  if (!st) return;
+  for (void* p : st->allocs) cudaFree(p);
+  delete st;
+}
+
+eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n) {
+  if (!n) return EB_ERR_INVALID;
+  *n = (int32_t)g_bad_faces.size();
+  for (int32_t i = 0; i < cap && i < *n && ids_host; ++i) ids_host[i] = g_bad_faces[i];
+  return EB_OK;
+}
+
+static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils* st, eb_build_info* info,
+                            cudaStream_t s);
+
+eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_stencils** out, eb_build_info* info,
+                            eb_stream_t stream) {
+  if (!out) { set_error("out is NULL"); return EB_ERR_INVALID; }
+  *out = nullptr;
+  g_bad_faces.clear();
+  eb_stencils* st = new eb_stencils();
+  eb_build_info local;
+  memset(&local, 0, sizeof(local));
+  eb_status r = build_impl(geom, params, st, info ? info : &local, (cudaStream_t)stream);
+  if (r != EB_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    eb_stencils_destroy(st);
+    return r;
+  }
+  *out = st;
+  return EB_OK;
+}
+
+static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils* st, eb_build_info* info,
+                            cudaStream_t s) {
+  if (!g) { set_error("geometry descriptor is NULL"); return EB_ERR_INVALID; }
+  eb_params P = {4, 0, EB_NBR_BOX, 1, 0.5, 5.0};
+  if (prm) P = *prm;
+  if (g->dim != 2 && g->dim != 3) { set_error("dim must be 2 or 3"); return EB_ERR_INVALID; }
+  if (P.order != 2 && P.order != 4) { set_error("order must be 2 or 4"); return EB_ERR_INVALID; }
+  if (g->moment_degree < P.order) { set_error("moment tables shallower than the order"); return EB_ERR_INVALID; }
+  if (P.nbr_metric != EB_NBR_BOX && P.nbr_metric != EB_NBR_PATH) { set_error("bad nbr_metric"); return EB_ERR_INVALID; }
+  int R = P.path_radius > 0 ? P.path_radius : (P.order == 2 ? 2 : 3);
+  if (R > 3) { set_error("path radius > 3 not supported"); return EB_ERR_INVALID; }
+  Dims& dm = st->dm;
+  memset(&dm, 0, sizeof(dm));
+  dm.dim = g->dim;
+  for (int d = 0; d < 3; ++d) dm.n[d] = d < g->dim ? g->n[d] : 1;
+  for (int d = 0; d < g->dim; ++d)
+    if (dm.n[d] < 1) { set_error("bad grid size"); return EB_ERR_INVALID; }
+  dm.ncell = (int64_t)dm.n[0] * dm.n[1] * dm.n[2];
+  if (dm.ncell >= (1ll << 31)) { set_error("grid too large for int32 cell indices"); return EB_ERR_INVALID; }
+  int64_t fb = 0;
+  for (int d = 0; d < 3; ++d) {
+    dm.nface[d] = d < g->dim ? (int64_t)(dm.n[0] + (d == 0)) * (dm.n[1] + (d == 1)) * (dm.n[2] + (d == 2)) : 0;
+    dm.face_base[d] = fb;
+    fb += dm.nface[d];
+  }
+  dm.n_grid_faces = fb;
+  dm.order = P.order;
+  dm.R = R;
+  dm.nbr_box = P.nbr_metric == EB_NBR_BOX;
+  dm.weighted = P.weighted;
+  dm.w_threshold = P.w_threshold;
+  dm.w_power = P.w_power;
+  dm.mdeg = g->moment_degree;
+  dm.h = g->h;
+  dm.n_cut = g->n_cut;
+  if (!(g->h > 0)) { set_error("h must be positive"); return EB_ERR_INVALID; }
+  if (!g->cell_flag || (g->n_cut > 0 && (!g->cut_cell || !g->vol_mom || !g->eb_mom || !g->eb_nmom))) {
+    set_error("missing geometry arrays");
+    return EB_ERR_INVALID;
+  }
+  Tables T;
+  if (!make_tables(g->dim, P.order, g->moment_degree, &T)) { set_error("table construction failed"); return EB_ERR_INVALID; }
+  dm.K = T.K;
+  dm.KS = T.KS;
+  dm.KFS = T.KFS;
+  const int D = g->dim;
+  const int64_t N = dm.ncell;
+  Tmp tmp;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) EB_CUDA(cudaEventCreate(&ev[i]));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+    }
+  } evg{ev};
+  EB_CUDA(cudaEventRecord(ev[0], s));
+
+  // ---- library-owned copies of the geometry
+  Tables* dT;
+  EB_TRY(dalloc(st, &dT, 1));
+  EB_CUDA(cudaMemcpyAsync(dT, &T, sizeof(T), cudaMemcpyHostToDevice, s));
+  EB_TRY(dalloc(st, &st->flag, N));
+  EB_CUDA(cudaMemcpyAsync(st->flag, g->cell_flag, N, cudaMemcpyDeviceToDevice, s));
+  const int64_t nc = g->n_cut;
+  EB_TRY(dalloc(st, &st->cut_cell, nc));
+  EB_TRY(dalloc(st, &st->vol_mom, nc * T.KS));
+  EB_TRY(dalloc(st, &st->eb_mom, nc * T.KS));
+  EB_TRY(dalloc(st, &st->eb_nmom, nc * D * T.KS));
+  EB_TRY(dalloc(st, &st->eb_bc, nc));
+  if (nc > 0) {
+    EB_CUDA(cudaMemcpyAsync(st->cut_cell, g->cut_cell, nc * 4, cudaMemcpyDeviceToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(st->vol_mom, g->vol_mom, nc * T.KS * 8, cudaMemcpyDeviceToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(st->eb_mom, g->eb_mom, nc * T.KS * 8, cudaMemcpyDeviceToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(st->eb_nmom, g->eb_nmom, nc * D * T.KS * 8, cudaMemcpyDeviceToDevice, s));
+    if (g->eb_bc) EB_CUDA(cudaMemcpyAsync(st->eb_bc, g->eb_bc, nc, cudaMemcpyDeviceToDevice, s));
+    else EB_CUDA(cudaMemsetAsync(st->eb_bc, 0, nc, s));
+  }
+  EB_TRY(dalloc(st, &st->cut_of_cell, N));
+  EB_CUDA(cudaMemsetAsync(st->cut_of_cell, 0xFF, N * 4, s));
+  if (nc > 0) k_scatter_index<<<nblk(nc, 256), 256, 0, s>>>(st->cut_cell, nc, st->cut_of_cell);
+  for (int d = 0; d < D; ++d) {
+    if (!g->face_flag[d]) { set_error("missing face flags"); return EB_ERR_INVALID; }
+    EB_TRY(dalloc(st, &st->face_flag[d], dm.nface[d]));
+    EB_CUDA(cudaMemcpyAsync(st->face_flag[d], g->face_flag[d], dm.nface[d], cudaMemcpyDeviceToDevice, s));
+    int64_t ncf = g->n_cutface[d];
+    EB_TRY(dalloc(st, &st->cutface_of[d], dm.nface[d]));
+    EB_CUDA(cudaMemsetAsync(st->cutface_of[d], 0xFF, dm.nface[d] * 4, s));
+    EB_TRY(dalloc(st, &st->face_mom[d], ncf * T.KFS));
+    if (ncf > 0) {
+      if (!g->cutface[d] || !g->face_mom[d]) { set_error("missing cut-face arrays"); return EB_ERR_INVALID; }
+      EB_CUDA(cudaMemcpyAsync(st->face_mom[d], g->face_mom[d], ncf * T.KFS * 8, cudaMemcpyDeviceToDevice, s));
+      k_scatter_index<<<nblk(ncf, 256), 256, 0, s>>>(g->cutface[d], ncf, st->cutface_of[d]);
+    }
+  }
+  EB_TRY(dalloc(st, &st->kappa, N));
+  double* invk;
+  EB_TRY(dalloc(st, &invk, N));
+  k_kappa<<<nblk(N, 256), 256, 0, s>>>(N, st->flag, st->cut_of_cell, st->vol_mom, T.KS, st->kappa, invk);
+  EB_CUDA(cudaGetLastError());
+
+  // ---- 1. masks, face classes, slots
+  uint8_t *m0, *m1;
+  EB_TRY(tmp.get(&m0, N));
+  EB_TRY(tmp.get(&m1, N));
+  k_mark<<<nblk(N, 256), 256, 0, s>>>(dm, st->flag, m0);
+  uint8_t* cur = m0;
+  uint8_t* nxt = m1;
+  for (int ax = 0; ax < D; ++ax) {
+    k_dilate<<<nblk(N, 256), 256, 0, s>>>(dm, ax, R, cur, nxt);
+    std::swap(cur, nxt);
+  }
+  uint8_t* dil = cur;
+  const int M = R + 3;
+  int64_t nkeys = 3;
+  for (int d = 0; d < D; ++d) nkeys *= (int64_t)M * M;
+  int64_t* class_rep;
+  EB_TRY(tmp.get(&class_rep, nkeys));
+  EB_CUDA(cudaMemsetAsync(class_rep, 0xFF, nkeys * 8, s));
+  int32_t* state[3] = {nullptr, nullptr, nullptr};
+  int32_t* isu[3] = {nullptr, nullptr, nullptr};
+  int64_t* upos[3] = {nullptr, nullptr, nullptr};
+  int64_t nu[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) {
+    EB_TRY(tmp.get(&state[d], dm.nface[d]));
+    EB_TRY(tmp.get(&isu[d], dm.nface[d]));
+    EB_TRY(tmp.get(&upos[d], dm.nface[d]));
+    k_classify_faces<<<nblk(dm.nface[d], 256), 256, 0, s>>>(dm, d, st->face_flag[d], dil, state[d], class_rep, isu[d]);
+    EB_CUDA(cudaGetLastError());
+    EB_TRY(scan<int32_t>(isu[d], dm.nface[d], upos[d], &nu[d], s, tmp));
+  }
+  std::vector<int64_t> h_rep(nkeys);
+  EB_CUDA(cudaMemcpyAsync(h_rep.data(), class_rep, nkeys * 8, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  int64_t n_unique_grid = nu[0] + nu[1] + nu[2];
+  int64_t n_unique = n_unique_grid + nc;
+  std::vector<int32_t> h_class_slot(nkeys, -1);
+  std::vector<int64_t> class_faces;
+  int32_t tmpl_slot_h[3] = {-1, -1, -1};
+  for (int64_t k = 0; k < nkeys; ++k) {
+    if (h_rep[k] == -1) continue;
+    h_class_slot[k] = (int32_t)(n_unique + class_faces.size());
+    class_faces.push_back(h_rep[k]);
+  }
+  // template class of direction d: every clamped distance at its maximum
+  for (int d = 0; d < D; ++d) {
+    int64_t key = 0;
+    for (int k = D - 1; k >= 0; --k) key = (key * M + (M - 1)) * M + (M - 1);
+    key = key * 3 + d;
+    tmpl_slot_h[d] = h_class_slot[key];
+  }
+  const int64_t n_slots = n_unique + (int64_t)class_faces.size();
+  st->n_slots = n_slots;
+  st->n_unique = n_unique;
+  st->n_classes = (int32_t)class_faces.size();
+  EB_TRY(dalloc(st, &st->slot_face, n_slots));
+  int32_t* class_slot_d;
+  EB_TRY(tmp.get(&class_slot_d, nkeys));
+  EB_CUDA(cudaMemcpyAsync(class_slot_d, h_class_slot.data(), nkeys * 4, cudaMemcpyHostToDevice, s));
+  if (!class_faces.empty())
+    EB_CUDA(cudaMemcpyAsync(st->slot_face + n_unique, class_faces.data(), class_faces.size() * 8,
+                            cudaMemcpyHostToDevice, s));
+  int64_t ub = 0;
+  for (int d = 0; d < D; ++d) {
+    EB_TRY(dalloc(st, &st->face_slot[d], dm.nface[d]));
+    k_face_slots<<<nblk(dm.nface[d], 256), 256, 0, s>>>(dm, d, state[d], upos[d], ub, class_slot_d,
+                                                       st->face_slot[d], st->slot_face);
+    ub += nu[d];
+  }
+  EB_TRY(dalloc(st, &st->eb_slot, nc));
+  if (nc > 0) k_eb_slots<<<nblk(nc, 256), 256, 0, s>>>(nc, n_unique_grid, dm.n_grid_faces, st->slot_face, st->eb_slot);
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaEventRecord(ev[1], s));
+
+  // ---- 2. reach masks of cells whose neighbourhood sees a non-full cell
+  int32_t *sel, *near_list, *reach_idx;
+  int64_t* near_pos;
+  int64_t n_near = 0;
+  EB_TRY(tmp.get(&sel, N));
+  EB_TRY(tmp.get(&near_pos, N));
+  EB_TRY(tmp.get(&reach_idx, N));
+  k_flag_list<<<nblk(N, 256), 256, 0, s>>>(dil, st->flag, N, sel);
+  EB_TRY(scan<int32_t>(sel, N, near_pos, &n_near, s, tmp));
+  EB_TRY(tmp.get(&near_list, n_near));
+  k_compact<<<nblk(N, 256), 256, 0, s>>>(sel, near_pos, N, near_list, reach_idx);
+  Mask* masks;
+  EB_TRY(tmp.get(&masks, n_near));
+  if (n_near > 0)
+    k_reach<<<nblk(n_near, 128), 128, 0, s>>>(dm, near_list, n_near, st->flag, st->face_flag[0],
+                                              D > 1 ? st->face_flag[1] : st->face_flag[0],
+                                              D > 2 ? st->face_flag[2] : st->face_flag[0], masks);
+  EB_CUDA(cudaGetLastError());
+
+  // ---- 3. gather row lists
+  GatherArgs ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.dm = dm;
+  ga.flag = st->flag;
+  for (int d = 0; d < 3; ++d) ga.ff[d] = d < D ? st->face_flag[d] : st->face_flag[0];
+  ga.reach_idx = reach_idx;
+  ga.masks = masks;
+  ga.cut_of_cell = st->cut_of_cell;
+  ga.slot_face = st->slot_face;
+  int64_t* counts;
+  int32_t* too_many;
+  EB_TRY(tmp.get(&counts, n_slots + 1));
+  EB_TRY(tmp.get(&too_many, 1));
+  EB_CUDA(cudaMemsetAsync(too_many, 0, 4, s));
+  ga.count = counts;
+  ga.too_many = too_many;
+  ga.row_ptr = nullptr;
+  k_gather<<<nblk(n_slots, 128), 128, 0, s>>>(ga, n_slots, st->cut_cell);
+  EB_CUDA(cudaGetLastError());
+  EB_TRY(dalloc(st, &st->row_ptr, n_slots + 1));
+  int64_t nnz = 0;
+  EB_CUDA(cudaMemsetAsync(counts + n_slots, 0, 8, s));
+  EB_TRY(scan<int64_t>(counts, n_slots + 1, st->row_ptr, &nnz, s, tmp));
+  int32_t h_too = 0;
+  EB_CUDA(cudaMemcpy(&h_too, too_many, 4, cudaMemcpyDeviceToHost));
+  if (h_too) { set_error("a face has more LS rows than the kernel supports"); return EB_ERR_CAPACITY; }
+  EB_TRY(dalloc(st, &st->row_desc, nnz));
+  EB_TRY(dalloc(st, &st->row_val, nnz));
+  ga.row_ptr = st->row_ptr;
+  ga.row_desc = st->row_desc;
+  k_gather<<<nblk(n_slots, 128), 128, 0, s>>>(ga, n_slots, st->cut_cell);
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaEventRecord(ev[2], s));
+
+  // ---- 4. weighted least squares (FP64)
+  int dev = 0, nsm = 0;
+  EB_CUDA(cudaGetDevice(&dev));
+  EB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  size_t ls_smem = (size_t)LS_WARPS * LS_SMEM_PER_WARP;
+  EB_CUDA(cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
+  int64_t nblocks = std::min<int64_t>(nsm, (n_slots + LS_WARPS - 1) / LS_WARPS);
+  if (nblocks < 1) nblocks = 1;
+  double* scratch;
+  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_WARPS * MAXROWS * (MAXK + 2)));
+  int32_t *next, *status;
+  EB_TRY(tmp.get(&next, 1));
+  EB_TRY(tmp.get(&status, n_slots));
+  EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
+  LsArgs la;
+  memset(&la, 0, sizeof(la));
+  la.dm = dm;
+  la.T = dT;
+  la.flag = st->flag;
+  la.cut_of_cell = st->cut_of_cell;
+  la.cut_cell = st->cut_cell;
+  la.vol_mom = st->vol_mom;
+  la.eb_mom = st->eb_mom;
+  la.eb_nmom = st->eb_nmom;
+  la.eb_bc = st->eb_bc;
+  for (int d = 0; d < 3; ++d) {
+    la.cutface_of[d] = d < D ? st->cutface_of[d] : st->cutface_of[0];
+    la.face_mom[d] = d < D ? st->face_mom[d] : st->face_mom[0];
+  }
+  la.slot_face = st->slot_face;
+  la.row_ptr = st->row_ptr;
+  la.row_desc = st->row_desc;
+  la.row_val = st->row_val;
+  la.n_slots = n_slots;
+  la.next = next;
+  la.status = status;
+  la.scratch = scratch;
+  if (n_slots > 0) k_lsq<<<(unsigned)nblocks, LS_WARPS * 32, ls_smem, s>>>(la);
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaEventRecord(ev[3], s));
+  {
+    std::vector<int32_t> hs(n_slots);
+    EB_CUDA(cudaMemcpyAsync(hs.data(), status, n_slots * 4, cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> hf(n_slots);
+    EB_CUDA(cudaMemcpyAsync(hf.data(), st->slot_face, n_slots * 8, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    int unsupported = 0;
+    for (int64_t i = 0; i < n_slots; ++i) {
+      if (hs[i] == 1) g_bad_faces.push_back(hf[i]);
+      if (hs[i] == 2) unsupported = 1;
+    }
+    if (unsupported) { set_error("Neumann EB rows are not supported by the GPU build"); return EB_ERR_INVALID; }
+    if (!g_bad_faces.empty()) {
+      set_error("rank-deficient LS systems: " + std::to_string(g_bad_faces.size()) + " faces");
+      return EB_ERR_RANK_DEFICIENT;
+    }
+  }
+
+  // ---- 5. operator rows and boundary matrix
+  // footprint
+  {
+    std::vector<int32_t> off;
+    std::vector<int8_t> dd;
+    int L = R + 1, S = 2 * L + 1;
+    std::vector<int16_t> lut(S * S * S, -1);
+    int zr = D == 3 ? L : 0;
+    for (int z = -zr; z <= zr; ++z)
+      for (int y = -L; y <= L; ++y)
+        for (int x = -L; x <= L; ++x) {
+          if (!in_footprint(x, y, z, R, dm.nbr_box)) continue;
+          lut[(x + L) + S * ((y + L) + S * (z + L))] = (int16_t)off.size();
+          off.push_back((int32_t)((int64_t)x + (int64_t)dm.n[0] * ((int64_t)y + (int64_t)dm.n[1] * z)));
+          dd.push_back((int8_t)x);
+          dd.push_back((int8_t)y);
+          dd.push_back((int8_t)z);
+        }
+    st->nfoot = (int)off.size();
+    EB_TRY(dalloc(st, &st->foot_off, off.size()));
+    EB_TRY(dalloc(st, &st->foot_d, dd.size()));
+    int16_t* dlut;
+    EB_TRY(tmp.get(&dlut, lut.size()));
+    EB_CUDA(cudaMemcpyAsync(st->foot_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(st->foot_d, dd.data(), dd.size(), cudaMemcpyHostToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(dlut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, s));
+    int center = lut[L + S * (L + S * L)];
+    int64_t nrk = 1;
+    for (int d = 0; d < D; ++d) nrk *= (int64_t)M * M;
+    nrk += 1;  // key 0: template
+    int64_t* row_rep;
+    int32_t *rowkey, *isuc, *tslot;
+    int64_t* upc;
+    EB_TRY(tmp.get(&row_rep, nrk));
+    EB_TRY(tmp.get(&rowkey, N));
+    EB_TRY(tmp.get(&isuc, N));
+    EB_TRY(tmp.get(&upc, N));
+    EB_TRY(tmp.get(&tslot, 3));
+    EB_CUDA(cudaMemsetAsync(row_rep, 0xFF, nrk * 8, s));
+    EB_CUDA(cudaMemcpyAsync(tslot, tmpl_slot_h, 12, cudaMemcpyHostToDevice, s));
+    EB_TRY(dalloc(st, &st->cell_kind, N));
+    k_cell_kind<<<nblk(N, 256), 256, 0, s>>>(dm, st->flag, st->face_slot[0], D > 1 ? st->face_slot[1] : nullptr,
+                                            D > 2 ? st->face_slot[2] : nullptr, n_unique, tslot, st->cell_kind,
+                                            rowkey, row_rep, isuc);
+    EB_CUDA(cudaGetLastError());
+    int64_t n_ucell = 0;
+    EB_TRY(scan<int32_t>(isuc, N, upc, &n_ucell, s, tmp));
+    std::vector<int64_t> h_rrep(nrk);
+    EB_CUDA(cudaMemcpyAsync(h_rrep.data(), row_rep, nrk * 8, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    // rows: [template (always row 0, even if unused)] [class rows] [unique rows]
+    std::vector<int32_t> key_row(nrk, -1), rep_cells;
+    rep_cells.push_back(h_rrep[0] >= 0 ? (int32_t)h_rrep[0] : -1);
+    key_row[0] = 0;
+    for (int64_t k = 1; k < nrk; ++k)
+      if (h_rrep[k] >= 0) {
+        key_row[k] = (int32_t)rep_cells.size();
+        rep_cells.push_back((int32_t)h_rrep[k]);
+      }
+    int64_t n_class_rows = (int64_t)rep_cells.size();
+    st->n_row_classes = (int32_t)n_class_rows;
+    st->n_rows = n_class_rows + n_ucell;
+    // irregular list
+    int32_t* k2;
+    int64_t* k2pos;
+    EB_TRY(tmp.get(&k2, N));
+    EB_TRY(tmp.get(&k2pos, N));
+    k_is_kind2<<<nblk(N, 256), 256, 0, s>>>(N, st->cell_kind, k2);
+    EB_TRY(scan<int32_t>(k2, N, k2pos, &st->n_irr, s, tmp));
+    EB_TRY(dalloc(st, &st->irr_cell, st->n_irr));
+    EB_TRY(dalloc(st, &st->irr_row, st->n_irr));
+    int32_t *key_row_d, *rep_d;
+    EB_TRY(tmp.get(&key_row_d, nrk));
+    EB_TRY(tmp.get(&rep_d, st->n_rows));
+    EB_CUDA(cudaMemcpyAsync(key_row_d, key_row.data(), nrk * 4, cudaMemcpyHostToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(rep_d, rep_cells.data(), n_class_rows * 4, cudaMemcpyHostToDevice, s));
+    k_irr_list<<<nblk(N, 256), 256, 0, s>>>(N, st->cell_kind, k2pos, rowkey, key_row_d, upc, n_class_rows,
+                                           st->irr_cell, st->irr_row, rep_d);
+    EB_CUDA(cudaGetLastError());
+    // operator rows
+    EB_TRY(dalloc(st, &st->rows64, (size_t)st->nfoot * st->n_rows));
+    EB_TRY(dalloc(st, &st->rows32, (size_t)st->nfoot * st->n_rows));
+    AsmArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.dm = dm;
+    aa.flag = st->flag;
+    aa.cut_of_cell = st->cut_of_cell;
+    for (int d = 0; d < 3; ++d) {
+      aa.face_slot[d] = d < D ? st->face_slot[d] : nullptr;
+      aa.ff[d] = d < D ? st->face_flag[d] : nullptr;
+    }
+    aa.eb_slot = st->eb_slot;
+    aa.slot_face = st->slot_face;
+    aa.row_ptr = st->row_ptr;
+    aa.row_desc = st->row_desc;
+    aa.row_val = st->row_val;
+    aa.nfoot = st->nfoot;
+    aa.foot_lut = dlut;
+    aa.n_rows = st->n_rows;
+    aa.rows64 = st->rows64;
+    aa.rows32 = st->rows32;
+    aa.inv_h2 = 1.0 / (dm.h * dm.h);
+    int32_t* aerr;
+    EB_TRY(tmp.get(&aerr, 1));
+    EB_CUDA(cudaMemsetAsync(aerr, 0, 4, s));
+    // the template row may have no representative on small grids: build the others, fill it below
+    int first = rep_cells[0] >= 0 ? 0 : 1;
+    int64_t nrep = st->n_rows - first;
+    if (first) EB_CUDA(cudaMemsetAsync(st->rows64, 0, 8, s));  // row 0 of entry 0 only; the template row is unused
+    if (nrep > 0) {
+      size_t sm = (size_t)8 * st->nfoot * 8;
+      k_assemble_rows<<<nblk(nrep, 8), 256, sm, s>>>(aa, rep_d + first, nrep, first, aerr);
+    }
+    EB_CUDA(cudaGetLastError());
+    EB_TRY(dalloc(st, &st->tmpl64, st->nfoot));
+    EB_TRY(dalloc(st, &st->tmpl32, st->nfoot));
+    EB_CUDA(cudaMemsetAsync(st->tmpl64, 0, st->nfoot * 8, s));
+    EB_CUDA(cudaMemsetAsync(st->tmpl32, 0, st->nfoot * 4, s));
+    if (first == 0) {
+      EB_CUDA(cudaMemcpy2DAsync(st->tmpl64, 8, st->rows64, st->n_rows * 8, 8, st->nfoot, cudaMemcpyDeviceToDevice, s));
+      EB_CUDA(cudaMemcpy2DAsync(st->tmpl32, 4, st->rows32, st->n_rows * 4, 4, st->nfoot, cudaMemcpyDeviceToDevice, s));
+    }
+    // Jacobi diagonal of the kappa-weighted operator
+    double* dinv64;
+    float* dinv32;
+    EB_TRY(dalloc(st, &dinv64, N));
+    EB_TRY(dalloc(st, &dinv32, N));
+    k_diag_inv<<<nblk(N, 256), 256, 0, s>>>(N, st->cell_kind, nullptr, st->tmpl64, center, dinv64, dinv32);
+    if (st->n_irr > 0)
+      k_diag_irr<<<nblk(st->n_irr, 256), 256, 0, s>>>(st->n_irr, st->irr_cell, st->irr_row, st->rows64, st->n_rows,
+                                                       center, dinv64, dinv32);
+    EB_CUDA(cudaGetLastError());
+    // boundary matrix over irregular cells
+    int64_t *bcnt, nbnz = 0;
+    EB_TRY(tmp.get(&bcnt, st->n_irr + 1));
+    EB_CUDA(cudaMemsetAsync(bcnt, 0, (st->n_irr + 1) * 8, s));
+    if (st->n_irr > 0)
+      k_assemble_b<<<nblk(st->n_irr, 128), 128, 0, s>>>(aa, st->irr_cell, st->n_irr, bcnt, nullptr, nullptr, nullptr,
+                                                        nullptr);
+    EB_TRY(dalloc(st, &st->b_ptr, st->n_irr + 1));
+    EB_TRY(scan<int64_t>(bcnt, st->n_irr + 1, st->b_ptr, &nbnz, s, tmp));
+    EB_TRY(dalloc(st, &st->b_col, nbnz));
+    EB_TRY(dalloc(st, &st->b_val, nbnz));
+    if (st->n_irr > 0)
+      k_assemble_b<<<nblk(st->n_irr, 128), 128, 0, s>>>(aa, st->irr_cell, st->n_irr, nullptr, st->b_ptr, st->b_col,
+                                                        st->b_val, nullptr);
+    EB_CUDA(cudaGetLastError());
+    int32_t h_aerr = 0;
+    EB_CUDA(cudaMemcpyAsync(&h_aerr, aerr, 4, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    if (h_aerr) { set_error("stencil column outside the operator footprint"); return EB_ERR_INVALID; }
+    // wall faces (ascending id) and the position of each B wall entry in that list
+    {
+      std::vector<int64_t> cand;
+      for (int d = 0; d < D; ++d) {
+        int64_t m0 = dm.n[0] + (d == 0), m1 = dm.n[1] + (d == 1);
+        int nz = dm.n[2] + (d == 2), ny = dm.n[1] + (d == 1), nx = dm.n[0] + (d == 0);
+        for (int z = 0; z < nz; ++z)
+          for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+              int c[3] = {x, y, z};
+              if (c[d] != 0 && c[d] != dm.n[d]) {
+                if (d == 0) x = dm.n[0] - 1;  // jump to the high wall
+                continue;
+              }
+              cand.push_back(dm.face_base[d] + x + m0 * ((int64_t)y + m1 * z));
+            }
+      }
+      std::sort(cand.begin(), cand.end());
+      int64_t nc2 = (int64_t)cand.size();
+      int64_t* dcand;
+      uint8_t* dfl;
+      EB_TRY(tmp.get(&dcand, nc2));
+      EB_TRY(tmp.get(&dfl, nc2));
+      EB_CUDA(cudaMemcpyAsync(dcand, cand.data(), nc2 * 8, cudaMemcpyHostToDevice, s));
+      std::vector<uint8_t> hfl(nc2);
+      int64_t off0 = 0;
+      for (int d = 0; d < D; ++d) {
+        // candidates of direction d are contiguous after sorting (global ids are direction-major)
+        int64_t lo = std::lower_bound(cand.begin(), cand.end(), dm.face_base[d]) - cand.begin();
+        int64_t hi = std::lower_bound(cand.begin(), cand.end(), dm.face_base[d] + dm.nface[d]) - cand.begin();
+        if (hi > lo) {
+          // shift ids to local indices on the fly
+          std::vector<int64_t> loc(cand.begin() + lo, cand.begin() + hi);
+          for (auto& v : loc) v -= dm.face_base[d];
+          int64_t* dloc;
+          EB_TRY(tmp.get(&dloc, hi - lo));
+          EB_CUDA(cudaMemcpyAsync(dloc, loc.data(), (hi - lo) * 8, cudaMemcpyHostToDevice, s));
+          k_gather_flags<<<nblk(hi - lo, 256), 256, 0, s>>>(st->face_flag[d], dloc, hi - lo, dfl + lo);
+          EB_CUDA(cudaMemcpyAsync(hfl.data() + lo, dfl + lo, hi - lo, cudaMemcpyDeviceToHost, s));
+          EB_CUDA(cudaStreamSynchronize(s));
+        }
+        off0 = hi;
+      }
+      (void)off0;
+      st->wall_ids_host.clear();
+      for (int64_t i = 0; i < nc2; ++i)
+        if (hfl[i]) st->wall_ids_host.push_back(cand[i]);
+      st->n_wall = (int64_t)st->wall_ids_host.size();
+      EB_TRY(dalloc(st, &st->wall_ids, st->n_wall));
+      if (st->n_wall)
+        EB_CUDA(cudaMemcpyAsync(st->wall_ids, st->wall_ids_host.data(), st->n_wall * 8, cudaMemcpyHostToDevice, s));
+      int64_t* wpos;
+      EB_TRY(dalloc(st, &wpos, nbnz));
+      if (nbnz > 0)
+        k_wall_pos<<<nblk(nbnz, 256), 256, 0, s>>>(nbnz, st->b_col, dm.n_grid_faces, st->wall_ids, st->n_wall, wpos);
+      EB_CUDA(cudaGetLastError());
+      st->b_wpos = wpos;
+      st->dinv64 = dinv64;
+      st->dinv32 = dinv32;
+      st->inv_kappa = invk;
+    }
+    info->n_irregular_rows = st->n_rows - n_class_rows;
+    info->n_row_classes = (int32_t)n_class_rows;
+  }
+  EB_CUDA(cudaEventRecord(ev[4], s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  // ---- info
+  info->n_unique_faces = n_unique;
+  info->n_class_faces = 0;
+  for (int d = 0; d < D; ++d) info->n_class_faces += dm.nface[d];  // refined below
+  {
+    int64_t n_open = 0, n_cls = 0;
+    for (int d = 0; d < D; ++d) {
+      std::vector<int32_t> hs(dm.nface[d]);
+      EB_CUDA(cudaMemcpy(hs.data(), st->face_slot[d], dm.nface[d] * 4, cudaMemcpyDeviceToHost));
+      for (int32_t v : hs) {
+        if (v >= 0) ++n_open;
+        if (v >= n_unique) ++n_cls;
+      }
+    }
+    info->n_flux_faces = n_open + nc;
+    info->n_class_faces = n_cls;
+  }
+  info->n_classes = st->n_classes;
+  {
+    std::vector<int64_t> rp(n_slots + 1);
+    EB_CUDA(cudaMemcpy(rp.data(), st->row_ptr, (n_slots + 1) * 8, cudaMemcpyDeviceToHost));
+    int32_t mx = 0;
+    double fl = 0.0;
+    int K = T.K;
+    for (int64_t i = 0; i < n_slots; ++i) {
+      int64_t n = rp[i + 1] - rp[i];
+      mx = std::max<int32_t>(mx, (int32_t)n);
+      // Householder QR of an n x K matrix plus the semi-normal solves and corrections
+      fl += 2.0 * n * K * K - 2.0 / 3.0 * K * K * K + 6.0 * n * K + 2.0 * K * K;
+    }
+    info->max_rows = mx;
+    info->lsq_flops = (int64_t)fl;
+  }
+  float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
+  cudaEventElapsedTime(&t01, ev[0], ev[1]);
+  cudaEventElapsedTime(&t12, ev[1], ev[2]);
+  cudaEventElapsedTime(&t23, ev[2], ev[3]);
+  cudaEventElapsedTime(&t34, ev[3], ev[4]);
+  info->ms_classify = t01;
+  info->ms_gather = t12;
+  info->ms_lsq = t23;
+  info->ms_assemble = t34;
+  return EB_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== apply / solve / query
+
+namespace eb {
+
+template <typename T>
+static ApplyArgs<T> apply_args(const eb_stencils* st, int kw);
+
+template <>
+ApplyArgs<float> apply_args<float>(const eb_stencils* st, int kw) {
+  ApplyArgs<float> a;
+  a.ncell = st->dm.ncell;
+  a.nfoot = st->nfoot;
+  a.foot_off = st->foot_off;
+  a.tmpl = st->tmpl32;
+  a.kind = st->cell_kind;
+  a.inv_kappa = st->inv_kappa;
+  a.n_irr = st->n_irr;
+  a.irr_cell = st->irr_cell;
+  a.irr_row = st->irr_row;
+  a.n_rows = st->n_rows;
+  a.rows = st->rows32;
+  a.phi = nullptr;
+  a.y = nullptr;
+  a.kappa_weighted = kw;
+  return a;
+}
+template <>
+ApplyArgs<double> apply_args<double>(const eb_stencils* st, int kw) {
+  ApplyArgs<double> a;
+  a.ncell = st->dm.ncell;
+  a.nfoot = st->nfoot;
+  a.foot_off = st->foot_off;
+  a.tmpl = st->tmpl64;
+  a.kind = st->cell_kind;
+  a.inv_kappa = st->inv_kappa;
+  a.n_irr = st->n_irr;
+  a.irr_cell = st->irr_cell;
+  a.irr_row = st->irr_row;
+  a.n_rows = st->n_rows;
+  a.rows = st->rows64;
+  a.phi = nullptr;
+  a.y = nullptr;
+  a.kappa_weighted = kw;
+  return a;
+}
+
+}  // namespace eb
+
+extern "C" {
+
+eb_status eb_apply(const eb_stencils* st, const void* phi, void* y, int32_t dtype, int32_t kappa_weighted,
+                   eb_stream_t stream) {
+  if (!st || !phi || !y) { set_error("null argument"); return EB_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == EB_F32) {
+    ApplyArgs<float> a = apply_args<float>(st, kappa_weighted);
+    a.phi = (const float*)phi;
+    a.y = (float*)y;
+    EB_CUDA(launch_apply<float>(a, s));
+  } else if (dtype == EB_F64) {
+    ApplyArgs<double> a = apply_args<double>(st, kappa_weighted);
+    a.phi = (const double*)phi;
+    a.y = (double*)y;
+    EB_CUDA(launch_apply<double>(a, s));
+  } else {
+    set_error("dtype must be EB_F32 or EB_F64");
+    return EB_ERR_INVALID;
+  }
+  return EB_OK;
+}
+
+eb_status eb_bc_rhs(const eb_stencils* st, const double* g_eb, const double* g_wall, double* Bg,
+                    int32_t kappa_weighted, eb_stream_t stream) {
+  if (!st || !Bg) { set_error("null argument"); return EB_ERR_INVALID; }
+  if ((st->dm.n_cut > 0 && !g_eb) || (st->n_wall > 0 && !g_wall)) { set_error("missing boundary data"); return EB_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  EB_CUDA(vec_fill64(st->dm.ncell, Bg, 0.0, s));
+  EB_CUDA(launch_bg(st->n_irr, st->irr_cell, st->b_ptr, st->b_col, st->b_val, st->dm.n_grid_faces, st->b_wpos, g_eb,
+                    g_wall, st->inv_kappa, kappa_weighted, Bg, s));
+  return EB_OK;
+}
+
+eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, eb_stream_t stream) {
+  if (!st || !err || !out_host) { set_error("null argument"); return EB_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d;
+  EB_CUDA(cudaMallocAsync((void**)&d, 4 * sizeof(double), s));
+  EB_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(double), s));
+  EB_CUDA(launch_norms(st->dm.ncell, st->flag, st->kappa, err, d, s));
+  double h[4];
+  EB_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaFreeAsync(d, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  double sw = h[2] > 0 ? h[2] : 1.0;
+  out_host[0] = h[3];
+  out_host[1] = h[0] / sw;
+  out_host[2] = sqrt(h[1] / sw);
+  return EB_OK;
+}
+
+eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
+                   const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream) {
+  if (!st || !rho || !phi) { set_error("null argument"); return EB_ERR_INVALID; }
+  eb_solve_opts o = {1, 1e-5, 20000, 30, 200000, 1};
+  if (opts) o = *opts;
+  eb_solve_info loc;
+  memset(&loc, 0, sizeof(loc));
+  eb_solve_info* inf = info ? info : &loc;
+  memset(inf, 0, sizeof(*inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = st->dm.ncell;
+  Tmp tmp;
+  double *bg, *rhs, *y64, *r64, *dscr;
+  EB_TRY(tmp.get(&bg, n));
+  EB_TRY(tmp.get(&rhs, n));
+  EB_TRY(tmp.get(&y64, n));
+  EB_TRY(tmp.get(&r64, n));
+  EB_TRY(tmp.get(&dscr, 4));
+  EB_TRY(eb_bc_rhs(st, g_eb, g_wall, bg, 1, stream));
+  EB_CUDA(compute_rhs(n, st->flag, st->kappa, rho, bg, rhs, s));
+  double bnorm = 0.0;
+  EB_CUDA(norm2_64(n, rhs, dscr, &bnorm, s));
+  if (bnorm == 0.0) bnorm = 1.0;
+  ApplyArgs<double> A64 = apply_args<double>(st, 1);
+  eb_status ret = EB_OK;
+  if (o.mixed) {
+    float *w32, *b32, *x32;
+    EB_TRY(tmp.get(&w32, 8 * n));
+    EB_TRY(tmp.get(&b32, n));
+    EB_TRY(tmp.get(&x32, n));
+    ApplyArgs<float> A32 = apply_args<float>(st, 1);
+    int total = 0;
+    for (int sweep = 0;; ++sweep) {
+      A64.phi = phi;
+      A64.y = y64;
+      EB_CUDA(launch_apply<double>(A64, s));
+      EB_CUDA(resid64(n, rhs, y64, r64, s));
+      double rn = 0.0;
+      EB_CUDA(norm2_64(n, r64, dscr, &rn, s));
+      inf->rel_residual = rn / bnorm;
+      if (inf->n_history < 64) inf->history[inf->n_history++] = inf->rel_residual;
+      if (inf->rel_residual <= tol) break;
+      if (sweep >= o.max_outer || total >= o.max_iters) { ret = EB_ERR_NOT_CONVERGED; break; }
+      EB_CUDA(to32(n, r64, 1.0 / rn, b32, s));
+      EB_CUDA(fill32(n, x32, 0.0f, s));
+      int it = 0;
+      double rr = 0.0;
+      int cap = std::min(o.max_inner, o.max_iters - total);
+      EB_CUDA(bicgstab<float>(A32, b32, x32, st->dinv32, w32, n, o.inner_tol, cap, dscr, &it, &rr, s));
+      total += it;
+      EB_CUDA(add32(n, phi, rn, x32, s));
+      inf->sweeps = sweep + 1;
+    }
+    inf->iterations = total;
+  } else {
+    double* w64;
+    EB_TRY(tmp.get(&w64, 8 * n));
+    int it = 0;
+    double rr = 0.0;
+    EB_CUDA(bicgstab<double>(A64, rhs, phi, st->dinv64, w64, n, tol, o.max_iters, dscr, &it, &rr, s));
+    inf->iterations = it;
+    A64.phi = phi;
+    A64.y = y64;
+    EB_CUDA(launch_apply<double>(A64, s));
+    EB_CUDA(resid64(n, rhs, y64, r64, s));
+    double rn = 0.0;
+    EB_CUDA(norm2_64(n, r64, dscr, &rn, s));
+    inf->rel_residual = rn / bnorm;
+    inf->history[0] = inf->rel_residual;
+    inf->n_history = 1;
+    if (inf->rel_residual > tol * 10) ret = EB_ERR_NOT_CONVERGED;
+  }
+  EB_CUDA(cudaStreamSynchronize(s));
+  if (ret != EB_OK) set_error("solve did not reach the requested tolerance");
+  return ret;
+}
+
+eb_status eb_wall_faces(const eb_stencils* st, int64_t* ids_host, int64_t cap, int64_t* n) {
+  if (!st || !n) { set_error("null argument"); return EB_ERR_INVALID; }
+  *n = st->n_wall;
+  for (int64_t i = 0; i < cap && i < st->n_wall && ids_host; ++i) ids_host[i] = st->wall_ids_host[i];
+  return EB_OK;
+}
+
+eb_status eb_stencil_query(const eb_stencils* st, int64_t face, int32_t* n, int64_t* cols_host, double* coef_host,
+                           int32_t cap, eb_stream_t stream) {
+  if (!st || !n) { set_error("null argument"); return EB_ERR_INVALID; }
+  const Dims& dm = st->dm;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t slot = -1;
+  int base[3] = {0, 0, 0};
+  if (face < 0 || face >= dm.n_grid_faces + dm.n_cut) { set_error("face id out of range"); return EB_ERR_INVALID; }
+  if (face >= dm.n_grid_faces) {
+    int64_t cut = face - dm.n_grid_faces;
+    EB_CUDA(cudaMemcpyAsync(&slot, st->eb_slot + cut, 4, cudaMemcpyDeviceToHost, s));
+    int32_t c = 0;
+    EB_CUDA(cudaMemcpyAsync(&c, st->cut_cell + cut, 4, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    base[0] = c % dm.n[0];
+    base[1] = (c / dm.n[0]) % dm.n[1];
+    base[2] = c / (dm.n[0] * dm.n[1]);
+  } else {
+    int d = 0;
+    for (int k = 0; k < dm.dim; ++k)
+      if (face >= dm.face_base[k]) d = k;
+    int64_t f = face - dm.face_base[d];
+    EB_CUDA(cudaMemcpyAsync(&slot, st->face_slot[d] + f, 4, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    int64_t m0 = dm.n[0] + (d == 0), m1 = dm.n[1] + (d == 1);
+    base[0] = (int)(f % m0);
+    base[1] = (int)((f / m0) % m1);
+    base[2] = (int)(f / (m0 * m1));
+  }
+  if (slot < 0) { *n = 0; return EB_OK; }
+  int64_t rp[2];
+  EB_CUDA(cudaMemcpyAsync(rp, st->row_ptr + slot, 16, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  int32_t cnt = (int32_t)(rp[1] - rp[0]);
+  *n = cnt;
+  if (!cols_host) return EB_OK;
+  if (cap < cnt) { set_error("capacity too small"); return EB_ERR_INVALID; }
+  std::vector<uint32_t> desc(cnt);
+  EB_CUDA(cudaMemcpyAsync(desc.data(), st->row_desc + rp[0], cnt * 4, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(coef_host, st->row_val + rp[0], cnt * 8, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  for (int32_t i = 0; i < cnt; ++i) {
+    uint32_t ds = desc[i];
+    int c[3];
+    for (int d = 0; d < 3; ++d) c[d] = base[d] + (d < dm.dim ? rd_off(ds, d) : 0);
+    int64_t cid = (int64_t)c[0] + (int64_t)dm.n[0] * ((int64_t)c[1] + (int64_t)dm.n[1] * c[2]);
+    int kind = rd_kind(ds);
+    if (kind == 0) cols_host[i] = cid;
+    else if (kind == 1) {
+      int32_t cut = -1;
+      EB_CUDA(cudaMemcpy(&cut, st->cut_of_cell + cid, 4, cudaMemcpyDeviceToHost));
+      cols_host[i] = -(1 + dm.n_grid_faces + cut);
+    } else {
+      int wd = rd_wdir(ds);
+      if (rd_wside(ds)) c[wd] += 1;
+      int64_t m0 = dm.n[0] + (wd == 0), m1 = dm.n[1] + (wd == 1);
+      cols_host[i] = -(1 + dm.face_base[wd] + c[0] + m0 * ((int64_t)c[1] + m1 * c[2]));
+    }
+  }
+  return EB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Argument structures of the build kernels (eb_build.cu), shared with the host code.
+#pragma once
+#include <stdint.h>
+
+#include "eb_internal.cuh"
+#include "eb_tables.cuh"
+
+namespace eb {
+
+constexpr int RW = 6;  // 64-bit words of a (2R+1)^3 <= 343-bit mask
+
+struct Mask {
+  uint64_t w[RW];
+};
+
+struct GatherArgs {
+  Dims dm;
+  const uint8_t* flag;
+  const uint8_t* ff[3];
+  const int32_t* reach_idx;  // [ncell] index into masks or -1 (clean: whole box / ball)
+  const Mask* masks;
+  const int32_t* cut_of_cell;
+  const int64_t* slot_face;
+  const int64_t* row_ptr;    // null in the counting pass
+  uint32_t* row_desc;
+  int64_t* count;            // [n_slots] counting pass output
+  int32_t* too_many;         // capacity flag
+};
+
+constexpr int LS_WARPS = 4;
+constexpr int RPL = 3;        // rows per lane per chunk
+constexpr int CH = 32 * RPL;  // rows per chunk
+constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
+
+struct LsWarpSmem {
+  double R[MAXK * MAXK];
+  double C[CH * KST];
+  double P[32 * (MAXK + 1)];
+  double vec[4 * MAXK];  // F, y, z, tau/work
+};
+
+struct LsArgs {
+  Dims dm;
+  const Tables* T;
+  const uint8_t* flag;
+  const int32_t* cut_of_cell;
+  const int32_t* cut_cell;
+  const double* vol_mom;
+  const double* eb_mom;
+  const double* eb_nmom;
+  const uint8_t* eb_bc;
+  const int32_t* cutface_of[3];
+  const double* face_mom[3];
+  const int64_t* slot_face;
+  const int64_t* row_ptr;
+  const uint32_t* row_desc;
+  double* row_val;
+  int64_t n_slots;
+  int32_t* next;       // work counter
+  int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row
+  double* scratch;     // per warp: MAXROWS * (K + 2) doubles
+};
+
+struct AsmArgs {
+  Dims dm;
+  const uint8_t* flag;
+  const int32_t* cut_of_cell;
+  const int32_t* face_slot[3];
+  const int32_t* eb_slot;
+  const int64_t* slot_face;
+  const int64_t* row_ptr;
+  const uint32_t* row_desc;
+  const double* row_val;
+  const uint8_t* ff[3];
+  int nfoot;
+  const int16_t* foot_lut;  // [(2R+3)^3] footprint index of an offset, -1 outside
+  int64_t n_rows;
+  double* rows64;
+  float* rows32;
+  double inv_h2;
+};
+
+__global__ void k_mark(Dims dm, const uint8_t* flag, uint8_t* mark);
+__global__ void k_dilate(Dims dm, int axis, int R, const uint8_t* in, uint8_t* out);
+__global__ void k_classify_faces(Dims dm, int d, const uint8_t* fflag, const uint8_t* dil, int32_t* state,
+                                 int64_t* class_rep, int32_t* is_unique);
+__global__ void k_face_slots(Dims dm, int d, const int32_t* state, const int64_t* upos, int64_t ubase,
+                             const int32_t* class_slot, int32_t* slot, int64_t* slot_face);
+__global__ void k_reach(Dims dm, const int32_t* cells, int64_t ncells, const uint8_t* flag, const uint8_t* ff0,
+                        const uint8_t* ff1, const uint8_t* ff2, Mask* out);
+__global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* cut_cell);
+__global__ void k_lsq(LsArgs a);
+__global__ void k_assemble_rows(AsmArgs a, const int32_t* rep_cell, int64_t nrep, int64_t row0, int32_t* err);
+__global__ void k_assemble_b(AsmArgs a, const int32_t* cells, int64_t ncells, int64_t* cnt, const int64_t* bptr,
+                             int64_t* bcol, double* bval, const int32_t* unused);
+
+}  // namespace eb

@@ -1,0 +1,297 @@
+// Linear solve of the kappa-weighted system kappa L phi = kappa (rho - B g)
+// (the paper uses PETSc GMRES + algebraic multigrid, Sec. 3.2; here a
+// Jacobi-preconditioned BiCGStab written for the GPU):
+//   mixed: FP32 BiCGStab inner solves on the FP32 operator copy, wrapped in
+//          FP64 iterative refinement whose residual uses the FP64 operator;
+//   plain: FP64 BiCGStab throughout.
+// Dot products accumulate in FP64 whatever the vector precision.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "eb_apply.cuh"
+#include "eb_internal.cuh"
+#include "eb_solve.cuh"
+
+namespace eb {
+
+constexpr int VB = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// out[k] += sum_i a_k[i] * b_k[i] for up to 3 pairs (FP64 accumulation)
+template <typename T>
+__global__ void k_dots(int64_t n, const T* a0, const T* b0, const T* a1, const T* b1, const T* a2, const T* b2,
+                       double* out) {
+  __shared__ double sh[32];
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s0 += (double)a0[i] * (double)b0[i];
+    if (a1) s1 += (double)a1[i] * (double)b1[i];
+    if (a2) s2 += (double)a2[i] * (double)b2[i];
+  }
+  s0 = block_sum(s0, sh);
+  __syncthreads();
+  if (a1) { s1 = block_sum(s1, sh); __syncthreads(); }
+  if (a2) { s2 = block_sum(s2, sh); __syncthreads(); }
+  if (threadIdx.x == 0) {
+    atomicAdd(out, s0);
+    if (a1) atomicAdd(out + 1, s1);
+    if (a2) atomicAdd(out + 2, s2);
+  }
+}
+
+// p = r + beta (p - omega v); phat = dinv p
+template <typename T>
+__global__ void k_bicg_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* dinv, double beta, double omega) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T pi = r[i] + (T)beta * (p[i] - (T)omega * v[i]);
+    p[i] = pi;
+    ph[i] = dinv[i] * pi;
+  }
+}
+
+// s = r - alpha v; shat = dinv s
+template <typename T>
+__global__ void k_bicg_s(int64_t n, const T* r, const T* v, T* s, T* sh, const T* dinv, double alpha) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T si = r[i] - (T)alpha * v[i];
+    s[i] = si;
+    sh[i] = dinv[i] * si;
+  }
+}
+
+// x += alpha phat + omega shat; r = s - omega t
+template <typename T>
+__global__ void k_bicg_x(int64_t n, T* x, const T* ph, const T* sh, T* r, const T* s, const T* t, double alpha,
+                         double omega) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (T)alpha * ph[i] + (T)omega * sh[i];
+    r[i] = s[i] - (T)omega * t[i];
+  }
+}
+
+// r = b - y (FP64), on volumes only
+__global__ void k_resid64(int64_t n, const double* b, const double* y, double* r) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+
+// r32 = scale * r64
+__global__ void k_to32(int64_t n, const double* a, double scale, float* o) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (float)(scale * a[i]);
+}
+
+// x64 += scale * d32
+__global__ void k_add32(int64_t n, double* x, double scale, const float* d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += scale * (double)d[i];
+}
+
+template <typename T>
+__global__ void k_fill(int64_t n, T* x, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+template <typename T>
+__global__ void k_copy(int64_t n, const T* a, T* b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+// rhs = kappa rho - Bg_kw on volumes, 0 on covered cells
+__global__ void k_rhs(int64_t n, const uint8_t* flag, const double* kappa, const double* rho, const double* bg,
+                      double* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = flag[i] ? kappa[i] * rho[i] - bg[i] : 0.0;
+}
+
+// norms of Sec. 3.3: [sum |e| kappa, sum e^2 kappa, sum kappa, max |e|] over volumes
+__global__ void k_norms(int64_t n, const uint8_t* flag, const double* kappa, const double* e, double* out) {
+  __shared__ double sh[32];
+  double a = 0, b = 0, c = 0, m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    double v = fabs(e[i]), k = kappa[i];
+    a += v * k;
+    b += v * v * k;
+    c += k;
+    m = fmax(m, v);
+  }
+  a = block_sum(a, sh); __syncthreads();
+  b = block_sum(b, sh); __syncthreads();
+  c = block_sum(c, sh); __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double mx[32];
+  if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, mx[w]);
+    atomicAdd(out, a);
+    atomicAdd(out + 1, b);
+    atomicAdd(out + 2, c);
+    atomicMax((unsigned long long*)(out + 3), (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// B g (kappa-weighted B, CSR over irregular cells)
+__global__ void k_bg(int64_t n_irr, const int32_t* irr_cell, const int64_t* bptr, const int64_t* bcol,
+                     const double* bval, int64_t n_grid_faces, const int64_t* wall_pos, const double* g_eb,
+                     const double* g_wall, const double* inv_kappa, int kw, double* out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_irr) return;
+  double acc = 0.0;
+  for (int64_t k = bptr[t]; k < bptr[t + 1]; ++k) {
+    int64_t col = bcol[k];
+    double g = col >= n_grid_faces ? g_eb[col - n_grid_faces] : g_wall[wall_pos[k]];
+    acc += bval[k] * g;
+  }
+  int64_t c = irr_cell[t];
+  out[c] = kw ? acc : acc * inv_kappa[c];
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + VB - 1) / VB;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ----------------------------------------------------------------- host drivers
+
+cudaError_t vec_fill64(int64_t n, double* x, double v, cudaStream_t s) {
+  k_fill<double><<<grid_for(n), VB, 0, s>>>(n, x, v);
+  return cudaGetLastError();
+}
+
+cudaError_t compute_rhs(int64_t n, const uint8_t* flag, const double* kappa, const double* rho, const double* bg,
+                        double* out, cudaStream_t s) {
+  k_rhs<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, rho, bg, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bg(int64_t n_irr, const int32_t* irr_cell, const int64_t* bptr, const int64_t* bcol,
+                      const double* bval, int64_t n_grid_faces, const int64_t* wall_pos, const double* g_eb,
+                      const double* g_wall, const double* inv_kappa, int kw, double* out, cudaStream_t s) {
+  if (n_irr == 0) return cudaSuccess;
+  k_bg<<<(unsigned)((n_irr + 255) / 256), 256, 0, s>>>(n_irr, irr_cell, bptr, bcol, bval, n_grid_faces, wall_pos,
+                                                       g_eb, g_wall, inv_kappa, kw, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norms(int64_t n, const uint8_t* flag, const double* kappa, const double* e, double* out,
+                         cudaStream_t s) {
+  k_norms<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, e, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dots(int64_t n, const T* a0, const T* b0, const T* a1, const T* b1, const T* a2, const T* b2,
+                        double* dev, double* host, int cnt, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(dev, 0, 3 * sizeof(double), s);
+  if (e) return e;
+  k_dots<T><<<grid_for(n), VB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dev);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
+  return cudaStreamSynchronize(s);
+}
+
+// Jacobi-preconditioned BiCGStab on A x = b (x in/out).  Returns iterations
+// used; *relres = ||b - A x|| / ||b|| as tracked by the recurrence.
+template <typename T>
+cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T* work, int64_t n, double tol,
+                     int maxit, double* dscr, int* iters, double* relres, cudaStream_t s) {
+  T* r = work;
+  T* rh = work + n;
+  T* p = work + 2 * n;
+  T* v = work + 3 * n;
+  T* ph = work + 4 * n;
+  T* sv = work + 5 * n;
+  T* shv = work + 6 * n;
+  T* t = work + 7 * n;
+  ApplyArgs<T> A = A0;
+  cudaError_t e;
+  double h[3];
+  // r = b - A x
+  A.phi = x; A.y = r;
+  if ((e = launch_apply<T>(A, s))) return e;
+  k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, b, r, r, rh, dinv, 1.0);  // r = b - Ax (rh scratch)
+  k_copy<T><<<grid_for(n), VB, 0, s>>>(n, r, rh);
+  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, p, (T)0);
+  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, v, (T)0);
+  if ((e = dots<T>(n, b, b, r, r, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
+  double bn = sqrt(h[0]);
+  if (bn == 0.0) bn = 1.0;
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  double rn = sqrt(h[1]);
+  *relres = rn / bn;
+  int it = 0;
+  if (*relres <= tol) { *iters = 0; return cudaSuccess; }
+  for (it = 1; it <= maxit; ++it) {
+    if ((e = dots<T>(n, rh, r, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
+      return e;
+    double rho = h[0];
+    if (rho == 0.0) break;
+    double beta = (rho / rho_old) * (alpha / omega);
+    k_bicg_p<T><<<grid_for(n), VB, 0, s>>>(n, r, v, p, ph, dinv, it == 1 ? 0.0 : beta, omega);
+    A.phi = ph; A.y = v;
+    if ((e = launch_apply<T>(A, s))) return e;
+    if ((e = dots<T>(n, rh, v, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
+      return e;
+    if (h[0] == 0.0) break;
+    alpha = rho / h[0];
+    k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, r, v, sv, shv, dinv, alpha);
+    A.phi = shv; A.y = t;
+    if ((e = launch_apply<T>(A, s))) return e;
+    if ((e = dots<T>(n, t, sv, t, t, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
+    omega = h[1] > 0 ? h[0] / h[1] : 0.0;
+    k_bicg_x<T><<<grid_for(n), VB, 0, s>>>(n, x, ph, shv, r, sv, t, alpha, omega);
+    rho_old = rho;
+    if ((e = dots<T>(n, r, r, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
+      return e;
+    *relres = sqrt(h[0]) / bn;
+    if (*relres <= tol || omega == 0.0) break;
+  }
+  *iters = it > maxit ? maxit : it;
+  return cudaGetLastError();
+}
+
+template cudaError_t bicgstab<float>(const ApplyArgs<float>&, const float*, float*, const float*, float*, int64_t,
+                                     double, int, double*, int*, double*, cudaStream_t);
+template cudaError_t bicgstab<double>(const ApplyArgs<double>&, const double*, double*, const double*, double*,
+                                      int64_t, double, int, double*, int*, double*, cudaStream_t);
+
+cudaError_t resid64(int64_t n, const double* b, const double* y, double* r, cudaStream_t s) {
+  k_resid64<<<grid_for(n), VB, 0, s>>>(n, b, y, r);
+  return cudaGetLastError();
+}
+cudaError_t to32(int64_t n, const double* a, double scale, float* o, cudaStream_t s) {
+  k_to32<<<grid_for(n), VB, 0, s>>>(n, a, scale, o);
+  return cudaGetLastError();
+}
+cudaError_t add32(int64_t n, double* x, double scale, const float* d, cudaStream_t s) {
+  k_add32<<<grid_for(n), VB, 0, s>>>(n, x, scale, d);
+  return cudaGetLastError();
+}
+cudaError_t fill32(int64_t n, float* x, float v, cudaStream_t s) {
+  k_fill<float><<<grid_for(n), VB, 0, s>>>(n, x, v);
+  return cudaGetLastError();
+}
+cudaError_t norm2_64(int64_t n, const double* a, double* dscr, double* out, cudaStream_t s) {
+  double h[3];
+  cudaError_t e = dots<double>(n, a, a, nullptr, nullptr, nullptr, nullptr, dscr, h, 1, s);
+  *out = sqrt(h[0]);
+  return e;
+}
+
+}  // namespace eb

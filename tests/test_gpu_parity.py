@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: stencil coefficients 1e-10 relative to the face's largest coefficient; FP64 kappa-weighted
+apply 1e-12 normwise relative; refined solutions 1e-9 relative to max|phi|; FP32 apply 1e-5 normwise
+(single precision storage of coefficients and of phi).  The unweighted operator and B divide rows by
+kappa (down to ~1e-4), which magnifies the rounding of their sums; they are held to the rounding bound
+of a length-n dot product, |y - y_ref|_i <= 4 n eps (|L| |phi|)_i with n the footprint size.
+"""
+EPS = 2.220446049250313e-16
+import numpy as np
+import pytest
+
+import eb_inputs as E
+from gpu_helpers import build_gpu, compare_stencils, sample_faces, split_boundary, to_dev
+from oracle.eb_oracle import Oracle, Params, run_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def circle32():
+    g = E.circle_config(32, center=(0.51, 0.49), r=0.3)
+    man = E.Manufactured(g, E.sin_product("config2d"))
+    ref = run_problem(g, man, Params(order=4))
+    return g, man, ref
+
+
+def test_library_loaded():
+    import paper_1411_4283_gb300 as P
+    assert P.load().eb_abi_version() == 1
+
+
+@pytest.mark.parametrize("Q", [4, 2])
+def test_all_stencils_2d(Q):
+    g = E.circle_config(32, center=(0.51, 0.49), r=0.3)
+    o = Oracle(g, Params(order=Q))
+    st, _ = build_gpu(g, order=Q)
+    compare_stencils(st, o, o.flux_faces())
+
+
+def test_wall_face_order(circle32):
+    import paper_1411_4283_gb300 as P
+    g, man, ref = circle32
+    st, _ = build_gpu(g)
+    _, _, walls = split_boundary(ref["oracle"], ref["G"])
+    assert np.array_equal(P.eb_wall_faces(st), np.array(walls))
+
+
+@pytest.mark.parametrize("kw", [False, True])
+def test_apply_fp64_2d(circle32, kw):
+    import torch
+    import paper_1411_4283_gb300 as P
+    g, man, ref = circle32
+    st, _ = build_gpu(g)
+    phi = E.seeded_field(11, g.ncell) * (g.flag > 0)
+    y = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
+    P.eb_apply(st, to_dev(phi), y, kappa_weighted=kw)
+    yo = ref["L"] @ phi
+    if kw:
+        yo = g.kappa * yo
+    yg = y.cpu().numpy()
+    if kw:
+        assert np.linalg.norm(yg - yo) <= 1e-12 * np.linalg.norm(yo)
+    else:
+        bound = 4 * 77 * EPS * (abs(ref["L"]) @ np.abs(phi))
+        assert np.all(np.abs(yg - yo) <= bound + 1e-300)
+    assert np.all(yg[g.flag == 0] == 0)
+
+
+def test_apply_fp32_2d(circle32):
+    import torch
+    import paper_1411_4283_gb300 as P
+    g, man, ref = circle32
+    st, _ = build_gpu(g)
+    phi = E.seeded_field(12, g.ncell) * (g.flag > 0)
+    y = torch.empty(g.ncell, dtype=torch.float32, device="cuda")
+    P.eb_apply(st, to_dev(phi, torch.float32), y, kappa_weighted=True)
+    yo = g.kappa * (ref["L"] @ phi)
+    assert np.linalg.norm(y.cpu().numpy() - yo) <= 1e-5 * np.linalg.norm(yo)
+
+
+def test_bc_rhs_2d(circle32):
+    import torch
+    import paper_1411_4283_gb300 as P
+    g, man, ref = circle32
+    st, _ = build_gpu(g)
+    gw, ge, _ = split_boundary(ref["oracle"], ref["G"])
+    Bg = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
+    P.eb_bc_rhs(st, to_dev(ge), to_dev(gw), Bg, kappa_weighted=False)
+    bo = ref["B"] @ ref["G"]
+    bound = 4 * 64 * EPS * (abs(ref["B"]) @ np.abs(ref["G"]))
+    assert np.all(np.abs(Bg.cpu().numpy() - bo) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_solve_2d(circle32, mixed):
+    import torch
+    import paper_1411_4283_gb300 as P
+    g, man, ref = circle32
+    st, _ = build_gpu(g)
+    gw, ge, _ = split_boundary(ref["oracle"], ref["G"])
+    x = torch.zeros(g.ncell, dtype=torch.float64, device="cuda")
+    info = P.eb_solve(st, to_dev(ref["rho"]), to_dev(ge), to_dev(gw), x, tol=1e-12, mixed=mixed)
+    xo = ref["phi"]
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-9 * np.abs(xo).max(), info
+    err = x - to_dev(ref["Phi"])
+    nrm = P.eb_norms(st, err * to_dev((g.flag > 0).astype(float)))
+    assert nrm["linf"] == pytest.approx(ref["sol"]["linf"], rel=1e-6)
+    assert nrm["l1"] == pytest.approx(ref["sol"]["l1"], rel=1e-6)
+
+
+def test_no_embedded_boundary_box():
+    """Degenerate geometry: no body at all -- only interior template faces and wall classes."""
+    g = E.Geometry(2, 24, np.zeros((0, 3)), np.zeros(0), False, 4, name="box")
+    o = Oracle(g, Params(order=4))
+    st, _ = build_gpu(g)
+    assert st.info["n_unique_faces"] == 0
+    compare_stencils(st, o, o.flux_faces()[::3])
+
+
+def test_sampled_stencils_3d():
+    g = E.sphere_box_config(20)
+    o = Oracle(g, Params(order=4))
+    st, _ = build_gpu(g)
+    compare_stencils(st, o, sample_faces(o, 60, seed=2))
+
+
+def test_apply_fp64_3d_sampled_rows():
+    """Operator rows at sampled cells: (L phi)_v assembled by the oracle from the cell's own face
+    stencils, against the GPU apply of the whole field."""
+    import torch
+    import paper_1411_4283_gb300 as P
+    g = E.sphere_box_config(20)
+    o = Oracle(g, Params(order=4))
+    st, _ = build_gpu(g)
+    phi = E.seeded_field(21, g.ncell) * (g.flag > 0)
+    y = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
+    P.eb_apply(st, to_dev(phi), y, kappa_weighted=True)
+    yg = y.cpu().numpy()
+    rng = np.random.default_rng(4)
+    cells = list(rng.choice(g.cut_cells, 6, replace=False)) + list(rng.choice(np.nonzero(g.flag == 1)[0], 6))
+    for c in cells:
+        c = int(c)
+        acc = 0.0
+        for fid, sg in o.cell_flux_faces(c):
+            cols, s = o.stencil(fid)
+            vm = cols >= 0
+            acc += sg * float(s[vm] @ phi[cols[vm]])
+        acc /= g.h ** 2
+        assert abs(yg[c] - acc) <= 1e-12 * max(abs(acc), np.abs(yg).max() * 1e-3), (c, yg[c], acc)
