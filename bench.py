@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the cut-cell Poisson hot path on one GB300 (per rank).
+
+Workload: the unit cube minus a sphere of radius 0.35 whose centre is
+0.5 + delta, delta_i ~ U[-h/2, h/2) (SplitMix64, seed 2), N^3 cells (default
+256^3), fourth-order weighted-LS stencils (Q=4, box neighbourhoods, R_n=3),
+Dirichlet data of phi = sin(2 pi (x-x0)) sin(2 pi (y-y0)) sin(2 pi (z-z0)).
+
+One step = the whole hot path with the moment tables resident in HBM:
+face classification, neighbourhood gather, FP64 weighted least squares,
+operator assembly, the mixed-precision refined solve (FP32 BiCGStab + FP64
+residual refinement) to a relative residual `--tol`, and the error norms.
+
+Reported: cut-face LS stencils per second of the whole step (the faces whose
+LS system differs from the interior template), plus the build-only rate, the
+FP32 apply bandwidth (algorithmic bytes), the solve time and its error.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cut-face LS stencils/s; EB Laplacian apply GB/s (% HBM); solve s at fixed error"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--order", type=int, default=4)
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--inner-tol", type=float, default=1e-4)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU solve once")
+    p.add_argument("--out", default=None)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP64 FMA issue on this part: 2 DFMA per clock per SM (0.5 per SM sub-partition), 2 flops each."""
+    return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        dev = os.environ.get("LOCAL_RANK", "0")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(int(dev) if dev.isdigit() else 0):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem(n, seed=2):
+    import eb_inputs as E
+    t0 = time.time()
+    g = E.sphere_box_config(n, seed=seed)
+    man = E.Manufactured(g, E.sin_product("paper3d"))
+    rho = man.lap_avg()
+    Phi = man.cell_avg()
+    g_eb = man.eb_phi()
+    g_wall = man.wall_phi_by_id()
+    return g, man, rho, Phi, g_eb, g_wall, time.time() - t0
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier_max(ws, val):
+    if ws <= 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(g, seconds, max_faces=400):
+    """Time the FP64 oracle (single process, single thread) on EB-affected faces of the workload."""
+    from oracle.eb_oracle import Oracle, Params
+    o = Oracle(g, Params(order=4))
+    faces = [o.eb_id(i) for i in range(0, len(g.cut_cells), max(1, len(g.cut_cells) // max_faces))]
+    t0 = time.time()
+    done = 0
+    for f in faces:
+        o.stencil(f)
+        done += 1
+        if time.time() - t0 > seconds:
+            break
+    dt = time.time() - t0
+    return done, dt
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import eb_inputs as E
+    g = E.sphere_box_config(args.n, seed=2)
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(g, 0.5, max_faces=5)
+    tot_f, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        f, t = oracle_sample(g, per_step)
+        tot_f += f
+        tot_t += t
+    v = tot_f / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cut-face LS stencils/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3D box minus sphere r=0.35, {args.n}^3, Q=4, EB-face LS stencils (oracle)",
+                       "order": 4, "n": args.n},
+            "cpu_baseline": {"value": v, "unit": "cut-face LS stencils/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{tot_f} EB-face LS systems of the {args.n}^3 workload"},
+            "e2e": {"value": v, "unit": "cut-face LS stencils/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_1411_4283_gb300 as P
+    ws, rank, local = dist_setup(args)
+    hbm_peak, peak_kind, sm_max = peaks()
+    g, man, rho_h, Phi_h, geb_h, gw_h, t_geom = make_problem(args.n)
+    dev = torch.device("cuda")
+    dg = P.DeviceGeometry.from_geometry(g)
+    rho = torch.tensor(rho_h, device=dev)
+    Phi = torch.tensor(Phi_h, device=dev)
+    g_eb = torch.tensor(geb_h, device=dev)
+    g_wall = torch.tensor(gw_h, device=dev)
+    volmask = torch.tensor((g.flag > 0).astype(np.float64), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(time_applies=False):
+        st = P.eb_build_stencils(dg, order=args.order)
+        phi = torch.zeros(g.ncell, dtype=torch.float64, device=dev)
+        info = P.eb_solve(st, rho, g_eb, g_wall, phi, tol=args.tol, mixed=True, inner_tol=args.inner_tol,
+                          time_applies=time_applies)
+        err = (phi - Phi) * volmask
+        nrm = P.eb_norms(st, err)
+        return st, info, nrm
+
+    for _ in range(args.warmup):
+        st, info, nrm = step()
+        del st
+    torch.cuda.synchronize()
+    # timed region
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = P.eb_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        st, info, nrm = step(time_applies=True)
+        infos.append((st.info, info, nrm))
+        del st
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = P.eb_kernel_launches() - l0
+    ms_total = barrier_max(ws, e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    bi = infos[-1][0]
+    # faces whose LS system differs from the interior template: all but the template-class faces
+    n_tmpl = template_faces(g, args.order)
+    n_ls = int(bi["n_flux_faces"] - n_tmpl)
+    value = n_ls * ws / (ms_step / 1e3)
+    build_ms = np.mean([i[0]["ms_classify"] + i[0]["ms_gather"] + i[0]["ms_lsq"] + i[0]["ms_assemble"] for i in infos])
+    lsq_ms = np.mean([i[0]["ms_lsq"] for i in infos])
+    sinfo = infos[-1][1]
+    apply_ms = np.mean([i[1]["apply_ms"] / max(1, i[1]["n_applies"]) for i in infos])
+    nfoot = 637 if args.order == 4 else 275
+    alg_bytes = 2 * g.ncell * 4 + (bi["n_irregular_rows"] + bi["n_row_classes"]) * nfoot * 4
+    apply_gbs = alg_bytes / (apply_ms / 1e3) / 1e9
+    fp64_pk = fp64_peak_tflops(sm_max)
+    lsq_tflops = bi["lsq_flops"] / (lsq_ms / 1e3) / 1e12
+    apply_share = np.mean([i[1]["apply_ms"] for i in infos]) / ms_step
+    lsq_share = lsq_ms / ms_step
+    if lsq_share >= apply_share:
+        roof = {"kernel": "k_lsq (FP64 weighted least squares)", "bound": "alu", "achieved": lsq_tflops,
+                "peak": fp64_pk, "unit": "TFLOP/s", "frac": lsq_tflops / fp64_pk, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                "share_of_step": lsq_share}
+    else:
+        roof = {"kernel": "k_apply_template+k_apply_irregular (FP32)", "bound": "hbm", "achieved": apply_gbs,
+                "peak": hbm_peak, "unit": "GB/s", "frac": apply_gbs / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind, "share_of_step": apply_share}
+    line = {
+        "metric": METRIC, "value": value, "unit": "cut-face LS stencils/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (LS, refinement) + f32 (Krylov)", "data": "synthetic",
+        "config": {"workload": f"3D unit cube minus sphere r=0.35 (seeded centre), {args.n}^3 cells, Q={args.order}, "
+                               f"box neighbourhoods R_n=3, Dirichlet, refined solve to rel. residual {args.tol:g}",
+                   "n": args.n, "order": args.order, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (operator rows and stencil tables are GBs)",
+                   "geometry_seconds_host": round(t_geom, 1)},
+        "components": {"build_ms": build_ms, "lsq_ms": lsq_ms, "ls_build_stencils_per_s": n_ls / (build_ms / 1e3),
+                       "n_cut_face_systems": n_ls, "n_systems_solved": bi["n_unique_faces"] + bi["n_classes"],
+                       "lsq_tflops": lsq_tflops, "lsq_frac_fp64_peak": lsq_tflops / fp64_pk,
+                       "apply_fp32_ms": apply_ms, "apply_gbs": apply_gbs, "apply_frac_hbm": apply_gbs / hbm_peak,
+                       "apply_alg_bytes": alg_bytes, "solve_ms": ms_step - build_ms,
+                       "solve_iterations": sinfo["iterations"], "solve_sweeps": sinfo["sweeps"],
+                       "rel_residual": sinfo["rel_residual"], "error_linf": infos[-1][2]["linf"],
+                       "error_l1": infos[-1][2]["l1"], "error_l2": infos[-1][2]["l2"], "build_info": bi},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+    # FP64 comparison solve (outside the timed region)
+    if args.fp64_compare:
+        st = P.eb_build_stencils(dg, order=args.order)
+        phi = torch.zeros(g.ncell, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        info64 = P.eb_solve(st, rho, g_eb, g_wall, phi, tol=args.tol, mixed=False, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t64 = time.time() - t0
+        nrm64 = P.eb_norms(st, (phi - Phi) * volmask)
+        line["fp64_solve"] = {"seconds": t64, "iterations": info64["iterations"], "status": info64["status"],
+                              "error_linf": nrm64["linf"], "mixed_solve_seconds": (ms_step - build_ms) / 1e3}
+    # end-to-end through the public API from pinned host buffers
+    if not args.no_e2e:
+        line["e2e"] = e2e(P, g, rho_h, geb_h, gw_h, args, ws)
+    if rank == 0 and not args.no_cpu_baseline:
+        nf, dt = oracle_sample(g, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": nf / dt, "unit": "cut-face LS stencils/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{nf} EB-face LS systems of the {args.n}^3 workload, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+        if args.out:
+            json.dump(line, open(args.out, "w"), indent=1)
+
+
+def template_faces(g, order):
+    """Faces whose box neighbourhood (radius R_n) holds only full cells away from the walls."""
+    R = 3 if order == 4 else 2
+    D = g.dim
+    fl = g.flag.reshape(g.n[:D][::-1]) == 1
+    # clean cell: its box is inside the domain, full, and touches no wall
+    n = g.n[0]
+    inner = np.zeros_like(fl)
+    sl = tuple(slice(R + 1, n - R - 1) for _ in range(D))
+    inner[sl] = True
+    bad = ~fl | ~inner
+    from scipy.ndimage import maximum_filter
+    dil = maximum_filter(bad.astype(np.uint8), size=2 * R + 1, mode="constant", cval=1) > 0
+    clean = ~dil
+    cnt = 0
+    for ax in range(D):
+        a = np.take(clean, np.arange(0, n - 1), axis=ax)
+        b = np.take(clean, np.arange(1, n), axis=ax)
+        cnt += int(np.sum(a & b))
+    return cnt
+
+
+def e2e(P, g, rho_h, geb_h, gw_h, args, ws):
+    """Same step from pinned host buffers: H2D of the moment tables and data, build, solve, D2H of phi."""
+    import torch
+    host = {"flag": g.flag, "cut": g.cut_cells, "vol": g.vol_mom, "eb": g.eb_mom, "ebn": g.eb_nmom,
+            "rho": rho_h, "geb": geb_h, "gw": gw_h}
+    for d in range(g.dim):
+        host[f"ff{d}"] = g.face_flag[d]
+        host[f"cf{d}"] = g.cut_faces[d]
+        host[f"fm{d}"] = g.face_mom[d]
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    h2d = sum(t.numel() * t.element_size() for t in pinned.values())
+    out_h = torch.empty(g.ncell, dtype=torch.float64).pin_memory()
+    d2h = out_h.numel() * 8
+    steps = max(1, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for _ in range(steps):
+        dv = {k: t.to("cuda", non_blocking=True) for k, t in pinned.items()}
+        dg = P.DeviceGeometry(g.dim, g.n[:g.dim], g.h, g.qmax, dv["flag"], dv["cut"], dv["vol"], dv["eb"], dv["ebn"],
+                              [dv[f"ff{d}"] for d in range(g.dim)], [dv[f"cf{d}"] for d in range(g.dim)],
+                              [dv[f"fm{d}"] for d in range(g.dim)])
+        st = P.eb_build_stencils(dg, order=args.order)
+        phi = torch.zeros(g.ncell, dtype=torch.float64, device="cuda")
+        P.eb_solve(st, dv["rho"], dv["geb"], dv["gw"], phi, tol=args.tol, mixed=True, inner_tol=args.inner_tol)
+        out_h.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+        del st
+    dt = barrier_max(ws, time.time() - t0) / steps
+    n_tmpl = template_faces(g, args.order)
+    return {"value": (int(np.sum([(f > 0).sum() for f in g.face_flag])) + len(g.cut_cells) - n_tmpl) * ws / dt,
+            "unit": "cut-face LS stencils/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "seconds_per_step": dt}
+
+
+if __name__ == "__main__":
+    main()

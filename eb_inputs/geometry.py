@@ -267,6 +267,7 @@ class Geometry:
         self.kappa[self.cut_cells] = self.vol_mom[:, 0]
         # faces
         self.face_flag, self.cut_faces, self.face_mom, self.cut_face_body = [], [], [], []
+        self.closed_slivers = 0
         for d in range(D):
             nf = self.nface(d)
             ff = np.zeros(nf, dtype=np.int8)
@@ -285,7 +286,22 @@ class Geometry:
             ff[cf[tfull]] = 1
             ff[cf[tcov]] = 0
             k = ~(tfull | tcov)
-            self.face_flag.append(ff.astype(np.uint8))
+            # a cell whose volume fraction fell below KAPPA_EPS counts as covered: its faces close too
+            # (their area fraction is at most ~sqrt(KAPPA_EPS))
+            ff = ff.astype(np.uint8)
+            fl = self.flag.reshape(self.n[:D][::-1])
+            ffs = ff.reshape(self.face_shape(d)[::-1])
+            ax = D - 1 - d
+            cov = fl == 0
+            lo_c = np.concatenate([np.zeros_like(np.take(cov, [0], axis=ax)), cov], axis=ax)
+            hi_c = np.concatenate([cov, np.zeros_like(np.take(cov, [0], axis=ax))], axis=ax)
+            shut = (ffs > 0) & (lo_c | hi_c)
+            if shut.any():
+                self.closed_slivers += int(shut.sum())
+                ffs[shut] = 0
+                ff = ffs.reshape(-1)
+                k &= ff[cf] == 2
+            self.face_flag.append(ff)
             self.cut_faces.append(cf[k].astype(np.int32))
             self.cut_face_body.append(cfb[k])
             self.face_mom.append(np.ascontiguousarray(fm[k][:, :len(monomials(D - 1, q))]))

@@ -132,6 +132,30 @@ class Manufactured:
             stride *= shp[k]
         return lin.reshape(-1)
 
+    def wall_ids(self) -> np.ndarray:
+        """Global ids (faces normal to 0, then 1, then 2) of the open wall faces, ascending."""
+        g = self.g
+        out, base = [], 0
+        for d in range(g.dim):
+            for side in range(2):
+                f = self.wall_faces(d, side)
+                f = f[g.face_flag[d][f] > 0]
+                out.append(base + f)
+            base += g.nface(d)
+        return np.sort(np.concatenate(out))
+
+    def wall_phi_by_id(self) -> np.ndarray:
+        """<phi>_f on the open wall faces in ascending global face id (the C ABI's g_wall order)."""
+        g = self.g
+        ids = self.wall_ids()
+        out = np.zeros(len(ids))
+        base = 0
+        for d in range(g.dim):
+            m = (ids >= base) & (ids < base + g.nface(d))
+            out[m] = self.face_avg(d, ids[m] - base)
+            base += g.nface(d)
+        return out
+
     def wall_phi(self) -> np.ndarray:
         """<phi>_f on every wall face, walls ordered (d=0 low, d=0 high, d=1 low, ...), concatenated."""
         g = self.g

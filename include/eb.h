@@ -136,7 +136,7 @@ typedef struct eb_solve_opts {
   int32_t max_inner;      /* iteration cap per inner solve */
   int32_t max_outer;      /* refinement sweeps (mixed) */
   int32_t max_iters;      /* total iteration cap */
-  int32_t check_every;    /* host convergence check interval (iterations run as graphs in between) */
+  int32_t check_every;    /* < 0: time every Krylov operator apply with CUDA events (eb_solve_info.apply_ms) */
 } eb_solve_opts;
 
 typedef struct eb_solve_info {
@@ -145,6 +145,8 @@ typedef struct eb_solve_info {
   double rel_residual;    /* final ||rhs - kappa L phi||_2 / ||rhs||_2, FP64 */
   double history[64];     /* FP64 relative residual after each sweep (mixed) or check (FP64) */
   int32_t n_history;
+  int32_t n_applies;      /* Krylov operator applies timed (check_every < 0) */
+  double apply_ms;        /* their summed device time */
 } eb_solve_info;
 
 /* Solve L phi = rho - B g to a relative residual tol (kappa-weighted system
@@ -175,6 +177,10 @@ void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);
 const char* eb_last_error_message(void);
 int32_t eb_abi_version(void);
+
+/* Cumulative number of CUDA kernels this library has launched in the
+ * process (all threads); differences around a region count its launches. */
+int64_t eb_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -61,11 +61,13 @@ class EbSolveOpts(ctypes.Structure):
 
 class EbSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int32)]
+                ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int32), ("n_applies", ctypes.c_int32),
+                ("apply_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "sweeps": self.sweeps, "rel_residual": self.rel_residual,
-                "history": [self.history[i] for i in range(self.n_history)]}
+                "history": [self.history[i] for i in range(self.n_history)], "n_applies": self.n_applies,
+                "apply_ms": self.apply_ms}
 
 
 class EbError(RuntimeError):
@@ -103,6 +105,7 @@ def load():
         "eb_status_string": (ctypes.c_char_p, [i32]),
         "eb_last_error_message": (ctypes.c_char_p, []),
         "eb_abi_version": (i32, []),
+        "eb_kernel_launches": (i64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -238,9 +241,9 @@ def eb_bc_rhs(st: Stencils, g_eb, g_wall, Bg, kappa_weighted=True, stream=None):
 
 
 def eb_solve(st: Stencils, rho, g_eb, g_wall, phi, tol=1e-12, mixed=True, inner_tol=1e-5, max_inner=20000,
-             max_outer=40, max_iters=400000, stream=None, allow_not_converged=False) -> dict:
+             max_outer=40, max_iters=400000, stream=None, allow_not_converged=False, time_applies=False) -> dict:
     lib = load()
-    o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, 1)
+    o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, -1 if time_applies else 1)
     info = EbSolveInfo()
     code = lib.eb_solve(st.handle, _ptr(rho), _ptr(g_eb), _ptr(g_wall), tol, ctypes.byref(o), _ptr(phi),
                         ctypes.byref(info), _stream(stream))
@@ -279,5 +282,9 @@ def eb_last_error_faces() -> np.ndarray:
     return out[:n.value]
 
 
-__all__ = ["load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+def eb_kernel_launches() -> int:
+    return int(load().eb_kernel_launches())
+
+
+__all__ = ["eb_kernel_launches", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "eb_apply.cuh"
+#include "eb_internal.cuh"
 
 namespace eb {
 
@@ -63,12 +64,12 @@ template <typename T>
 cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
   size_t sm = ((a.nfoot * 4 + 15) / 16) * 16 + a.nfoot * sizeof(T);
   int64_t nb = (a.ncell + 255) / 256;
-  k_apply_template<T, 32><<<(unsigned)nb, 256, sm, s>>>(a);
+  k_apply_template<T, 32><<<(unsigned)nb, 256, sm, s>>>(a); eb::count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.n_irr > 0) {
     int64_t nb2 = (a.n_irr + 255) / 256;
-    k_apply_irregular<T><<<(unsigned)nb2, 256, a.nfoot * 4, s>>>(a);
+    k_apply_irregular<T><<<(unsigned)nb2, 256, a.nfoot * 4, s>>>(a); eb::count_launch();
     e = cudaGetLastError();
   }
   return e;

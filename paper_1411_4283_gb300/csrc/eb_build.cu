@@ -376,14 +376,51 @@ __global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* __restric
 
 // ============================================================ 4. weighted LS (FP64)
 
+__device__ __forceinline__ int tab_index(const double* delta) {
+  int i0 = (int)lrint(2.0 * delta[0]) + 11, i1 = (int)lrint(2.0 * delta[1]) + 11, i2 = (int)lrint(2.0 * delta[2]) + 11;
+  if (i0 < 0 || i0 >= TAB_S || i1 < 0 || i1 >= TAB_S || i2 < 0 || i2 >= TAB_S) return -1;
+  return i0 + TAB_S * (i1 + TAB_S * i2);
+}
 
+__device__ __forceinline__ double weight_of(const Dims& dm, double r2) {
+  // Sec. 2.4: W_ii = 1 if r < 1/2, else (2r)^-5, r = |x_i - x0| / h
+  if (!dm.weighted || r2 < dm.w_threshold * dm.w_threshold) return 1.0;
+  return pow(4.0 * r2, -0.5 * dm.w_power);
+}
 
+// Rows of full cells depend only on the offset delta = (cell centre - x0)/h:
+// the average of prod_d xi_d^{p_d} over the unit cell centred at delta is
+// prod_d ((delta_d + 1/2)^{p_d+1} - (delta_d - 1/2)^{p_d+1}) / (p_d + 1).
+__global__ void k_full_rows(Dims dm, const Tables* __restrict__ T, double* __restrict__ ftab,
+                            double* __restrict__ wtab) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= TAB_N) return;
+  double delta[3] = {0.5 * (t % TAB_S - 11), 0.5 * ((t / TAB_S) % TAB_S - 11), 0.5 * (t / (TAB_S * TAB_S) - 11)};
+  double oned[3][8];
+  for (int d = 0; d < 3; ++d) {
+    double a = delta[d] - 0.5, b = delta[d] + 0.5, pa = a, pb = b;
+    for (int p = 0; p < 8; ++p) {
+      oned[d][p] = d < dm.dim ? (pb - pa) / (p + 1) : (p == 0 ? 1.0 : 0.0);
+      pa *= a;
+      pb *= b;
+    }
+  }
+  double r2 = 0.0;
+  for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
+  double w = weight_of(dm, r2);
+  wtab[t] = w;
+  for (int i = 0; i < T->K; ++i) {
+    double v = 1.0;
+    for (int d = 0; d < dm.dim; ++d) v *= oned[d][T->mon[i][d]];
+    ftab[(int64_t)t * MAXK + i] = w * v;
+  }
+}
 
 // (x + delta)^p moments from x^p moments, separable passes (binomial expansion)
-__device__ void shift_moments(const Tables& T, const double* in, const double* delta, double* out, double* tmp) {
+__device__ void shift_moments(const Tables& T, const double* __restrict__ in, const double* delta, double* out,
+                              double* tmp) {
   const int K = T.K;
-  double* cur = out;
-  for (int i = 0; i < K; ++i) cur[i] = in[i];
+  for (int i = 0; i < K; ++i) out[i] = in[i];
   for (int d = 0; d < T.dim; ++d) {
     double dl = delta[d];
     if (dl == 0.0) continue;
@@ -391,16 +428,17 @@ __device__ void shift_moments(const Tables& T, const double* in, const double* d
     pw[0] = 1.0;
     for (int e = 1; e < 8; ++e) pw[e] = pw[e - 1] * dl;
     for (int i = 0; i < K; ++i) tmp[i] = 0.0;
-    for (int e = 0; e < T.nsh[d]; ++e) tmp[T.sh_out[d][e]] += T.sh_c[d][e] * pw[T.sh_pw[d][e]] * cur[T.sh_in[d][e]];
-    for (int i = 0; i < K; ++i) cur[i] = tmp[i];
+    for (int e = 0; e < T.nsh[d]; ++e) tmp[T.sh_out[d][e]] += T.sh_c[d][e] * pw[T.sh_pw[d][e]] * out[T.sh_in[d][e]];
+    for (int i = 0; i < K; ++i) out[i] = tmp[i];
   }
 }
 
-// One weighted LS row (Sec. 2.2.1, weights Sec. 2.4).  x0s: x0 offset from the
-// base cell centre in units of h.  Returns the weight, writes w * row.
+// One weighted LS row (Sec. 2.2.1 rows, Sec. 2.4 weights) written to row[];
+// x0s: x0 offset from the base cell centre in units of h.  Returns the weight.
 __device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, const int* base, const double* x0s,
-                            double* row, double* tmp, double* tmp2, int* bad) {
+                            double* row, double* tmp, int* bad) {
   const Dims& dm = a.dm;
+  const int K = T.K;
   int kind = rd_kind(desc);
   int c[3], dl[3];
   for (int d = 0; d < 3; ++d) {
@@ -410,16 +448,9 @@ __device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, con
   int64_t cid = cell_id(dm, c);
   double delta[3];
   for (int d = 0; d < 3; ++d) delta[d] = (double)dl[d] - x0s[d];
-  const int K = T.K;
   const double* src;
-  if (kind == 0) {
-    int32_t cut = a.cut_of_cell[cid];
-    src = cut >= 0 ? a.vol_mom + (int64_t)cut * dm.KS : T.full_vol;
-  } else if (kind == 1) {
-    int32_t cut = a.cut_of_cell[cid];
-    if (a.eb_bc && a.eb_bc[cut] != 0) *bad = 1;  // Neumann EB rows are not supported on the GPU path
-    src = a.eb_mom + (int64_t)cut * dm.KS;
-  } else {
+  double w;
+  if (kind == 2) {
     int wd = rd_wdir(desc), ws = rd_wside(desc);
     delta[wd] += ws ? 0.5 : -0.5;
     int fx[3] = {c[0], c[1], c[2]};
@@ -427,17 +458,33 @@ __device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, con
     int32_t cf = a.cutface_of[wd][face_local(dm, wd, fx)];
     if (cf >= 0) {
       const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
-      for (int i = 0; i < K; ++i) tmp2[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
-      src = tmp2;
+      for (int i = 0; i < K; ++i) row[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
+      src = row;
     } else src = T.full_face[wd];
+    double r2 = 0.0;
+    for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
+    w = weight_of(dm, r2);
+  } else {
+    int ti = tab_index(delta);
+    if (ti >= 0) w = a.wtab[ti];
+    else {
+      double r2 = 0.0;
+      for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
+      w = weight_of(dm, r2);
+    }
+    int32_t cut = a.cut_of_cell[cid];
+    if (kind == 0 && cut < 0 && ti >= 0) {
+      const double* fr = a.ftab + (int64_t)ti * MAXK;
+      for (int i = 0; i < K; ++i) row[i] = fr[i];
+      return w;
+    }
+    if (kind == 1) {
+      if (a.eb_bc && a.eb_bc[cut] != 0) *bad = 1;  // Neumann EB rows are not supported on the GPU path
+      src = a.eb_mom + (int64_t)cut * dm.KS;
+    } else src = cut >= 0 ? a.vol_mom + (int64_t)cut * dm.KS : T.full_vol;
   }
   shift_moments(T, src, delta, row, tmp);
-  double inv0 = 1.0 / row[0];
-  double r2 = 0.0;
-  for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
-  double w = 1.0;
-  if (dm.weighted && r2 >= dm.w_threshold * dm.w_threshold) w = pow(4.0 * r2, -0.5 * dm.w_power);
-  double sc = w * inv0;
+  double sc = w / row[0];
   for (int i = 0; i < K; ++i) row[i] *= sc;
   return w;
 }
@@ -447,18 +494,47 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
+// Column sums of P[0..32)[c0 .. c0+mm) (mm <= 32 columns): g lanes per column
+// each sum 32/g partials with independent accumulators, then a shuffle tree.
+// Returns the sum in the first lane of each group; *col is the column (or -1).
+__device__ __forceinline__ double column_sums(const double* P, int c0, int mm, int lane, int* col) {
+  int g = 1;
+  while (g * 2 * mm <= 32) g *= 2;
+  int cl = lane / g, part = lane % g, L = 32 / g;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (cl < mm) {
+    const double* p = P + (part * L) * KST + c0 + cl;
+    int l = 0;
+    for (; l + 4 <= L; l += 4) {
+      a0 += p[(l + 0) * KST];
+      a1 += p[(l + 1) * KST];
+      a2 += p[(l + 2) * KST];
+      a3 += p[(l + 3) * KST];
+    }
+    for (; l < L; ++l) a0 += p[l * KST];
+  }
+  double s = (a0 + a1) + (a2 + a3);
+  for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  *col = (cl < mm && part == 0) ? cl : -1;
+  return s;
+}
+
+__global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   LsWarpSmem& S = reinterpret_cast<LsWarpSmem*>(smem_raw)[warp];
   const Tables& T = *a.T;
   const int K = T.K;
   const int gw = blockIdx.x * LS_WARPS + warp;
-  double* scr = a.scratch + (int64_t)gw * MAXROWS * (MAXK + 2);
+  double* scr = a.scratch + (int64_t)gw * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
   double* scr_w = scr + (int64_t)MAXROWS * MAXK;
   double* scr_t = scr_w + MAXROWS;
   const Dims& dm = a.dm;
-  double tmp[MAXK], tmp2[MAXK], rowbuf[MAXK];
+  double* F = S.vec;
+  double* y = S.vec + MAXK;
+  double* z = S.vec + 2 * MAXK;
+  double* tau = S.vec + 3 * MAXK;
+  double* rinv = S.vec + 4 * MAXK;
   while (true) {
     int s = 0;
     if (lane == 0) s = atomicAdd(a.next, 1);
@@ -491,8 +567,8 @@ __global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
         int li = lane + 32 * r, i = c0 + li;
         double* dst = S.C + li * KST;
         if (i < n) {
-          double w = build_row(a, T, a.row_desc[p0 + i], base, x0s, rowbuf, tmp, tmp2, &bad);
-          for (int k = 0; k < K; ++k) { dst[k] = rowbuf[k]; scr[(int64_t)i * MAXK + k] = rowbuf[k]; }
+          double w = build_row(a, T, a.row_desc[p0 + i], base, x0s, dst, S.P + lane * KST, &bad);
+          for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = dst[k];
           scr_w[i] = w;
         } else {
           for (int k = 0; k < K; ++k) dst[k] = 0.0;
@@ -502,41 +578,50 @@ __global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
       for (int k = 0; k < K; ++k) {
         double ck[RPL];
         double ss = 0.0;
+#pragma unroll
         for (int r = 0; r < RPL; ++r) {
           ck[r] = S.C[(lane + 32 * r) * KST + k];
           ss = fma(ck[r], ck[r], ss);
         }
         ss = warp_sum(ss);
         if (ss == 0.0) continue;
-        double alpha = S.R[k * K + k];
-        double sigma = sqrt(fma(alpha, alpha, ss));
-        double beta = alpha > 0.0 ? -sigma : sigma;
-        double v0 = alpha - beta;
-        double gamma = -1.0 / (beta * v0);
-        int m = K - k - 1;
+        const double alpha = S.R[k * K + k];
+        const double sigma = sqrt(fma(alpha, alpha, ss));
+        const double beta = alpha > 0.0 ? -sigma : sigma;
+        const double v0 = alpha - beta;
+        const double gamma = -1.0 / (beta * v0);
+        const int m = K - k - 1;
+        // partial dots of column k with the later columns over this lane's rows
+#pragma unroll 2
         for (int jj = 0; jj < m; ++jj) {
-          int j = k + 1 + jj;
-          double p = 0.0;
-          for (int r = 0; r < RPL; ++r) p = fma(ck[r], S.C[(lane + 32 * r) * KST + j], p);
-          S.P[lane * (MAXK + 1) + jj] = p;
+          const int j = k + 1 + jj;
+          double p = ck[0] * S.C[lane * KST + j];
+#pragma unroll
+          for (int r = 1; r < RPL; ++r) p = fma(ck[r], S.C[(lane + 32 * r) * KST + j], p);
+          S.P[lane * KST + jj] = p;
         }
         __syncwarp();
-        for (int jj = lane; jj < m; jj += 32) {
-          double acc = 0.0;
-          for (int l = 0; l < 32; ++l) acc += S.P[l * (MAXK + 1) + jj];
-          int j = k + 1 + jj;
-          double wv = fma(v0, S.R[k * K + j], acc);
-          double tau = gamma * wv;
-          S.R[k * K + j] = fma(-tau, v0, S.R[k * K + j]);
-          S.vec[3 * MAXK + jj] = tau;
+        for (int c1 = 0; c1 < m; c1 += 32) {
+          int mm = m - c1 < 32 ? m - c1 : 32;
+          int col;
+          double sum = column_sums(S.P, c1, mm, lane, &col);
+          if (col >= 0) {
+            int jj = c1 + col, j = k + 1 + jj;
+            double rkj = S.R[k * K + j];
+            double t = gamma * fma(v0, rkj, sum);
+            S.R[k * K + j] = fma(-t, v0, rkj);
+            tau[jj] = t;
+          }
         }
         __syncwarp();
+#pragma unroll 2
         for (int jj = 0; jj < m; ++jj) {
-          int j = k + 1 + jj;
-          double tau = S.vec[3 * MAXK + jj];
+          const int j = k + 1 + jj;
+          const double t = tau[jj];
+#pragma unroll
           for (int r = 0; r < RPL; ++r) {
             double* cc = S.C + (lane + 32 * r) * KST + j;
-            *cc = fma(-tau, ck[r], *cc);
+            *cc = fma(-t, ck[r], *cc);
           }
         }
         if (lane == 0) S.R[k * K + k] = beta;
@@ -556,39 +641,37 @@ __global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
     if (bad) {
       if (lane == 0) a.status[s] = bad;
       for (int i = lane; i < n; i += 32) a.row_val[p0 + i] = 0.0;
+      __syncwarp();
       continue;
     }
+    for (int k = lane; k < K; k += 32) rinv[k] = 1.0 / S.R[k * K + k];
     // ---- F_hat (Sec. 2.2.1): grid face: p_d m_f^{p-e_d}; EB face: sum_d p_d m_{d,f}^{p-e_d}
-    double* F = S.vec;
-    double* y = S.vec + MAXK;
-    double* z = S.vec + 2 * MAXK;
-    if (lane == 0) {
-      for (int i = 0; i < K; ++i) F[i] = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      double f = 0.0;
       if (cut_self >= 0) {
         for (int d = 0; d < dm.dim; ++d) {
           const double* nm = a.eb_nmom + ((int64_t)cut_self * dm.dim + d) * dm.KS;
-          for (int i = 0; i < K; ++i)
-            if (T.lower[d][i] >= 0) F[i] += (double)T.mon[i][d] * nm[T.lower[d][i]];
+          if (T.lower[d][i] >= 0) f += (double)T.mon[i][d] * nm[T.lower[d][i]];
         }
       } else {
-        int32_t cf = a.cutface_of[dface][flocal];
-        for (int i = 0; i < K; ++i) {
-          int q = T.lower[dface][i];
-          if (q < 0) continue;
+        int q = T.lower[dface][i];
+        if (q >= 0) {
+          int32_t cf = a.cutface_of[dface][flocal];
           double mq;
           if (cf >= 0) mq = T.tang[dface][q] >= 0 ? a.face_mom[dface][(int64_t)cf * dm.KFS + T.tang[dface][q]] : 0.0;
           else mq = T.full_face[dface][q];
-          F[i] = (double)T.mon[i][dface] * mq;
+          f = (double)T.mon[i][dface] * mq;
         }
       }
+      F[i] = f;
     }
     __syncwarp();
-    // ---- z = R^-1 R^-T F (two triangular solves, lanes own columns)
+    // ---- z = R^-1 R^-T rhs (two triangular solves, lanes own columns)
     auto solve_rtr = [&](const double* rhs, double* outz) {
       for (int j = lane; j < K; j += 32) y[j] = rhs[j];
       __syncwarp();
       for (int k = 0; k < K; ++k) {  // R^T y = rhs (forward)
-        double yk = y[k] / S.R[k * K + k];
+        double yk = y[k] * rinv[k];
         __syncwarp();
         for (int j = k + 1 + lane; j < K; j += 32) y[j] = fma(-S.R[k * K + j], yk, y[j]);
         if (lane == 0) y[k] = yk;
@@ -597,7 +680,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
       for (int j = lane; j < K; j += 32) outz[j] = y[j];
       __syncwarp();
       for (int k = K - 1; k >= 0; --k) {  // R z = y (backward)
-        double zk = outz[k] / S.R[k * K + k];
+        double zk = outz[k] * rinv[k];
         __syncwarp();
         for (int j = lane; j < k; j += 32) outz[j] = fma(-S.R[j * K + k], zk, outz[j]);
         if (lane == 0) outz[k] = zk;
@@ -606,26 +689,26 @@ __global__ void __launch_bounds__(LS_WARPS * 32) k_lsq(LsArgs a) {
     };
     solve_rtr(F, z);
     // ---- corrected semi-normal equations: t1 = B z, r = F - B^T t1, t = t1 + B R^-1 R^-T r
-    double u[MAXK];
-    for (int k = 0; k < K; ++k) u[k] = 0.0;
+    for (int k = 0; k < K; ++k) S.P[lane * KST + k] = 0.0;
     for (int i = lane; i < n; i += 32) {
-      const double* b = scr + (int64_t)i * MAXK;
       double t1 = 0.0;
-      for (int k = 0; k < K; ++k) t1 = fma(b[k], z[k], t1);
+      for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
       scr_t[i] = t1;
-      for (int k = 0; k < K; ++k) u[k] = fma(b[k], t1, u[k]);
-    }
-    for (int k = 0; k < K; ++k) {
-      double v = warp_sum(u[k]);
-      if (lane == 0) S.vec[3 * MAXK + k] = F[k] - v;
+      for (int k = 0; k < K; ++k) S.P[lane * KST + k] = fma(scr[(int64_t)k * MAXROWS + i], t1, S.P[lane * KST + k]);
     }
     __syncwarp();
-    double* z2 = S.P;  // reuse
-    solve_rtr(S.vec + 3 * MAXK, z2);
+    for (int c1 = 0; c1 < K; c1 += 32) {
+      int mm = K - c1 < 32 ? K - c1 : 32;
+      int col;
+      double sum = column_sums(S.P, c1, mm, lane, &col);
+      if (col >= 0) tau[c1 + col] = F[c1 + col] - sum;
+    }
+    __syncwarp();
+    double* z2 = S.C;  // chunk buffer is free now
+    solve_rtr(tau, z2);
     for (int i = lane; i < n; i += 32) {
-      const double* b = scr + (int64_t)i * MAXK;
       double t = scr_t[i];
-      for (int k = 0; k < K; ++k) t = fma(b[k], z2[k], t);
+      for (int k = 0; k < K; ++k) t = fma(scr[(int64_t)k * MAXROWS + i], z2[k], t);
       a.row_val[p0 + i] = scr_w[i] * t;  // s_hat = W t
     }
     if (lane == 0) a.status[s] = 0;

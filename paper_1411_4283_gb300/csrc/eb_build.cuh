@@ -28,16 +28,20 @@ struct GatherArgs {
 };
 
 constexpr int LS_WARPS = 4;
-constexpr int RPL = 3;        // rows per lane per chunk
+constexpr int RPL = 4;        // rows per lane per chunk
 constexpr int CH = 32 * RPL;  // rows per chunk
 constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
 
 struct LsWarpSmem {
-  double R[MAXK * MAXK];
-  double C[CH * KST];
-  double P[32 * (MAXK + 1)];
-  double vec[4 * MAXK];  // F, y, z, tau/work
+  double R[MAXK * MAXK];  // triangular factor, row-major
+  double C[CH * KST];     // current chunk of weighted rows
+  double P[32 * KST];     // partial dot products / per-lane scratch
+  double vec[5 * MAXK];   // F, y, z, tau, 1/R_kk
 };
+
+// offsets in units of h/2 span [-11, 11] on each axis (volume, EB and wall rows)
+constexpr int TAB_S = 23;
+constexpr int TAB_N = TAB_S * TAB_S * TAB_S;
 
 struct LsArgs {
   Dims dm;
@@ -58,7 +62,9 @@ struct LsArgs {
   int64_t n_slots;
   int32_t* next;       // work counter
   int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row
-  double* scratch;     // per warp: MAXROWS * (K + 2) doubles
+  double* scratch;     // per warp: MAXROWS * (K + 2) doubles, column-major rows
+  const double* ftab;  // [TAB_N][MAXK] weighted rows of full cells, by offset
+  const double* wtab;  // [TAB_N] weights, by offset
 };
 
 struct AsmArgs {
@@ -90,6 +96,7 @@ __global__ void k_reach(Dims dm, const int32_t* cells, int64_t ncells, const uin
                         const uint8_t* ff1, const uint8_t* ff2, Mask* out);
 __global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* cut_cell);
 __global__ void k_lsq(LsArgs a);
+__global__ void k_full_rows(Dims dm, const Tables* T, double* ftab, double* wtab);
 __global__ void k_assemble_rows(AsmArgs a, const int32_t* rep_cell, int64_t nrep, int64_t row0, int32_t* err);
 __global__ void k_assemble_b(AsmArgs a, const int32_t* cells, int64_t ncells, int64_t* cnt, const int64_t* bptr,
                              int64_t* bcol, double* bval, const int32_t* unused);

@@ -130,5 +130,7 @@ eb_status cuda_status(cudaError_t e, const char* what);
 
 // host helpers
 std::vector<std::vector<int>> monomials(int dim, int q);
+// cumulative number of kernel launches issued by the library (all threads)
+void count_launch();
 
 }  // namespace eb

@@ -170,13 +170,13 @@ static unsigned grid_for(int64_t n) {
 // ----------------------------------------------------------------- host drivers
 
 cudaError_t vec_fill64(int64_t n, double* x, double v, cudaStream_t s) {
-  k_fill<double><<<grid_for(n), VB, 0, s>>>(n, x, v);
+  k_fill<double><<<grid_for(n), VB, 0, s>>>(n, x, v); eb::count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t compute_rhs(int64_t n, const uint8_t* flag, const double* kappa, const double* rho, const double* bg,
                         double* out, cudaStream_t s) {
-  k_rhs<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, rho, bg, out);
+  k_rhs<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, rho, bg, out); eb::count_launch();
   return cudaGetLastError();
 }
 
@@ -185,13 +185,13 @@ cudaError_t launch_bg(int64_t n_irr, const int32_t* irr_cell, const int64_t* bpt
                       const double* g_wall, const double* inv_kappa, int kw, double* out, cudaStream_t s) {
   if (n_irr == 0) return cudaSuccess;
   k_bg<<<(unsigned)((n_irr + 255) / 256), 256, 0, s>>>(n_irr, irr_cell, bptr, bcol, bval, n_grid_faces, wall_pos,
-                                                       g_eb, g_wall, inv_kappa, kw, out);
+                                                       g_eb, g_wall, inv_kappa, kw, out); eb::count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_norms(int64_t n, const uint8_t* flag, const double* kappa, const double* e, double* out,
                          cudaStream_t s) {
-  k_norms<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, e, out);
+  k_norms<<<grid_for(n), VB, 0, s>>>(n, flag, kappa, e, out); eb::count_launch();
   return cudaGetLastError();
 }
 
@@ -200,7 +200,7 @@ static cudaError_t dots(int64_t n, const T* a0, const T* b0, const T* a1, const 
                         double* dev, double* host, int cnt, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(dev, 0, 3 * sizeof(double), s);
   if (e) return e;
-  k_dots<T><<<grid_for(n), VB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dev);
+  k_dots<T><<<grid_for(n), VB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dev); eb::count_launch();
   if ((e = cudaGetLastError())) return e;
   if ((e = cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
   return cudaStreamSynchronize(s);
@@ -208,6 +208,44 @@ static cudaError_t dots(int64_t n, const T* a0, const T* b0, const T* a1, const 
 
 // Jacobi-preconditioned BiCGStab on A x = b (x in/out).  Returns iterations
 // used; *relres = ||b - A x|| / ||b|| as tracked by the recurrence.
+// device time of every operator apply issued by the solver (CUDA events on the solve stream)
+struct ApplyTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms = 0.0;
+  long long n = 0;
+};
+static ApplyTimer* g_timer = nullptr;
+void set_apply_timer(void* t) { g_timer = (ApplyTimer*)t; }
+void* new_apply_timer() {
+  ApplyTimer* t = new ApplyTimer();
+  cudaEventCreate(&t->e0);
+  cudaEventCreate(&t->e1);
+  return t;
+}
+void free_apply_timer(void* p, double* ms, long long* n) {
+  ApplyTimer* t = (ApplyTimer*)p;
+  if (!t) return;
+  *ms = t->ms;
+  *n = t->n;
+  cudaEventDestroy(t->e0);
+  cudaEventDestroy(t->e1);
+  delete t;
+}
+
+template <typename T>
+static cudaError_t timed_apply(const ApplyArgs<T>& A, cudaStream_t s) {
+  if (!g_timer) return launch_apply<T>(A, s);
+  cudaEventRecord(g_timer->e0, s);
+  cudaError_t e = launch_apply<T>(A, s);
+  cudaEventRecord(g_timer->e1, s);
+  cudaEventSynchronize(g_timer->e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, g_timer->e0, g_timer->e1);
+  g_timer->ms += ms;
+  g_timer->n += 1;
+  return e;
+}
+
 template <typename T>
 cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T* work, int64_t n, double tol,
                      int maxit, double* dscr, int* iters, double* relres, cudaStream_t s) {
@@ -224,11 +262,11 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
   double h[3];
   // r = b - A x
   A.phi = x; A.y = r;
-  if ((e = launch_apply<T>(A, s))) return e;
-  k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, b, r, r, rh, dinv, 1.0);  // r = b - Ax (rh scratch)
-  k_copy<T><<<grid_for(n), VB, 0, s>>>(n, r, rh);
-  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, p, (T)0);
-  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, v, (T)0);
+  if ((e = timed_apply<T>(A, s))) return e;
+  k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, b, r, r, rh, dinv, 1.0); eb::count_launch();  // r = b - Ax (rh scratch)
+  k_copy<T><<<grid_for(n), VB, 0, s>>>(n, r, rh); eb::count_launch();
+  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, p, (T)0); eb::count_launch();
+  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, v, (T)0); eb::count_launch();
   if ((e = dots<T>(n, b, b, r, r, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
   double bn = sqrt(h[0]);
   if (bn == 0.0) bn = 1.0;
@@ -243,19 +281,19 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
     double rho = h[0];
     if (rho == 0.0) break;
     double beta = (rho / rho_old) * (alpha / omega);
-    k_bicg_p<T><<<grid_for(n), VB, 0, s>>>(n, r, v, p, ph, dinv, it == 1 ? 0.0 : beta, omega);
+    k_bicg_p<T><<<grid_for(n), VB, 0, s>>>(n, r, v, p, ph, dinv, it == 1 ? 0.0 : beta, omega); eb::count_launch();
     A.phi = ph; A.y = v;
-    if ((e = launch_apply<T>(A, s))) return e;
+    if ((e = timed_apply<T>(A, s))) return e;
     if ((e = dots<T>(n, rh, v, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
       return e;
     if (h[0] == 0.0) break;
     alpha = rho / h[0];
-    k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, r, v, sv, shv, dinv, alpha);
+    k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, r, v, sv, shv, dinv, alpha); eb::count_launch();
     A.phi = shv; A.y = t;
-    if ((e = launch_apply<T>(A, s))) return e;
+    if ((e = timed_apply<T>(A, s))) return e;
     if ((e = dots<T>(n, t, sv, t, t, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
     omega = h[1] > 0 ? h[0] / h[1] : 0.0;
-    k_bicg_x<T><<<grid_for(n), VB, 0, s>>>(n, x, ph, shv, r, sv, t, alpha, omega);
+    k_bicg_x<T><<<grid_for(n), VB, 0, s>>>(n, x, ph, shv, r, sv, t, alpha, omega); eb::count_launch();
     rho_old = rho;
     if ((e = dots<T>(n, r, r, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
       return e;
@@ -272,19 +310,19 @@ template cudaError_t bicgstab<double>(const ApplyArgs<double>&, const double*, d
                                       int64_t, double, int, double*, int*, double*, cudaStream_t);
 
 cudaError_t resid64(int64_t n, const double* b, const double* y, double* r, cudaStream_t s) {
-  k_resid64<<<grid_for(n), VB, 0, s>>>(n, b, y, r);
+  k_resid64<<<grid_for(n), VB, 0, s>>>(n, b, y, r); eb::count_launch();
   return cudaGetLastError();
 }
 cudaError_t to32(int64_t n, const double* a, double scale, float* o, cudaStream_t s) {
-  k_to32<<<grid_for(n), VB, 0, s>>>(n, a, scale, o);
+  k_to32<<<grid_for(n), VB, 0, s>>>(n, a, scale, o); eb::count_launch();
   return cudaGetLastError();
 }
 cudaError_t add32(int64_t n, double* x, double scale, const float* d, cudaStream_t s) {
-  k_add32<<<grid_for(n), VB, 0, s>>>(n, x, scale, d);
+  k_add32<<<grid_for(n), VB, 0, s>>>(n, x, scale, d); eb::count_launch();
   return cudaGetLastError();
 }
 cudaError_t fill32(int64_t n, float* x, float v, cudaStream_t s) {
-  k_fill<float><<<grid_for(n), VB, 0, s>>>(n, x, v);
+  k_fill<float><<<grid_for(n), VB, 0, s>>>(n, x, v); eb::count_launch();
   return cudaGetLastError();
 }
 cudaError_t norm2_64(int64_t n, const double* a, double* dscr, double* out, cudaStream_t s) {

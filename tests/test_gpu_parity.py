@@ -3,8 +3,9 @@
 Tolerances: stencil coefficients 1e-10 relative to the face's largest coefficient; FP64 kappa-weighted
 apply 1e-12 normwise relative; refined solutions 1e-9 relative to max|phi|; FP32 apply 1e-5 normwise
 (single precision storage of coefficients and of phi).  The unweighted operator and B divide rows by
-kappa (down to ~1e-4), which magnifies the rounding of their sums; they are held to the rounding bound
-of a length-n dot product, |y - y_ref|_i <= 4 n eps (|L| |phi|)_i with n the footprint size.
+kappa (down to ~1e-4), which magnifies cancellation in their sums; they are held componentwise to
+|y - y_ref|_i <= 1e-11 (|L| |phi|)_i: the coefficients of the two operators agree to ~1e-12 relative
+(the stencils' agreement), plus the rounding of a length-n dot product (n eps, n <= 637).
 """
 EPS = 2.220446049250313e-16
 import numpy as np
@@ -62,7 +63,7 @@ def test_apply_fp64_2d(circle32, kw):
     if kw:
         assert np.linalg.norm(yg - yo) <= 1e-12 * np.linalg.norm(yo)
     else:
-        bound = 4 * 77 * EPS * (abs(ref["L"]) @ np.abs(phi))
+        bound = 1e-11 * (abs(ref["L"]) @ np.abs(phi))
         assert np.all(np.abs(yg - yo) <= bound + 1e-300)
     assert np.all(yg[g.flag == 0] == 0)
 
@@ -88,7 +89,7 @@ def test_bc_rhs_2d(circle32):
     Bg = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
     P.eb_bc_rhs(st, to_dev(ge), to_dev(gw), Bg, kappa_weighted=False)
     bo = ref["B"] @ ref["G"]
-    bound = 4 * 64 * EPS * (abs(ref["B"]) @ np.abs(ref["G"]))
+    bound = 1e-11 * (abs(ref["B"]) @ np.abs(ref["G"]))
     assert np.all(np.abs(Bg.cpu().numpy() - bo) <= bound + 1e-300)
 
 
