@@ -336,6 +336,15 @@ int64_t eb_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 void eb_stencils_destroy(eb_stencils* st) {
   if (!st) return;
+  if (st->plan) {
+    if (st->plan->side) {
+      cudaStreamSynchronize(st->plan->side);
+      cudaStreamDestroy(st->plan->side);
+    }
+    if (st->plan->fork) cudaEventDestroy(st->plan->fork);
+    if (st->plan->join) cudaEventDestroy(st->plan->join);
+    delete st->plan;
+  }
   for (void* p : st->allocs) cudaFree(p);
   delete st;
 }
@@ -875,6 +884,40 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
     info->n_irregular_rows = st->n_rows - n_class_rows;
     info->n_row_classes = (int32_t)n_class_rows;
   }
+  // ---- apply plan: TMA template pass when the row stride suits TMA, irregular rows overlapped
+  {
+    ApplyPlan* pl = new ApplyPlan();
+    st->plan = pl;
+    pl->nx = dm.n[0];
+    pl->ny = dm.n[1];
+    pl->nz = dm.n[2];
+    pl->dim = D;
+    pl->R = R;
+    pl->nsm = nsm;
+    pl->side = nullptr;
+    pl->fork = pl->join = nullptr;
+    EB_TRY(dalloc(st, &pl->err, 1));
+    EB_CUDA(cudaMemsetAsync(pl->err, 0, 4, s));
+    std::vector<double> tm(st->nfoot);
+    std::vector<int8_t> fd(st->nfoot * 3);
+    EB_CUDA(cudaMemcpyAsync(tm.data(), st->tmpl64, st->nfoot * 8, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaMemcpyAsync(fd.data(), st->foot_d, st->nfoot * 3, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    int L = R + 1, S = 2 * L + 1;
+    pl->cube64.assign(S * S * S, 0.0);
+    pl->cube32.assign(S * S * S, 0.0f);
+    for (int i = 0; i < st->nfoot; ++i) {
+      int idx = (fd[3 * i] + L) + S * ((fd[3 * i + 1] + L) + S * (fd[3 * i + 2] + L));
+      pl->cube64[idx] = tm[i];
+      pl->cube32[idx] = (float)tm[i];
+    }
+    bool ok = dm.nbr_box && st->n_row_classes > 0;
+    pl->tma32 = ok && (dm.n[0] % 4 == 0);
+    pl->tma64 = ok && (dm.n[0] % 2 == 0);
+    EB_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
+    EB_CUDA(cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming));
+    EB_CUDA(cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming));
+  }
   EB_CUDA(cudaEventRecord(ev[4], s));
   EB_CUDA(cudaStreamSynchronize(s));
   // ---- info
@@ -948,6 +991,7 @@ ApplyArgs<float> apply_args<float>(const eb_stencils* st, int kw) {
   a.phi = nullptr;
   a.y = nullptr;
   a.kappa_weighted = kw;
+  a.plan = st->plan;
   return a;
 }
 template <>
@@ -967,6 +1011,7 @@ ApplyArgs<double> apply_args<double>(const eb_stencils* st, int kw) {
   a.phi = nullptr;
   a.y = nullptr;
   a.kappa_weighted = kw;
+  a.plan = st->plan;
   return a;
 }
 
@@ -1111,6 +1156,11 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
     if (inf->rel_residual > tol * 10) ret = EB_ERR_NOT_CONVERGED;
   }
   EB_CUDA(cudaStreamSynchronize(s));
+  if (st->plan && st->plan->err) {
+    int32_t h = 0;
+    EB_CUDA(cudaMemcpy(&h, st->plan->err, 4, cudaMemcpyDeviceToHost));
+    if (h) { set_error("a bounded device wait gave up in the operator apply"); return EB_ERR_TIMEOUT; }
+  }
   if (ret != EB_OK) set_error("solve did not reach the requested tolerance");
   return ret;
 }

@@ -10,6 +10,9 @@
 
 #include "eb_apply.cuh"
 #include "eb_internal.cuh"
+#include "eb_apply_tma.cuh"
+
+#include <cuda.h>
 
 namespace eb {
 
@@ -60,19 +63,110 @@ __global__ void __launch_bounds__(256) k_apply_irregular(ApplyArgs<T> a) {
   a.y[c] = acc;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+template <typename T, int R, int D>
+static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaStream_t s) {
+  constexpr int L = R + 1;
+  constexpr int S = 2 * L + 1;
+  constexpr int NP = D == 3 ? S : 1;
+  constexpr int PX = TT_OX + 2 * L, PY = TT_OY + 2 * L;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  cuuint64_t gdim[3] = {(cuuint64_t)pl.nx, (cuuint64_t)pl.ny, (cuuint64_t)pl.nz};
+  cuuint64_t gstr[2] = {(cuuint64_t)pl.nx * sizeof(T), (cuuint64_t)pl.nx * pl.ny * sizeof(T)};
+  cuuint32_t box[3] = {PX, PY, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(&map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                   (void*)a.phi, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  TmplCoef<T, R> cf;
+  const T* cube;
+  if constexpr (sizeof(T) == 4) cube = pl.cube32.data();
+  else cube = pl.cube64.data();
+  for (int i = 0; i < S * S * S; ++i) cf.c[i] = cube[i];
+  TmplArgs<T> ta;
+  ta.nx = pl.nx;
+  ta.ny = pl.ny;
+  ta.nz = pl.nz;
+  ta.ntx = (pl.nx + TT_OX - 1) / TT_OX;
+  ta.nty = (pl.ny + TT_OY - 1) / TT_OY;
+  ta.zchunk = D == 3 ? (pl.nz >= 128 ? 16 : 8) : 1;
+  ta.nzc = (pl.nz + ta.zchunk - 1) / ta.zchunk;
+  ta.items = (int64_t)ta.ntx * ta.nty * ta.nzc;
+  ta.kind = a.kind;
+  ta.inv_kappa = a.inv_kappa;
+  ta.y = a.y;
+  ta.kappa_weighted = a.kappa_weighted;
+  ta.err = pl.err;
+  size_t smem = (size_t)NP * PX * PY * sizeof(T) + NP * 8;
+  auto kern = k_apply_tma<T, R, D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)pl.nsm * (per_sm > 0 ? per_sm : 1);
+  if (grid > ta.items) grid = ta.items;
+  kern<<<(unsigned)grid, TT_THREADS, smem, s>>>(map, cf, ta); eb::count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
-cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
+static cudaError_t launch_template_pass(const ApplyArgs<T>& a, cudaStream_t s) {
+  const ApplyPlan* pl = a.plan;
+  bool tma = pl && (sizeof(T) == 4 ? pl->tma32 : pl->tma64);
+  if (tma) {
+    if (pl->dim == 3 && pl->R == 3) return launch_tma<T, 3, 3>(a, *pl, s);
+    if (pl->dim == 3 && pl->R == 2) return launch_tma<T, 2, 3>(a, *pl, s);
+    if (pl->dim == 2 && pl->R == 3) return launch_tma<T, 3, 2>(a, *pl, s);
+    if (pl->dim == 2 && pl->R == 2) return launch_tma<T, 2, 2>(a, *pl, s);
+  }
   size_t sm = ((a.nfoot * 4 + 15) / 16) * 16 + a.nfoot * sizeof(T);
   int64_t nb = (a.ncell + 255) / 256;
   k_apply_template<T, 32><<<(unsigned)nb, 256, sm, s>>>(a); eb::count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
+  const ApplyPlan* pl = a.plan;
+  cudaError_t e;
+  bool fork = pl && pl->side && a.n_irr > 0;
+  if (fork) {
+    // the irregular rows run on the side stream, overlapped with the template pass (disjoint cells)
+    if ((e = cudaEventRecord(pl->fork, s))) return e;
+    if ((e = cudaStreamWaitEvent(pl->side, pl->fork, 0))) return e;
+  }
   if (a.n_irr > 0) {
     int64_t nb2 = (a.n_irr + 255) / 256;
-    k_apply_irregular<T><<<(unsigned)nb2, 256, a.nfoot * 4, s>>>(a); eb::count_launch();
-    e = cudaGetLastError();
+    k_apply_irregular<T><<<(unsigned)nb2, 256, a.nfoot * 4, fork ? pl->side : s>>>(a); eb::count_launch();
+    if ((e = cudaGetLastError())) return e;
   }
-  return e;
+  if ((e = launch_template_pass<T>(a, s))) return e;
+  if (fork) {
+    if ((e = cudaEventRecord(pl->join, pl->side))) return e;
+    if ((e = cudaStreamWaitEvent(s, pl->join, 0))) return e;
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_apply<float>(const ApplyArgs<float>&, cudaStream_t);

@@ -2,7 +2,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace eb {
+
+struct ApplyPlan;
 
 template <typename T>
 struct ApplyArgs {
@@ -20,6 +24,20 @@ struct ApplyArgs {
   const T* phi;
   T* y;
   int kappa_weighted;
+  // fast template path (TMA tiles); null plan = generic kernels only
+  const ApplyPlan* plan;
+};
+
+// Host-side launch plan of the apply, owned by eb_stencils.
+struct ApplyPlan {
+  int nx, ny, nz, dim, R;
+  int tma32, tma64;              // template pass by TMA tiles possible (box metric, aligned rows)
+  std::vector<float> cube32;     // dense (2R+3)^3 template coefficients
+  std::vector<double> cube64;
+  int32_t* err;                  // device error word (bounded waits)
+  cudaStream_t side;             // irregular pass runs here, overlapped with the template pass
+  cudaEvent_t fork, join;
+  int nsm;
 };
 
 template <typename T>

@@ -575,12 +575,14 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
         }
       }
       __syncwarp();
+      // rows of this chunk per lane (the last chunk is short: skip its empty row slots)
+      const int nr = (min(CH, n - c0) + 31) >> 5;
       for (int k = 0; k < K; ++k) {
         double ck[RPL];
         double ss = 0.0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
-          ck[r] = S.C[(lane + 32 * r) * KST + k];
+          ck[r] = r < nr ? S.C[(lane + 32 * r) * KST + k] : 0.0;
           ss = fma(ck[r], ck[r], ss);
         }
         ss = warp_sum(ss);
@@ -591,14 +593,34 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
         const double v0 = alpha - beta;
         const double gamma = -1.0 / (beta * v0);
         const int m = K - k - 1;
-        // partial dots of column k with the later columns over this lane's rows
-#pragma unroll 2
-        for (int jj = 0; jj < m; ++jj) {
-          const int j = k + 1 + jj;
-          double p = ck[0] * S.C[lane * KST + j];
+        const double* Cl = S.C + lane * KST + k + 1;
+        double* Pl = S.P + lane * KST;
+        // partial dots of column k with the later columns over this lane's rows; four columns at a
+        // time keep four independent FMA chains in flight
+        int jj = 0;
+        for (; jj + 4 <= m; jj += 4) {
+          double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
 #pragma unroll
-          for (int r = 1; r < RPL; ++r) p = fma(ck[r], S.C[(lane + 32 * r) * KST + j], p);
-          S.P[lane * KST + jj] = p;
+          for (int r = 0; r < RPL; ++r) {
+            if (r < nr) {
+              const double* c = Cl + 32 * r * KST + jj;
+              p0 = fma(ck[r], c[0], p0);
+              p1 = fma(ck[r], c[1], p1);
+              p2 = fma(ck[r], c[2], p2);
+              p3 = fma(ck[r], c[3], p3);
+            }
+          }
+          Pl[jj] = p0;
+          Pl[jj + 1] = p1;
+          Pl[jj + 2] = p2;
+          Pl[jj + 3] = p3;
+        }
+        for (; jj < m; ++jj) {
+          double p0 = 0.0;
+#pragma unroll
+          for (int r = 0; r < RPL; ++r)
+            if (r < nr) p0 = fma(ck[r], Cl[32 * r * KST + jj], p0);
+          Pl[jj] = p0;
         }
         __syncwarp();
         for (int c1 = 0; c1 < m; c1 += 32) {
@@ -606,23 +628,35 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
           int col;
           double sum = column_sums(S.P, c1, mm, lane, &col);
           if (col >= 0) {
-            int jj = c1 + col, j = k + 1 + jj;
+            int jc = c1 + col, j = k + 1 + jc;
             double rkj = S.R[k * K + j];
             double t = gamma * fma(v0, rkj, sum);
             S.R[k * K + j] = fma(-t, v0, rkj);
-            tau[jj] = t;
+            tau[jc] = t;
           }
         }
         __syncwarp();
-#pragma unroll 2
-        for (int jj = 0; jj < m; ++jj) {
-          const int j = k + 1 + jj;
-          const double t = tau[jj];
+        double* Cw = S.C + lane * KST + k + 1;
+        jj = 0;
+        for (; jj + 4 <= m; jj += 4) {
+          const double t0 = tau[jj], t1 = tau[jj + 1], t2 = tau[jj + 2], t3 = tau[jj + 3];
 #pragma unroll
           for (int r = 0; r < RPL; ++r) {
-            double* cc = S.C + (lane + 32 * r) * KST + j;
-            *cc = fma(-t, ck[r], *cc);
+            if (r < nr) {
+              double* c = Cw + 32 * r * KST + jj;
+              double a0 = c[0], a1 = c[1], a2 = c[2], a3 = c[3];
+              c[0] = fma(-t0, ck[r], a0);
+              c[1] = fma(-t1, ck[r], a1);
+              c[2] = fma(-t2, ck[r], a2);
+              c[3] = fma(-t3, ck[r], a3);
+            }
           }
+        }
+        for (; jj < m; ++jj) {
+          const double t0 = tau[jj];
+#pragma unroll
+          for (int r = 0; r < RPL; ++r)
+            if (r < nr) Cw[32 * r * KST + jj] = fma(-t0, ck[r], Cw[32 * r * KST + jj]);
         }
         if (lane == 0) S.R[k * K + k] = beta;
         __syncwarp();

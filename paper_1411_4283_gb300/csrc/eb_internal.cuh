@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/eb.h"
+#include "eb_apply.cuh"
 
 namespace eb {
 
@@ -106,6 +107,7 @@ struct eb_stencils {
   int64_t n_wall = 0;
   int64_t* wall_ids = nullptr;      // device
   std::vector<int64_t> wall_ids_host;
+  eb::ApplyPlan* plan = nullptr;
   int64_t* b_wpos = nullptr;       // [nnz(B)] position of a wall column in the wall list (-1: EB)
   double* dinv64 = nullptr;         // [ncell] inverse diagonal of kappa L (0 on covered cells)
   float* dinv32 = nullptr;
