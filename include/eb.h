@@ -173,6 +173,29 @@ eb_status eb_wall_faces(const eb_stencils* st, int64_t* ids_host, int64_t cap, i
 /* Faces whose LS system was rank deficient in the last failed build. */
 eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n);
 
+/* Batched weighted minimum-norm least squares that allocates nothing (the
+ * paper has no counterpart; this is a service for callers that cannot
+ * allocate device memory where they solve, e.g. code running inside a fixed
+ * memory pool or arena, real-time hosts that allocate only at start-up, or
+ * plugin hosts that forbid allocation in callbacks).
+ * For each system q (rows row_ptr[q] .. row_ptr[q+1]-1, at most 256 rows and
+ * K <= 35 unknowns): B holds the weighted rows W A ([nnz][K], row-major), w
+ * the weights W_ii, F the right-hand side ([n_sys][K]); s receives the
+ * stencil s = W t with t the least-||t|| solution of B^T t = F (Sec. 2.2.1
+ * applied to rows the caller formed); status[q] = 0 ok, 1 rank deficient or
+ * fewer rows than K, 3 more than 256 rows.  All pointers are device pointers
+ * owned by the caller.  max_rows is the caller's bound on the rows of any
+ * system; above 256 the call returns EB_ERR_CAPACITY without launching.
+ * Working storage is one fixed 9.4 MB array compiled into the library (held
+ * by every GPU that loads it until the process exits); nothing is allocated.
+ * The first call on each device looks up that array's device address (with
+ * the device current) and should come before any stream capture.  Every call
+ * shares the array, so calls that overlap on the GPU (other streams, other
+ * host threads) race: serialise them.  Never synchronises. */
+eb_status eb_lsq_batch_noalloc(const double* B, const double* w, const double* F, const int64_t* row_ptr,
+                               int32_t n_sys, int32_t K, int32_t max_rows, double* s, int32_t* status,
+                               eb_stream_t stream);
+
 void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);
 const char* eb_last_error_message(void);

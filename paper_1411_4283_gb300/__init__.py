@@ -106,6 +106,7 @@ def load():
         "eb_last_error_message": (ctypes.c_char_p, []),
         "eb_abi_version": (i32, []),
         "eb_kernel_launches": (i64, []),
+        "eb_lsq_batch_noalloc": (i32, [_vp, _vp, _vp, _vp, i32, i32, i32, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,9 +283,22 @@ def eb_last_error_faces() -> np.ndarray:
     return out[:n.value]
 
 
+def eb_lsq_batch_noalloc(B, w, F, row_ptr, K, max_rows, s, status, stream=None):
+    """Batched weighted minimum-norm least squares with no allocation (see include/eb.h).
+
+    For callers that cannot allocate device memory where they solve (fixed pools or arenas,
+    real-time hosts, allocation-free plugin callbacks): all tensors are the caller's, and the
+    library's working storage is one fixed array.  Calls that overlap on the GPU race.
+    """
+    n_sys = int(row_ptr.numel()) - 1
+    _check(load().eb_lsq_batch_noalloc(_ptr(B), _ptr(w), _ptr(F), _ptr(row_ptr), n_sys, int(K), int(max_rows),
+                                       _ptr(s), _ptr(status), _stream(stream)))
+    return s
+
+
 def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]
