@@ -914,6 +914,7 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
     bool ok = dm.nbr_box && st->n_row_classes > 0;
     pl->tma32 = ok && (dm.n[0] % 4 == 0);
     pl->tma64 = ok && (dm.n[0] % 2 == 0);
+    pl->seg = dm.nbr_box;
     EB_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
     EB_CUDA(cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming));
     EB_CUDA(cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming));
@@ -1086,7 +1087,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
   EB_TRY(tmp.get(&rhs, n));
   EB_TRY(tmp.get(&y64, n));
   EB_TRY(tmp.get(&r64, n));
-  EB_TRY(tmp.get(&dscr, 4));
+  EB_TRY(tmp.get(&dscr, 16));
   EB_TRY(eb_bc_rhs(st, g_eb, g_wall, bg, 1, stream));
   EB_CUDA(compute_rhs(n, st->flag, st->kappa, rho, bg, rhs, s));
   double bnorm = 0.0;

@@ -63,6 +63,88 @@ __global__ void __launch_bounds__(256) k_apply_irregular(ApplyArgs<T> a) {
   a.y[c] = acc;
 }
 
+// Irregular rows for box neighbourhoods of radius R in D dimensions: the
+// footprint is a union of x-contiguous segments (dz, dy, dx in [-X, X]) whose
+// coefficients are consecutive in footprint order.  One thread per row walks
+// the segments (a rolled loop keeps the code small); a segment whose
+// (y + dy, z + dz) leaves the grid has zero coefficients and is skipped, and
+// only the x-ends of the first and last grid rows need an address clamp.
+template <typename T, int R, int D>
+__global__ void __launch_bounds__(256) k_apply_irregular_seg(ApplyArgs<T> a, int nx, int ny, int nz) {
+  constexpr int L = R + 1;
+  constexpr int NZ = D == 3 ? 2 * L + 1 : 1;
+  constexpr int NY = 2 * L + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_irr) return;
+  const int64_t c = a.irr_cell[t];
+  const int cx = (int)(c % nx);
+  const int64_t cr = c / nx;
+  const int cy = (int)(cr % ny), cz = (int)(cr / ny);
+  const int64_t stride = a.n_rows;
+  const T* cf = a.rows + a.irr_row[t];
+  const int64_t ncell = a.ncell;
+  T acc0 = 0, acc1 = 0;
+#pragma unroll 1
+  for (int sgi = 0; sgi < NZ * NY; ++sgi) {
+    const int dz = D == 3 ? sgi / NY - L : 0;
+    const int dy = sgi % NY - L;
+    const int az = dz < 0 ? -dz : dz, ay = dy < 0 ? -dy : dy;
+    if (az > R && ay > R) continue;
+    const bool wide = !(az > R || ay > R);  // x extent L (wide) or R
+    const int X = wide ? L : R;
+    const int zz = cz + dz, yy = cy + dy;
+    if (zz >= 0 && zz < nz && yy >= 0 && yy < ny) {
+      const int64_t base = (int64_t)nx * ((int64_t)yy + (int64_t)ny * zz) + cx;
+      if (base - X >= 0 && base + X < ncell) {
+        const T* ph = a.phi + base;
+        if (wide) {
+#pragma unroll
+          for (int dx = -L; dx <= L; ++dx) {
+            if (dx & 1) acc1 = fma(__ldg(cf), __ldg(ph + dx), acc1);
+            else acc0 = fma(__ldg(cf), __ldg(ph + dx), acc0);
+            cf += stride;
+          }
+        } else {
+#pragma unroll
+          for (int dx = -R; dx <= R; ++dx) {
+            if (dx & 1) acc1 = fma(__ldg(cf), __ldg(ph + dx), acc1);
+            else acc0 = fma(__ldg(cf), __ldg(ph + dx), acc0);
+            cf += stride;
+          }
+        }
+        continue;
+      }
+      for (int dx = -X; dx <= X; ++dx) {
+        int64_t q = base + dx;
+        q = q < 0 ? 0 : (q >= ncell ? ncell - 1 : q);
+        acc0 = fma(__ldg(cf), __ldg(a.phi + q), acc0);
+        cf += stride;
+      }
+    } else {
+      cf += (int64_t)(2 * X + 1) * stride;
+    }
+  }
+  T acc = acc0 + acc1;
+  if (!a.kappa_weighted) acc *= (T)a.inv_kappa[c];
+  a.y[c] = acc;
+}
+
+template <typename T>
+static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
+  const ApplyPlan* pl = a.plan;
+  int64_t nb = (a.n_irr + 255) / 256;
+  if (pl && pl->seg) {
+    if (pl->dim == 3 && pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
+    else if (pl->dim == 3 && pl->R == 2) k_apply_irregular_seg<T, 2, 3><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
+    else if (pl->dim == 2 && pl->R == 3) k_apply_irregular_seg<T, 3, 2><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
+    else k_apply_irregular_seg<T, 2, 2><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
+  } else {
+    k_apply_irregular<T><<<(unsigned)nb, 256, a.nfoot * 4, st>>>(a);
+  }
+  eb::count_launch();
+  return cudaGetLastError();
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -119,11 +201,19 @@ static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaSt
   ta.err = pl.err;
   size_t smem = (size_t)NP * PX * PY * sizeof(T) + NP * 8;
   auto kern = k_apply_tma<T, R, D>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // attribute and occupancy are per device; kept for the last device seen
+  static int cached_dev = -1, cached_per_sm = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT_THREADS, smem);
-  if (e != cudaSuccess) return e;
+  if (dev != cached_dev) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_per_sm, kern, TT_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    cached_dev = dev;
+  }
+  int per_sm = cached_per_sm;
   int64_t grid = (int64_t)pl.nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > ta.items) grid = ta.items;
   kern<<<(unsigned)grid, TT_THREADS, smem, s>>>(map, cf, ta); eb::count_launch();
@@ -157,9 +247,7 @@ cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
     if ((e = cudaStreamWaitEvent(pl->side, pl->fork, 0))) return e;
   }
   if (a.n_irr > 0) {
-    int64_t nb2 = (a.n_irr + 255) / 256;
-    k_apply_irregular<T><<<(unsigned)nb2, 256, a.nfoot * 4, fork ? pl->side : s>>>(a); eb::count_launch();
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_irregular<T>(a, fork ? pl->side : s))) return e;
   }
   if ((e = launch_template_pass<T>(a, s))) return e;
   if (fork) {

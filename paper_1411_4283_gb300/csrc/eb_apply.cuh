@@ -32,6 +32,7 @@ struct ApplyArgs {
 struct ApplyPlan {
   int nx, ny, nz, dim, R;
   int tma32, tma64;              // template pass by TMA tiles possible (box metric, aligned rows)
+  int seg;                       // box footprint: irregular rows by x-contiguous segments
   std::vector<float> cube32;     // dense (2R+3)^3 template coefficients
   std::vector<double> cube64;
   int32_t* err;                  // device error word (bounded waits)

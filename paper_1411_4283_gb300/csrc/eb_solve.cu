@@ -52,35 +52,8 @@ __global__ void k_dots(int64_t n, const T* a0, const T* b0, const T* a1, const T
   }
 }
 
-// p = r + beta (p - omega v); phat = dinv p
-template <typename T>
-__global__ void k_bicg_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* dinv, double beta, double omega) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T pi = r[i] + (T)beta * (p[i] - (T)omega * v[i]);
-    p[i] = pi;
-    ph[i] = dinv[i] * pi;
-  }
-}
 
-// s = r - alpha v; shat = dinv s
-template <typename T>
-__global__ void k_bicg_s(int64_t n, const T* r, const T* v, T* s, T* sh, const T* dinv, double alpha) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T si = r[i] - (T)alpha * v[i];
-    s[i] = si;
-    sh[i] = dinv[i] * si;
-  }
-}
 
-// x += alpha phat + omega shat; r = s - omega t
-template <typename T>
-__global__ void k_bicg_x(int64_t n, T* x, const T* ph, const T* sh, T* r, const T* s, const T* t, double alpha,
-                         double omega) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += (T)alpha * ph[i] + (T)omega * sh[i];
-    r[i] = s[i] - (T)omega * t[i];
-  }
-}
 
 // r = b - y (FP64), on volumes only
 __global__ void k_resid64(int64_t n, const double* b, const double* y, double* r) {
@@ -206,46 +179,175 @@ static cudaError_t dots(int64_t n, const T* a0, const T* b0, const T* a1, const 
   return cudaStreamSynchronize(s);
 }
 
-// Jacobi-preconditioned BiCGStab on A x = b (x in/out).  Returns iterations
-// used; *relres = ||b - A x|| / ||b|| as tracked by the recurrence.
-// device time of every operator apply issued by the solver (CUDA events on the solve stream)
+// Device time of every operator apply issued by the solver, from CUDA events
+// on the solve stream.  Event pairs are read back lazily (at the next use of
+// the same pair, by which time the solver's per-iteration synchronisation has
+// completed them), so timing adds no synchronisation of its own.
 struct ApplyTimer {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0[4] = {}, e1[4] = {};
+  bool pending[4] = {false, false, false, false};
+  int next = 0;
   double ms = 0.0;
   long long n = 0;
+  void collect(int k) {
+    if (!pending[k]) return;
+    cudaEventSynchronize(e1[k]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0[k], e1[k]);
+    ms += t;
+    n += 1;
+    pending[k] = false;
+  }
 };
 static ApplyTimer* g_timer = nullptr;
 void set_apply_timer(void* t) { g_timer = (ApplyTimer*)t; }
 void* new_apply_timer() {
   ApplyTimer* t = new ApplyTimer();
-  cudaEventCreate(&t->e0);
-  cudaEventCreate(&t->e1);
+  for (int k = 0; k < 4; ++k) {
+    cudaEventCreate(&t->e0[k]);
+    cudaEventCreate(&t->e1[k]);
+  }
   return t;
 }
 void free_apply_timer(void* p, double* ms, long long* n) {
   ApplyTimer* t = (ApplyTimer*)p;
   if (!t) return;
+  for (int k = 0; k < 4; ++k) t->collect(k);
   *ms = t->ms;
   *n = t->n;
-  cudaEventDestroy(t->e0);
-  cudaEventDestroy(t->e1);
+  for (int k = 0; k < 4; ++k) {
+    cudaEventDestroy(t->e0[k]);
+    cudaEventDestroy(t->e1[k]);
+  }
   delete t;
 }
 
 template <typename T>
 static cudaError_t timed_apply(const ApplyArgs<T>& A, cudaStream_t s) {
   if (!g_timer) return launch_apply<T>(A, s);
-  cudaEventRecord(g_timer->e0, s);
+  int k = g_timer->next;
+  g_timer->next = (k + 1) & 3;
+  g_timer->collect(k);
+  cudaEventRecord(g_timer->e0[k], s);
   cudaError_t e = launch_apply<T>(A, s);
-  cudaEventRecord(g_timer->e1, s);
-  cudaEventSynchronize(g_timer->e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, g_timer->e0, g_timer->e1);
-  g_timer->ms += ms;
-  g_timer->n += 1;
+  cudaEventRecord(g_timer->e1[k], s);
+  g_timer->pending[k] = true;
   return e;
 }
 
+// Device-resident BiCGStab scalars (FP64): slots of the running dot products
+enum { SC_RHO0 = 0, SC_RHO1 = 1, SC_RV = 2, SC_TS = 3, SC_TT = 4, SC_RR = 5, SC_BB = 6, SC_N = 8 };
+
+__device__ __forceinline__ void block_accumulate(double v, double* dst, double* sh) {
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) atomicAdd(dst, v);
+}
+
+// p = r + beta (p - omega v), beta = (rho_i / rho_{i-1}) (alpha / omega); phat = dinv p.
+// Also clears the slot of (rhat, v) for this iteration.
+template <typename T>
+__global__ void k_bs_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* dinv, double* sc, int q, int first,
+                       const double* ao) {
+  double beta = 0.0, omega = 0.0;
+  if (!first) {
+    double rho = sc[q], rho_old = sc[1 - q];
+    beta = (rho / rho_old) * (ao[0] / ao[1]);
+    omega = ao[1];
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T pi = first ? r[i] : r[i] + (T)beta * (p[i] - (T)omega * v[i]);
+    p[i] = pi;
+    ph[i] = dinv[i] * pi;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_RV] = 0.0;
+}
+
+// (rhat, v) -> sc[SC_RV]
+template <typename T>
+__global__ void k_bs_dot_rv(int64_t n, const T* rh, const T* v, double* sc) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += (double)rh[i] * (double)v[i];
+  block_accumulate(a, sc + SC_RV, sh);
+}
+
+// alpha = rho_i / (rhat, v); s = r - alpha v; shat = dinv s.  Clears the slots filled later this iteration.
+template <typename T>
+__global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T* dinv, double* sc, int q, double* ao) {
+  double alpha = sc[q] / sc[SC_RV];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T si = r[i] - (T)alpha * v[i];
+    s[i] = si;
+    shv[i] = dinv[i] * si;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ao[0] = alpha;
+    sc[SC_TS] = 0.0;
+    sc[SC_TT] = 0.0;
+    sc[1 - q] = 0.0;
+    sc[SC_RR] = 0.0;
+  }
+}
+
+// (t, s) -> TS, (t, t) -> TT
+template <typename T>
+__global__ void k_bs_dot_ts(int64_t n, const T* t, const T* s, double* sc) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double ti = (double)t[i];
+    a += ti * (double)s[i];
+    b += ti * ti;
+  }
+  block_accumulate(a, sc + SC_TS, sh);
+  __syncthreads();
+  block_accumulate(b, sc + SC_TT, sh);
+}
+
+// omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t; rho_{i+1} = (rhat, r); (r, r)
+template <typename T>
+__global__ void k_bs_x(int64_t n, T* x, const T* ph, const T* shv, T* r, const T* s, const T* t, const T* rh,
+                       double* sc, int q, double* ao) {
+  __shared__ double sh[32];
+  double alpha = ao[0];
+  double omega = sc[SC_TT] > 0.0 ? sc[SC_TS] / sc[SC_TT] : 0.0;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (T)alpha * ph[i] + (T)omega * shv[i];
+    T ri = s[i] - (T)omega * t[i];
+    r[i] = ri;
+    a += (double)rh[i] * (double)ri;
+    b += (double)ri * (double)ri;
+  }
+  block_accumulate(a, sc + (1 - q), sh);
+  __syncthreads();
+  block_accumulate(b, sc + SC_RR, sh);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ao[1] = omega;
+}
+
+// r = b - r (in place, r holds A x); rhat = r; p = v = 0; rho_0 = (r, r) -> sc[0]; (b, b) -> sc[SC_BB]
+template <typename T>
+__global__ void k_bs_init(int64_t n, const T* bvec, T* r, T* rh, T* p, T* v, double* sc) {
+  __shared__ double sh[32];
+  double a = 0.0, bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ri = bvec[i] - r[i];
+    r[i] = ri;
+    rh[i] = ri;
+    p[i] = (T)0;
+    v[i] = (T)0;
+    a += (double)ri * (double)ri;
+    bb += (double)bvec[i] * (double)bvec[i];
+  }
+  block_accumulate(a, sc + SC_RHO0, sh);
+  __syncthreads();
+  block_accumulate(bb, sc + SC_BB, sh);
+}
+
+// Jacobi-preconditioned BiCGStab on A x = b (x in/out), scalars kept on the
+// device; the host reads ||r||^2 once per iteration.  Returns iterations used
+// and the recurrence's relative residual.
 template <typename T>
 cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T* work, int64_t n, double tol,
                      int maxit, double* dscr, int* iters, double* relres, cudaStream_t s) {
@@ -257,48 +359,42 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
   T* sv = work + 5 * n;
   T* shv = work + 6 * n;
   T* t = work + 7 * n;
+  double* sc = dscr;        // SC_N slots
+  double* ao = dscr + SC_N;  // alpha, omega
   ApplyArgs<T> A = A0;
   cudaError_t e;
-  double h[3];
-  // r = b - A x
-  A.phi = x; A.y = r;
+  const unsigned G = grid_for(n);
+  if ((e = cudaMemsetAsync(dscr, 0, (SC_N + 2) * sizeof(double), s))) return e;
+  A.phi = x;
+  A.y = r;
   if ((e = timed_apply<T>(A, s))) return e;
-  k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, b, r, r, rh, dinv, 1.0); eb::count_launch();  // r = b - Ax (rh scratch)
-  k_copy<T><<<grid_for(n), VB, 0, s>>>(n, r, rh); eb::count_launch();
-  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, p, (T)0); eb::count_launch();
-  k_fill<T><<<grid_for(n), VB, 0, s>>>(n, v, (T)0); eb::count_launch();
-  if ((e = dots<T>(n, b, b, r, r, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
-  double bn = sqrt(h[0]);
+  k_bs_init<T><<<G, VB, 0, s>>>(n, b, r, rh, p, v, sc); eb::count_launch();
+  double h[SC_N];
+  if ((e = cudaMemcpyAsync(h, sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  double bn = sqrt(h[SC_BB]);
   if (bn == 0.0) bn = 1.0;
-  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
-  double rn = sqrt(h[1]);
-  *relres = rn / bn;
+  *relres = sqrt(h[SC_RHO0]) / bn;
   int it = 0;
   if (*relres <= tol) { *iters = 0; return cudaSuccess; }
   for (it = 1; it <= maxit; ++it) {
-    if ((e = dots<T>(n, rh, r, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
-      return e;
-    double rho = h[0];
-    if (rho == 0.0) break;
-    double beta = (rho / rho_old) * (alpha / omega);
-    k_bicg_p<T><<<grid_for(n), VB, 0, s>>>(n, r, v, p, ph, dinv, it == 1 ? 0.0 : beta, omega); eb::count_launch();
-    A.phi = ph; A.y = v;
+    int q = (it - 1) & 1;
+    k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, dinv, sc, q, it == 1, ao); eb::count_launch();
+    A.phi = ph;
+    A.y = v;
     if ((e = timed_apply<T>(A, s))) return e;
-    if ((e = dots<T>(n, rh, v, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
-      return e;
-    if (h[0] == 0.0) break;
-    alpha = rho / h[0];
-    k_bicg_s<T><<<grid_for(n), VB, 0, s>>>(n, r, v, sv, shv, dinv, alpha); eb::count_launch();
-    A.phi = shv; A.y = t;
+    k_bs_dot_rv<T><<<G, VB, 0, s>>>(n, rh, v, sc); eb::count_launch();
+    k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, dinv, sc, q, ao); eb::count_launch();
+    A.phi = shv;
+    A.y = t;
     if ((e = timed_apply<T>(A, s))) return e;
-    if ((e = dots<T>(n, t, sv, t, t, (const T*)nullptr, (const T*)nullptr, dscr, h, 2, s))) return e;
-    omega = h[1] > 0 ? h[0] / h[1] : 0.0;
-    k_bicg_x<T><<<grid_for(n), VB, 0, s>>>(n, x, ph, shv, r, sv, t, alpha, omega); eb::count_launch();
-    rho_old = rho;
-    if ((e = dots<T>(n, r, r, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, dscr, h, 1, s)))
-      return e;
-    *relres = sqrt(h[0]) / bn;
-    if (*relres <= tol || omega == 0.0) break;
+    k_bs_dot_ts<T><<<G, VB, 0, s>>>(n, t, sv, sc); eb::count_launch();
+    k_bs_x<T><<<G, VB, 0, s>>>(n, x, ph, shv, r, sv, t, rh, sc, q, ao); eb::count_launch();
+    if ((e = cudaMemcpyAsync(h, sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    *relres = sqrt(h[SC_RR]) / bn;
+    if (!(*relres > tol)) break;                       // converged (or NaN: stop)
+    if (h[1 - q] == 0.0 || h[SC_TT] == 0.0) break;     // breakdown
   }
   *iters = it > maxit ? maxit : it;
   return cudaGetLastError();
