@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 GPU solve once")
     p.add_argument("--out", default=None)
+    p.add_argument("--mode", default="step", choices=["step", "build", "apply"],
+                   help="build: one stencil build and exit; apply: build plus 3 FP32 applies (profiling cases)")
     return p.parse_args()
 
 
@@ -211,6 +213,17 @@ def main():
     g_wall = torch.tensor(gw_h, device=dev)
     volmask = torch.tensor((g.flag > 0).astype(np.float64), device=dev)
     stream = torch.cuda.current_stream()
+    if args.mode != "step":
+        st = P.eb_build_stencils(dg, order=args.order)
+        if args.mode == "apply":
+            import eb_inputs as E
+            x = torch.tensor(E.seeded_field(3, g.ncell), dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                P.eb_apply(st, x, y, kappa_weighted=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": args.mode, "n": args.n, "build_info": st.info}))
+        return
 
     def step(time_applies=False):
         st = P.eb_build_stencils(dg, order=args.order)

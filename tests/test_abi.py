@@ -1,0 +1,71 @@
+"""The C ABI: every function include/eb.h declares is exported by the built library (no GPU needed),
+struct layouts of the binding match the header, and the product path refuses to run without its
+library (there is no CPU fallback)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "eb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eb_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_4283_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "eb_build_stencils" in names and "eb_solve" in names and "eb_lsq_batch_noalloc" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    import paper_1411_4283_gb300 as P
+    c = tmp_path / "sz.c"
+    c.write_text('#include <stdio.h>\n#include "%s"\nint main(){printf("%%zu %%zu %%zu %%zu %%zu\\n", sizeof(eb_geom), '
+                 'sizeof(eb_params), sizeof(eb_build_info), sizeof(eb_solve_opts), sizeof(eb_solve_info));}\n'
+                 % os.path.join(ROOT, "include", "eb.h"))
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", str(c), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(t) for t in (P.EbGeom, P.EbParams, P.EbBuildInfo, P.EbSolveOpts, P.EbSolveInfo)]
+    assert got == want
+
+
+def test_status_strings(lib):
+    lib.eb_status_string.restype = ctypes.c_char_p
+    assert lib.eb_status_string(0) == b"ok"
+    assert b"rank" in lib.eb_status_string(2)
+    lib.eb_abi_version.restype = ctypes.c_int32
+    assert lib.eb_abi_version() == 1
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    """Argument checks run before any CUDA call: a NULL descriptor and an oversized no-alloc
+    request are refused with their status codes."""
+    import paper_1411_4283_gb300 as P
+    P.load()
+    h = ctypes.c_void_p()
+    assert P._LIB.eb_build_stencils(None, None, ctypes.byref(h), None, None) == 1
+    assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 15, 300, None, None, None) == 8
+    assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 40, 10, None, None, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_1411_4283_gb300 as P
+    monkeypatch.setattr(P, "_LIB", None)
+    monkeypatch.setattr(P._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        P.load()
