@@ -137,6 +137,7 @@ typedef struct eb_solve_opts {
   int32_t max_outer;      /* refinement sweeps (mixed) */
   int32_t max_iters;      /* total iteration cap */
   int32_t check_every;    /* < 0: time every Krylov operator apply with CUDA events (eb_solve_info.apply_ms) */
+  int32_t precond;        /* 0: Jacobi (kappa-weighted diagonal); 1: geometric multigrid V-cycle (default) */
 } eb_solve_opts;
 
 typedef struct eb_solve_info {

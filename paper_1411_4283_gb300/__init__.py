@@ -56,7 +56,8 @@ class EbBuildInfo(ctypes.Structure):
 
 class EbSolveOpts(ctypes.Structure):
     _fields_ = [("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_inner", ctypes.c_int32),
-                ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("precond", ctypes.c_int32)]
 
 
 class EbSolveInfo(ctypes.Structure):
@@ -242,9 +243,11 @@ def eb_bc_rhs(st: Stencils, g_eb, g_wall, Bg, kappa_weighted=True, stream=None):
 
 
 def eb_solve(st: Stencils, rho, g_eb, g_wall, phi, tol=1e-12, mixed=True, inner_tol=1e-5, max_inner=20000,
-             max_outer=40, max_iters=400000, stream=None, allow_not_converged=False, time_applies=False) -> dict:
+             max_outer=40, max_iters=400000, stream=None, allow_not_converged=False, time_applies=False,
+             precond="mg") -> dict:
     lib = load()
-    o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, -1 if time_applies else 1)
+    o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, -1 if time_applies else 1,
+                    {"jacobi": 0, "mg": 1}[precond])
     info = EbSolveInfo()
     code = lib.eb_solve(st.handle, _ptr(rho), _ptr(g_eb), _ptr(g_wall), tol, ctypes.byref(o), _ptr(phi),
                         ctypes.byref(info), _stream(stream))

@@ -345,6 +345,10 @@ void eb_stencils_destroy(eb_stencils* st) {
     if (st->plan->join) cudaEventDestroy(st->plan->join);
     delete st->plan;
   }
+  if (st->mg) {
+    mg_free(st->mg);
+    delete st->mg;
+  }
   for (void* p : st->allocs) cudaFree(p);
   delete st;
 }
@@ -1073,7 +1077,8 @@ eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, e
 eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
                    const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream) {
   if (!st || !rho || !phi) { set_error("null argument"); return EB_ERR_INVALID; }
-  eb_solve_opts o = {1, 1e-5, 20000, 30, 200000, 1};
+  g_err.clear();
+  eb_solve_opts o = {1, 1e-5, 20000, 30, 200000, 1, 1};
   if (opts) o = *opts;
   eb_solve_info loc;
   memset(&loc, 0, sizeof(loc));
@@ -1095,6 +1100,33 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
   if (bnorm == 0.0) bnorm = 1.0;
   ApplyArgs<double> A64 = apply_args<double>(st, 1);
   eb_status ret = EB_OK;
+  const Multigrid* mg = nullptr;
+  if (o.precond == 1) {
+    if (!st->mg) {
+      Multigrid* m = new Multigrid();
+      MgFineInput in;
+      in.dim = st->dm.dim;
+      for (int d = 0; d < 3; ++d) in.n[d] = st->dm.n[d];
+      in.h = st->dm.h;
+      in.flag = st->flag;
+      for (int d = 0; d < 3; ++d) {
+        int dd = d < st->dm.dim ? d : 0;
+        in.ff[d] = st->face_flag[dd];
+        in.cf[d] = st->cutface_of[dd];
+        in.fm[d] = st->face_mom[dd];
+      }
+      in.KFS = st->dm.KFS;
+      in.dinv_high = st->dinv64;
+      cudaError_t me = mg_setup(in, m, s);
+      if (me != cudaSuccess) {
+        mg_free(m);
+        delete m;
+        return cuda_status(me, "multigrid setup");
+      }
+      const_cast<eb_stencils*>(st)->mg = m;
+    }
+    mg = st->mg;
+  }
   void* timer = o.check_every < 0 ? new_apply_timer() : nullptr;  // check_every < 0: time every Krylov apply
   set_apply_timer(timer);
   struct TimerGuard {
@@ -1132,10 +1164,15 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
       int it = 0;
       double rr = 0.0;
       int cap = std::min(o.max_inner, o.max_iters - total);
-      EB_CUDA(bicgstab<float>(A32, b32, x32, st->dinv32, w32, n, o.inner_tol, cap, dscr, &it, &rr, s));
+      EB_CUDA(bicgstab<float>(A32, b32, x32, st->dinv32, w32, n, o.inner_tol, cap, dscr, &it, &rr, s, mg));
       total += it;
-      EB_CUDA(add32(n, phi, rn, x32, s));
       inf->sweeps = sweep + 1;
+      if (!isfinite(rr)) {  // an FP32 breakdown produced no usable correction: stop, phi unchanged
+        ret = EB_ERR_NOT_CONVERGED;
+        set_error("FP32 inner solve broke down (non-finite residual)");
+        break;
+      }
+      EB_CUDA(add32(n, phi, rn, x32, s));
     }
     inf->iterations = total;
   } else {
@@ -1143,7 +1180,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
     EB_TRY(tmp.get(&w64, 8 * n));
     int it = 0;
     double rr = 0.0;
-    EB_CUDA(bicgstab<double>(A64, rhs, phi, st->dinv64, w64, n, tol, o.max_iters, dscr, &it, &rr, s));
+    EB_CUDA(bicgstab<double>(A64, rhs, phi, st->dinv64, w64, n, tol, o.max_iters, dscr, &it, &rr, s, mg));
     inf->iterations = it;
     A64.phi = phi;
     A64.y = y64;
@@ -1162,7 +1199,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
     EB_CUDA(cudaMemcpy(&h, st->plan->err, 4, cudaMemcpyDeviceToHost));
     if (h) { set_error("a bounded device wait gave up in the operator apply"); return EB_ERR_TIMEOUT; }
   }
-  if (ret != EB_OK) set_error("solve did not reach the requested tolerance");
+  if (ret != EB_OK && g_err.empty()) set_error("solve did not reach the requested tolerance");
   return ret;
 }
 

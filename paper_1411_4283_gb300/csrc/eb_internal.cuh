@@ -11,6 +11,7 @@
 
 #include "../../include/eb.h"
 #include "eb_apply.cuh"
+#include "eb_mg.cuh"
 
 namespace eb {
 
@@ -108,6 +109,7 @@ struct eb_stencils {
   int64_t* wall_ids = nullptr;      // device
   std::vector<int64_t> wall_ids_host;
   eb::ApplyPlan* plan = nullptr;
+  eb::Multigrid* mg = nullptr;     // geometric multigrid preconditioner (built at the first solve)
   int64_t* b_wpos = nullptr;       // [nnz(B)] position of a wall column in the wall list (-1: EB)
   double* dinv64 = nullptr;         // [ncell] inverse diagonal of kappa L (0 on covered cells)
   float* dinv32 = nullptr;

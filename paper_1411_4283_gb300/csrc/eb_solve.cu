@@ -14,6 +14,7 @@
 #include "eb_apply.cuh"
 #include "eb_internal.cuh"
 #include "eb_solve.cuh"
+#include "eb_mg.cuh"
 
 namespace eb {
 
@@ -251,8 +252,8 @@ __global__ void k_bs_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* 
   double beta = 0.0, omega = 0.0;
   if (!first) {
     double rho = sc[q], rho_old = sc[1 - q];
-    beta = (rho / rho_old) * (ao[0] / ao[1]);
     omega = ao[1];
+    beta = (rho_old != 0.0 && omega != 0.0) ? (rho / rho_old) * (ao[0] / omega) : 0.0;
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T pi = first ? r[i] : r[i] + (T)beta * (p[i] - (T)omega * v[i]);
@@ -275,7 +276,8 @@ __global__ void k_bs_dot_rv(int64_t n, const T* rh, const T* v, double* sc) {
 // alpha = rho_i / (rhat, v); s = r - alpha v; shat = dinv s.  Clears the slots filled later this iteration.
 template <typename T>
 __global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T* dinv, double* sc, int q, double* ao) {
-  double alpha = sc[q] / sc[SC_RV];
+  double rv = sc[SC_RV];
+  double alpha = rv != 0.0 ? sc[q] / rv : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T si = r[i] - (T)alpha * v[i];
     s[i] = si;
@@ -350,7 +352,7 @@ __global__ void k_bs_init(int64_t n, const T* bvec, T* r, T* rh, T* p, T* v, dou
 // and the recurrence's relative residual.
 template <typename T>
 cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T* work, int64_t n, double tol,
-                     int maxit, double* dscr, int* iters, double* relres, cudaStream_t s) {
+                     int maxit, double* dscr, int* iters, double* relres, cudaStream_t s, const Multigrid* mg) {
   T* r = work;
   T* rh = work + n;
   T* p = work + 2 * n;
@@ -380,11 +382,13 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
   for (it = 1; it <= maxit; ++it) {
     int q = (it - 1) & 1;
     k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, dinv, sc, q, it == 1, ao); eb::count_launch();
+    if (mg && (e = mg_precond<T>(*mg, p, ph, s))) return e;  // phat = V-cycle(p) instead of Jacobi
     A.phi = ph;
     A.y = v;
     if ((e = timed_apply<T>(A, s))) return e;
     k_bs_dot_rv<T><<<G, VB, 0, s>>>(n, rh, v, sc); eb::count_launch();
     k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, dinv, sc, q, ao); eb::count_launch();
+    if (mg && (e = mg_precond<T>(*mg, sv, shv, s))) return e;
     A.phi = shv;
     A.y = t;
     if ((e = timed_apply<T>(A, s))) return e;
@@ -393,17 +397,17 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
     if ((e = cudaMemcpyAsync(h, sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
     if ((e = cudaStreamSynchronize(s))) return e;
     *relres = sqrt(h[SC_RR]) / bn;
-    if (!(*relres > tol)) break;                       // converged (or NaN: stop)
-    if (h[1 - q] == 0.0 || h[SC_TT] == 0.0) break;     // breakdown
+    if (!(*relres > tol)) break;                                    // converged (or NaN: stop)
+    if (h[1 - q] == 0.0 || h[SC_TT] == 0.0 || h[SC_RV] == 0.0) break;  // breakdown
   }
   *iters = it > maxit ? maxit : it;
   return cudaGetLastError();
 }
 
 template cudaError_t bicgstab<float>(const ApplyArgs<float>&, const float*, float*, const float*, float*, int64_t,
-                                     double, int, double*, int*, double*, cudaStream_t);
+                                     double, int, double*, int*, double*, cudaStream_t, const Multigrid*);
 template cudaError_t bicgstab<double>(const ApplyArgs<double>&, const double*, double*, const double*, double*,
-                                      int64_t, double, int, double*, int*, double*, cudaStream_t);
+                                      int64_t, double, int, double*, int*, double*, cudaStream_t, const Multigrid*);
 
 cudaError_t resid64(int64_t n, const double* b, const double* y, double* r, cudaStream_t s) {
   k_resid64<<<grid_for(n), VB, 0, s>>>(n, b, y, r); eb::count_launch();

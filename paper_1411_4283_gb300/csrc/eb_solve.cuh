@@ -3,6 +3,7 @@
 #include <stdint.h>
 
 #include "eb_apply.cuh"
+#include "eb_mg.cuh"
 
 namespace eb {
 
@@ -16,7 +17,7 @@ cudaError_t launch_norms(int64_t n, const uint8_t* flag, const double* kappa, co
                          cudaStream_t s);
 template <typename T>
 cudaError_t bicgstab(const ApplyArgs<T>& A, const T* b, T* x, const T* dinv, T* work, int64_t n, double tol,
-                     int maxit, double* dscr, int* iters, double* relres, cudaStream_t s);
+                     int maxit, double* dscr, int* iters, double* relres, cudaStream_t s, const Multigrid* mg);
 cudaError_t resid64(int64_t n, const double* b, const double* y, double* r, cudaStream_t s);
 cudaError_t to32(int64_t n, const double* a, double scale, float* o, cudaStream_t s);
 cudaError_t add32(int64_t n, double* x, double scale, const float* d, cudaStream_t s);

@@ -93,15 +93,15 @@ def test_bc_rhs_2d(circle32):
     assert np.all(np.abs(Bg.cpu().numpy() - bo) <= bound + 1e-300)
 
 
-@pytest.mark.parametrize("mixed", [True, False])
-def test_solve_2d(circle32, mixed):
+@pytest.mark.parametrize("mixed,precond", [(True, "mg"), (False, "mg"), (True, "jacobi"), (False, "jacobi")])
+def test_solve_2d(circle32, mixed, precond):
     import torch
     import paper_1411_4283_gb300 as P
     g, man, ref = circle32
     st, _ = build_gpu(g)
     gw, ge, _ = split_boundary(ref["oracle"], ref["G"])
     x = torch.zeros(g.ncell, dtype=torch.float64, device="cuda")
-    info = P.eb_solve(st, to_dev(ref["rho"]), to_dev(ge), to_dev(gw), x, tol=1e-12, mixed=mixed)
+    info = P.eb_solve(st, to_dev(ref["rho"]), to_dev(ge), to_dev(gw), x, tol=1e-12, mixed=mixed, precond=precond)
     xo = ref["phi"]
     assert np.abs(x.cpu().numpy() - xo).max() <= 1e-9 * np.abs(xo).max(), info
     err = x - to_dev(ref["Phi"])
