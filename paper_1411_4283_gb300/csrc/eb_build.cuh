@@ -38,6 +38,7 @@ struct LsWarpSmem {
   double P[32 * KST];     // partial dot products / per-lane scratch
   double vec[5 * MAXK];   // F, y, z, tau, 1/R_kk
 };
+static_assert(sizeof(LsWarpSmem) % 16 == 0, "per-warp blocks stay 16-byte aligned");
 
 // offsets in units of h/2 span [-11, 11] on each axis (volume, EB and wall rows)
 constexpr int TAB_S = 23;
