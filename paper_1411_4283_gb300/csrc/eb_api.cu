@@ -31,6 +31,9 @@ static thread_local std::vector<int64_t> g_bad_faces;
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
 void set_error(const std::string& msg) { g_err = msg; }
 eb_status cuda_status(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);

@@ -136,5 +136,8 @@ eb_status cuda_status(cudaError_t e, const char* what);
 std::vector<std::vector<int>> monomials(int dim, int q);
 // cumulative number of kernel launches issued by the library (all threads)
 void count_launch();
+void count_launches(long long n);
+void uncount_launches(long long n);
+long long launches_so_far();
 
 }  // namespace eb

@@ -217,6 +217,103 @@ __global__ void k_mg_prolong(int dim, int nxf, int nyf, int nzf, int nxc, int ny
   xf[c] += xc[cc];
 }
 
+// The levels from `l0` down, when small, in one CTA: the same V-cycle with
+// block-wide barriers instead of kernel boundaries.
+template <typename T>
+struct MgDev {
+  int n[3];
+  const float* cp[3];
+  const float* dg;
+  T* b;
+  T* x;
+  T* w;
+};
+
+template <typename T>
+__device__ void cta_jacobi(int dim, const MgDev<T>& L, const T* x, T* out, float om) {
+  int64_t n = (int64_t)L.n[0] * L.n[1] * L.n[2];
+  for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    float d = L.dg[c];
+    if (d == 0.0f) { out[c] = (T)0; continue; }
+    if (!x) { out[c] = (T)om * L.b[c] / (T)d; continue; }
+    int p[3];
+    xyz_of(c, L.n[0], L.n[1], p);
+    T r = L.b[c] - mg_apply_at<T>(dim, L.n[0], L.n[1], L.n[2], c, p, L.cp[0], L.cp[1], L.cp[2], L.dg, x);
+    out[c] = x[c] + (T)om * r / (T)d;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_coarse(int dim, int nlev, const MgDev<T>* __restrict__ lev, float om,
+                                                    int nu, int ncoarse) {
+  // per-thread copies of the ping-pong pointers (identical in every thread)
+  T* xs[MG_MAXLEV];
+  T* ws[MG_MAXLEV];
+  for (int l = 0; l < nlev; ++l) {
+    xs[l] = lev[l].x;
+    ws[l] = lev[l].w;
+  }
+  for (int l = 0; l < nlev; ++l) {  // descend
+    MgDev<T> L = lev[l];
+    const bool last = l == nlev - 1;
+    const int sweeps = last ? ncoarse : nu;
+    cta_jacobi<T>(dim, L, nullptr, xs[l], om);
+    __syncthreads();
+    for (int it = 1; it < sweeps; ++it) {
+      cta_jacobi<T>(dim, L, xs[l], ws[l], om);
+      __syncthreads();
+      T* t = xs[l]; xs[l] = ws[l]; ws[l] = t;
+    }
+    if (!last) {
+      MgDev<T> C = lev[l + 1];
+      int64_t ncc = (int64_t)C.n[0] * C.n[1] * C.n[2];
+      const int nch = 1 << dim;
+      for (int64_t c = threadIdx.x; c < ncc; c += blockDim.x) {
+        int X[3];
+        xyz_of(c, C.n[0], C.n[1], X);
+        T acc = (T)0;
+        for (int k = 0; k < nch; ++k) {
+          int f[3] = {0, 0, 0};
+          bool in = true;
+          for (int d = 0; d < dim; ++d) {
+            f[d] = 2 * X[d] + ((k >> d) & 1);
+            if (f[d] >= L.n[d]) in = false;
+          }
+          if (!in) continue;
+          int64_t fc = (int64_t)f[0] + (int64_t)L.n[0] * ((int64_t)f[1] + (int64_t)L.n[1] * f[2]);
+          if (L.dg[fc] == 0.0f) continue;
+          acc += L.b[fc] - mg_apply_at<T>(dim, L.n[0], L.n[1], L.n[2], fc, f, L.cp[0], L.cp[1], L.cp[2], L.dg, xs[l]);
+        }
+        C.b[c] = acc / (T)nch;
+      }
+      __syncthreads();
+    }
+  }
+  for (int l = nlev - 2; l >= 0; --l) {  // ascend
+    MgDev<T> L = lev[l];
+    MgDev<T> C = lev[l + 1];
+    int64_t n = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      if (L.dg[c] == 0.0f) continue;
+      int p[3];
+      xyz_of(c, L.n[0], L.n[1], p);
+      int64_t cc = (int64_t)(p[0] >> 1) + (int64_t)C.n[0] * ((int64_t)(p[1] >> 1) + (int64_t)C.n[1] * (dim == 3 ? (p[2] >> 1) : 0));
+      xs[l][c] += xs[l + 1][cc];
+    }
+    __syncthreads();
+    for (int it = 0; it < nu; ++it) {
+      cta_jacobi<T>(dim, L, xs[l], ws[l], om);
+      __syncthreads();
+      T* t = xs[l]; xs[l] = ws[l]; ws[l] = t;
+    }
+  }
+  // the group's result belongs in level 0's x buffer
+  if (xs[0] != lev[0].x) {
+    int64_t n = (int64_t)lev[0].n[0] * lev[0].n[1] * lev[0].n[2];
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) lev[0].x[c] = xs[0][c];
+  }
+}
+
 static unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
@@ -256,10 +353,29 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
     if (mn <= 4) break;
     for (int d = 0; d < in.dim; ++d) n[d] = (n[d] + 1) / 2;
   }
-  return cudaSuccess;
+  // device descriptors of every level for the single-CTA coarse cycle
+  MgDev<float> h32[MG_MAXLEV];
+  MgDev<double> h64[MG_MAXLEV];
+  for (int l = 0; l < mg->nlev; ++l) {
+    MgLevel& L = mg->lev[l];
+    for (int d = 0; d < 3; ++d) { h32[l].n[d] = L.n[d]; h64[l].n[d] = L.n[d]; h32[l].cp[d] = L.cp[d]; h64[l].cp[d] = L.cp[d]; }
+    h32[l].dg = L.dg; h64[l].dg = L.dg;
+    h32[l].b = L.v32[0]; h32[l].x = L.v32[1]; h32[l].w = L.v32[2];
+    h64[l].b = L.v64[0]; h64[l].x = L.v64[1]; h64[l].w = L.v64[2];
+  }
+  if ((e = cudaMalloc(&mg->dev32, sizeof(h32)))) return e;
+  if ((e = cudaMalloc(&mg->dev64, sizeof(h64)))) return e;
+  if ((e = cudaMemcpyAsync(mg->dev32, h32, sizeof(h32), cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(mg->dev64, h64, sizeof(h64), cudaMemcpyHostToDevice, s))) return e;
+  return cudaStreamSynchronize(s);
 }
 
 void mg_free(Multigrid* mg) {
+  if (mg->dev32) cudaFree(mg->dev32);
+  if (mg->dev64) cudaFree(mg->dev64);
+  mg->dev32 = mg->dev64 = nullptr;
+  for (int k = 0; k < 2; ++k)
+    if (mg->exec[k]) { cudaGraphExecDestroy(mg->exec[k]); mg->exec[k] = nullptr; }
   for (int l = 0; l < mg->nlev; ++l) {
     MgLevel& L = mg->lev[l];
     for (int d = 0; d < 3; ++d) cudaFree(L.cp[d]);
@@ -280,11 +396,19 @@ template <>
 double* vbuf<double>(MgLevel& L, int k) { return L.v64[k]; }
 
 // z = V(b) on level l; b and z live in the level's buffers (0: b, 1: x, 2: work)
+constexpr int64_t MG_CTA_CELLS = 4096;  // levels at most this large run inside one CTA
+
 template <typename T>
 static cudaError_t vcycle(const Multigrid& mgc, int l, cudaStream_t s) {
   Multigrid& mg = const_cast<Multigrid&>(mgc);
   MgLevel& L = mg.lev[l];
   const int D = mg.dim;
+  if (L.ncell <= MG_CTA_CELLS) {
+    MgDev<T>* dev = sizeof(T) == 4 ? (MgDev<T>*)mg.dev32 : (MgDev<T>*)mg.dev64;
+    k_mg_coarse<T><<<1, 1024, 0, s>>>(D, mg.nlev - l, dev + l, 0.8f, MG_NU, 24);
+    eb::count_launch();
+    return cudaGetLastError();
+  }
   T* b = vbuf<T>(L, 0);
   T* x = vbuf<T>(L, 1);
   T* w = vbuf<T>(L, 2);
@@ -323,12 +447,35 @@ static cudaError_t vcycle(const Multigrid& mgc, int l, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The V-cycle works on the levels' fixed buffers, so it is captured once per
+// precision as a CUDA graph (on a private stream) and replayed; the input and
+// output copies stay outside the graph.
 template <typename T>
-cudaError_t mg_precond(const Multigrid& mg, const T* r, T* z, cudaStream_t s) {
-  MgLevel& L = const_cast<Multigrid&>(mg).lev[0];
-  cudaError_t e = cudaMemcpyAsync(vbuf<T>(L, 0), r, L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s);
-  if (e) return e;
-  if ((e = vcycle<T>(mg, 0, s))) return e;
+cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
+  Multigrid& mg = const_cast<Multigrid&>(mgc);
+  MgLevel& L = mg.lev[0];
+  const int k = sizeof(T) == 4 ? 0 : 1;
+  cudaError_t e;
+  if (!mg.exec[k]) {
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return e;
+    long long before = eb::launches_so_far();
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) { cudaStreamDestroy(cap); return e; }
+    cudaError_t ev = vcycle<T>(mg, 0, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (ev) return ev;
+    if (e) return e;
+    mg.nodes[k] = eb::launches_so_far() - before;
+    eb::uncount_launches(mg.nodes[k]);  // capture issued no work
+    e = cudaGraphInstantiate(&mg.exec[k], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) return e;
+  }
+  if ((e = cudaMemcpyAsync(vbuf<T>(L, 0), r, L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s))) return e;
+  if ((e = cudaGraphLaunch(mg.exec[k], s))) return e;
+  eb::count_launches(mg.nodes[k]);
   return cudaMemcpyAsync(z, vbuf<T>(L, 1), L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 

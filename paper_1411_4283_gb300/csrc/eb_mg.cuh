@@ -21,6 +21,10 @@ struct Multigrid {
   int dim = 0;
   int nlev = 0;
   MgLevel lev[MG_MAXLEV];
+  void* dev32 = nullptr;  // device descriptors of the levels (single-CTA coarse cycle)
+  void* dev64 = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // captured V-cycle (FP32, FP64)
+  long long nodes[2] = {0, 0};                    // kernels per replay
 };
 
 struct MgFineInput {
