@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--tol", type=float, default=0.0,
                    help="relative residual target; 0 = the loosest of 1e-7..1e-12 whose L_inf error is within "
                         "1.01x the error of the solve converged to 1e-12 (solve at fixed error), chosen in warm-up")
-    p.add_argument("--inner-tol", type=float, default=1e-4)
+    p.add_argument("--inner-tol", type=float, default=1e-5)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

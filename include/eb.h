@@ -137,7 +137,9 @@ typedef struct eb_solve_opts {
   int32_t max_outer;      /* refinement sweeps (mixed) */
   int32_t max_iters;      /* total iteration cap */
   int32_t check_every;    /* < 0: time every Krylov operator apply with CUDA events (eb_solve_info.apply_ms) */
-  int32_t precond;        /* 0: Jacobi (kappa-weighted diagonal); 1: geometric multigrid V-cycle (default) */
+  int32_t precond;        /* 0: Jacobi (kappa-weighted diagonal); 1 (default): geometric multigrid
+                             V-cycle followed by exact solves of the high-order operator on 3x3x3
+                             blocks around the cut cells whose diagonal is weak or positive (3-D) */
 } eb_solve_opts;
 
 typedef struct eb_solve_info {

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "eb_apply.cuh"
+#include "eb_apply_quad.cuh"
 #include "eb_internal.cuh"
 #include "eb_scan.cuh"
 #include "eb_solve.cuh"
@@ -280,6 +281,39 @@ __global__ void k_wall_pos(int64_t nnz, const int64_t* bcol, int64_t n_grid, con
   pos[k] = lo;
 }
 
+// irregular list -> cells with a unique row (by unique row) and cells with a class row (ascending)
+__global__ void k_flag_class(int64_t n_irr, const int32_t* irr_row, int64_t n_class, int32_t* flag) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_irr) flag[t] = irr_row[t] < n_class;
+}
+
+__global__ void k_split_irr(int64_t n_irr, const int32_t* irr_cell, const int32_t* irr_row, int64_t n_class,
+                            const int64_t* posC, int32_t* cellU, int32_t* cellC, int32_t* classC) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_irr) return;
+  const int32_t r = irr_row[t];
+  if (r >= n_class) {
+    cellU[r - n_class] = irr_cell[t];
+  } else {
+    cellC[posC[t]] = irr_cell[t];
+    classC[posC[t]] = r;
+  }
+}
+
+// canonical footprint-major unique rows -> quad layout (see eb_apply_quad.cuh); perm[e]: canonical
+// footprint index of apply-order entry e (-1: padding)
+template <typename T>
+__global__ void k_pack_quads(const T* __restrict__ rows, int64_t n_rows, const int16_t* __restrict__ perm, int nq,
+                             int64_t n_class, T* __restrict__ qU) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + n_class;
+  const int e = blockIdx.y;
+  if (r >= n_rows) return;
+  const int f = perm[e];
+  const T v = f >= 0 ? rows[(int64_t)f * n_rows + r] : (T)0;
+  const int64_t u = r - n_class;
+  qU[(((u >> 5) * nq + (e >> 2)) * 32 + (u & 31)) * 4 + (e & 3)] = v;
+}
+
 __global__ void k_diag_inv(int64_t ncell, const uint8_t* kind, const int32_t* irr_map_unused, const double* tmpl,
                            int center, double* dinv64, float* dinv32) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,6 +415,77 @@ eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_ste
     return r;
   }
   *out = st;
+  return EB_OK;
+}
+
+// apply order of the footprint for the quad layout (eb_apply_quad.cuh): groups of four wide segments,
+// groups of four narrow segments, the left-over wide segment, zero padding to a whole quad
+static std::vector<int16_t> quad_perm(int R, int box) {
+  const int L = R + 1, S = 2 * L + 1, W = 2 * R + 1;
+  std::vector<int16_t> lut(S * S * S, -1);
+  int n = 0;
+  for (int z = -L; z <= L; ++z)
+    for (int y = -L; y <= L; ++y)
+      for (int x = -L; x <= L; ++x)
+        if (in_footprint(x, y, z, R, box)) lut[(x + L) + S * ((y + L) + S * (z + L))] = (int16_t)n++;
+  std::vector<int16_t> perm;
+  auto seg = [&](int dy, int dz, int X) {
+    for (int dx = -X; dx <= X; ++dx) perm.push_back(lut[(dx + L) + S * ((dy + L) + S * (dz + L))]);
+  };
+  const int GW = W * W / 4;
+  for (int w = 0; w < 4 * GW; ++w) seg(w % W - R, w / W - R, L);
+  for (int v = 0; v < 4 * W; ++v) {
+    const int arm = v / W, j = v % W - R;
+    seg(arm < 2 ? (arm == 0 ? -L : L) : j, arm < 2 ? j : (arm == 2 ? -L : L), R);
+  }
+  seg(R, R, L);
+  while (perm.size() % 4) perm.push_back(-1);
+  return perm;
+}
+
+static eb_status build_quad_plan(eb_stencils* st, ApplyPlan* pl, int R, cudaStream_t s, Tmp& tmp) {
+  std::vector<int16_t> perm = quad_perm(R, 1);
+  const int nq = (int)(perm.size() / 4);
+  if (nq != (R == 3 ? QuadShape<3>::NQ : QuadShape<2>::NQ)) { set_error("quad layout mismatch"); return EB_ERR_INVALID; }
+  int64_t cnt = 0;
+  for (int16_t v : perm) cnt += v >= 0;
+  if (cnt != st->nfoot) { set_error("quad layout does not cover the footprint"); return EB_ERR_INVALID; }
+  const int64_t n_irr = st->n_irr, n_class = st->n_row_classes, nU = st->n_rows - n_class;
+  int32_t* flag;
+  int64_t* posC;
+  int64_t nC = 0;
+  EB_TRY(tmp.get(&flag, n_irr));
+  EB_TRY(tmp.get(&posC, n_irr));
+  k_flag_class<<<nblk(n_irr, 256), 256, 0, s>>>(n_irr, st->irr_row, n_class, flag); eb::count_launch();
+  EB_TRY(scan<int32_t>(flag, n_irr, posC, &nC, s, tmp));
+  if (nU + nC != n_irr) { set_error("irregular rows are not one per cell"); return EB_ERR_INVALID; }
+  pl->nU = nU;
+  pl->nC = nC;
+  pl->n_class = n_class;
+  EB_TRY(dalloc(st, &pl->cellU, std::max<int64_t>(nU, 1)));
+  EB_TRY(dalloc(st, &pl->cellC, std::max<int64_t>(nC, 1)));
+  EB_TRY(dalloc(st, &pl->classC, std::max<int64_t>(nC, 1)));
+  k_split_irr<<<nblk(n_irr, 256), 256, 0, s>>>(n_irr, st->irr_cell, st->irr_row, n_class, posC, pl->cellU, pl->cellC,
+                                               pl->classC); eb::count_launch();
+  const size_t nUp = (size_t)((nU + 31) / 32) * 32;
+  const size_t szU = std::max<size_t>(nUp * nq * 4, 4);
+  EB_TRY(dalloc(st, &pl->qU32, szU));
+  EB_TRY(dalloc(st, &pl->qU64, szU));
+  EB_CUDA(cudaMemsetAsync(pl->qU32, 0, szU * 4, s));
+  EB_CUDA(cudaMemsetAsync(pl->qU64, 0, szU * 8, s));
+  int16_t* dperm;
+  EB_TRY(tmp.get(&dperm, perm.size()));
+  EB_CUDA(cudaMemcpyAsync(dperm, perm.data(), perm.size() * 2, cudaMemcpyHostToDevice, s));
+  if (nU > 0) {
+    dim3 grid(nblk(nU, 256), (unsigned)(4 * nq));
+    k_pack_quads<float><<<grid, 256, 0, s>>>(st->rows32, st->n_rows, dperm, nq, n_class, pl->qU32);
+    eb::count_launch();
+    k_pack_quads<double><<<grid, 256, 0, s>>>(st->rows64, st->n_rows, dperm, nq, n_class, pl->qU64);
+    eb::count_launch();
+  }
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaStreamSynchronize(s));  // the plan outlives the temporaries
+  pl->quad = 1;
   return EB_OK;
 }
 
@@ -703,6 +808,7 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
     EB_CUDA(cudaMemcpyAsync(st->foot_d, dd.data(), dd.size(), cudaMemcpyHostToDevice, s));
     EB_CUDA(cudaMemcpyAsync(dlut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, s));
     int center = lut[L + S * (L + S * L)];
+    st->foot_center = center;
     int64_t nrk = 1;
     for (int d = 0; d < D; ++d) nrk *= (int64_t)M * M;
     nrk += 1;  // key 0: template
@@ -918,10 +1024,27 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
       pl->cube64[idx] = tm[i];
       pl->cube32[idx] = (float)tm[i];
     }
+    if (D == 3) {
+      // z symmetry of the interior template (exact in the mathematics, to rounding in the LS solves)
+      double mx = 0.0, dmax = 0.0;
+      for (double v : pl->cube64) mx = std::max(mx, fabs(v));
+      pl->zcube64 = pl->cube64;
+      for (int z = 1; z <= L; ++z)
+        for (int y = 0; y < S; ++y)
+          for (int x = 0; x < S; ++x) {
+            double& p = pl->zcube64[x + S * (y + S * (L + z))];
+            double m = pl->cube64[x + S * (y + S * (L - z))];
+            dmax = std::max(dmax, fabs(p - m));
+            p = 0.5 * (p + m);
+          }
+      pl->zsym = dmax <= 64.0 * 2.220446049250313e-16 * mx;
+      pl->zcube32.assign(pl->zcube64.begin(), pl->zcube64.end());
+    }
     bool ok = dm.nbr_box && st->n_row_classes > 0;
     pl->tma32 = ok && (dm.n[0] % 4 == 0);
     pl->tma64 = ok && (dm.n[0] % 2 == 0);
     pl->seg = dm.nbr_box;
+    if (pl->seg && D == 3 && (R == 2 || R == 3) && st->n_irr > 0) EB_TRY(build_quad_plan(st, pl, R, s, tmp));
     EB_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
     EB_CUDA(cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming));
     EB_CUDA(cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming));
@@ -1120,6 +1243,20 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
       }
       in.KFS = st->dm.KFS;
       in.dinv_high = st->dinv64;
+      in.rows64 = st->rows64;
+      in.rows32 = st->rows32;
+      in.n_rows = st->n_rows;
+      in.nfoot = st->nfoot;
+      in.center = st->foot_center;
+      in.irr_cell = st->irr_cell;
+      in.irr_row = st->irr_row;
+      in.n_irr = st->n_irr;
+      in.kind = st->cell_kind;
+      in.tmpl64 = st->tmpl64;
+      in.tmpl32 = st->tmpl32;
+      in.foot_off = st->foot_off;
+      in.R = st->dm.R;
+      in.box = st->dm.nbr_box;
       cudaError_t me = mg_setup(in, m, s);
       if (me != cudaSuccess) {
         mg_free(m);

@@ -11,6 +11,7 @@
 #include "eb_apply.cuh"
 #include "eb_internal.cuh"
 #include "eb_apply_tma.cuh"
+#include "eb_apply_quad.cuh"
 
 #include <cuda.h>
 
@@ -133,6 +134,28 @@ template <typename T>
 static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
   const ApplyPlan* pl = a.plan;
   int64_t nb = (a.n_irr + 255) / 256;
+  if (pl && pl->quad) {
+    // unique rows (HBM stream) in the quad layout, then the class rows (L2-resident, shared by the
+    // wall-layer cells) by the segment walk over the canonical rows
+    const QuadArgs<T> q = quad_args<T>(*pl);
+    const int64_t bu = (pl->nU + 127) / 128;
+    if (bu > 0) {
+      if (pl->R == 3) k_irr_quad<T, 3, ApplyEpi><<<(unsigned)bu, 128, 0, st>>>(a, q, ApplyEpi());
+      else k_irr_quad<T, 2, ApplyEpi><<<(unsigned)bu, 128, 0, st>>>(a, q, ApplyEpi());
+      eb::count_launch();
+    }
+    if (pl->nC > 0) {
+      ApplyArgs<T> c = a;
+      c.n_irr = pl->nC;
+      c.irr_cell = pl->cellC;
+      c.irr_row = pl->classC;
+      const int64_t bc = (pl->nC + 255) / 256;
+      if (pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
+      else k_apply_irregular_seg<T, 2, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
+      eb::count_launch();
+    }
+    return cudaGetLastError();
+  }
   if (pl && pl->seg) {
     if (pl->dim == 3 && pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
     else if (pl->dim == 3 && pl->R == 2) k_apply_irregular_seg<T, 2, 3><<<(unsigned)nb, 256, 0, st>>>(a, pl->nx, pl->ny, pl->nz);
@@ -163,12 +186,12 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <typename T, int R, int D>
+template <typename T, int R, int D, bool ZSYM>
 static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaStream_t s) {
   constexpr int L = R + 1;
   constexpr int S = 2 * L + 1;
-  constexpr int NP = D == 3 ? S : 1;
-  constexpr int PX = TT_OX + 2 * L, PY = TT_OY + 2 * L;
+  constexpr int NP = D == 3 ? S + 1 : 1;
+  constexpr int PX = TT_OX + 2 * TT_XH, PY = TT_OY + 2 * L;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap map;
@@ -182,8 +205,8 @@ static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaSt
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   TmplCoef<T, R> cf;
   const T* cube;
-  if constexpr (sizeof(T) == 4) cube = pl.cube32.data();
-  else cube = pl.cube64.data();
+  if constexpr (sizeof(T) == 4) cube = ZSYM ? pl.zcube32.data() : pl.cube32.data();
+  else cube = ZSYM ? pl.zcube64.data() : pl.cube64.data();
   for (int i = 0; i < S * S * S; ++i) cf.c[i] = cube[i];
   TmplArgs<T> ta;
   ta.nx = pl.nx;
@@ -191,7 +214,7 @@ static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaSt
   ta.nz = pl.nz;
   ta.ntx = (pl.nx + TT_OX - 1) / TT_OX;
   ta.nty = (pl.ny + TT_OY - 1) / TT_OY;
-  ta.zchunk = D == 3 ? (pl.nz >= 128 ? 16 : 8) : 1;
+  ta.zchunk = D == 3 ? 8 : 1;
   ta.nzc = (pl.nz + ta.zchunk - 1) / ta.zchunk;
   ta.items = (int64_t)ta.ntx * ta.nty * ta.nzc;
   ta.kind = a.kind;
@@ -199,8 +222,9 @@ static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaSt
   ta.y = a.y;
   ta.kappa_weighted = a.kappa_weighted;
   ta.err = pl.err;
-  size_t smem = (size_t)NP * PX * PY * sizeof(T) + NP * 8;
-  auto kern = k_apply_tma<T, R, D>;
+  constexpr size_t SLOT = ((PX * PY * sizeof(T) + 127) / 128) * 128;  // ring slot bytes (128-byte aligned TMA writes)
+  size_t smem = (size_t)NP * SLOT + NP * 8;
+  auto kern = k_apply_tma<T, R, D, ZSYM>;
   // attribute and occupancy are per device; kept for the last device seen
   static int cached_dev = -1, cached_per_sm = 0;
   int dev = 0;
@@ -225,10 +249,12 @@ static cudaError_t launch_template_pass(const ApplyArgs<T>& a, cudaStream_t s) {
   const ApplyPlan* pl = a.plan;
   bool tma = pl && (sizeof(T) == 4 ? pl->tma32 : pl->tma64);
   if (tma) {
-    if (pl->dim == 3 && pl->R == 3) return launch_tma<T, 3, 3>(a, *pl, s);
-    if (pl->dim == 3 && pl->R == 2) return launch_tma<T, 2, 3>(a, *pl, s);
-    if (pl->dim == 2 && pl->R == 3) return launch_tma<T, 3, 2>(a, *pl, s);
-    if (pl->dim == 2 && pl->R == 2) return launch_tma<T, 2, 2>(a, *pl, s);
+    if (pl->dim == 3 && pl->R == 3)
+      return pl->zsym ? launch_tma<T, 3, 3, true>(a, *pl, s) : launch_tma<T, 3, 3, false>(a, *pl, s);
+    if (pl->dim == 3 && pl->R == 2)
+      return pl->zsym ? launch_tma<T, 2, 3, true>(a, *pl, s) : launch_tma<T, 2, 3, false>(a, *pl, s);
+    if (pl->dim == 2 && pl->R == 3) return launch_tma<T, 3, 2, false>(a, *pl, s);
+    if (pl->dim == 2 && pl->R == 2) return launch_tma<T, 2, 2, false>(a, *pl, s);
   }
   size_t sm = ((a.nfoot * 4 + 15) / 16) * 16 + a.nfoot * sizeof(T);
   int64_t nb = (a.ncell + 255) / 256;

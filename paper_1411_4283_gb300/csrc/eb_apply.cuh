@@ -33,8 +33,19 @@ struct ApplyPlan {
   int nx, ny, nz, dim, R;
   int tma32, tma64;              // template pass by TMA tiles possible (box metric, aligned rows)
   int seg;                       // box footprint: irregular rows by x-contiguous segments
+  // irregular rows in the quad layout (3-D box neighbourhoods, R = 2 or 3; see eb_apply_quad.cuh)
+  int quad = 0;
+  int64_t nU = 0, nC = 0, n_class = 0;
+  int32_t* cellU = nullptr;      // [nU] cells with a unique row, ascending (unique row u = canonical n_class + u)
+  int32_t* cellC = nullptr;      // [nC] cells with a class row, ascending
+  int32_t* classC = nullptr;     // [nC] their class row
+  float* qU32 = nullptr;         // unique rows in the quad layout
+  double* qU64 = nullptr;
   std::vector<float> cube32;     // dense (2R+3)^3 template coefficients
   std::vector<double> cube64;
+  int zsym = 0;                  // template symmetric in z (to a few ulps): z-folded template pass
+  std::vector<float> zcube32;    // the cube with c(., ., a) = c(., ., -a) averaged (entries a >= 0 used)
+  std::vector<double> zcube64;
   int32_t* err;                  // device error word (bounded waits)
   cudaStream_t side;             // irregular pass runs here, overlapped with the template pass
   cudaEvent_t fork, join;

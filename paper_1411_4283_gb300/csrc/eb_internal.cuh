@@ -88,6 +88,7 @@ struct eb_stencils {
   // operator rows (kappa-weighted, h^2 included): footprint-dense
   int nfoot = 0;
   int32_t* foot_off = nullptr;      // [nfoot] linear cell offset of each footprint entry
+  int foot_center = 0;              // footprint index of the zero offset
   int8_t* foot_d = nullptr;         // [nfoot][3] offsets
   int64_t n_irr = 0;                // cells with a non-template row
   int32_t n_row_classes = 0;        // shared rows (class rows incl. template = row 0)

@@ -11,14 +11,27 @@
 // see).  Coarse levels average kappa and the face fractions of their
 // children and sum the EB terms (Galerkin scaling for piecewise-constant
 // transfers); smoothing is weighted Jacobi; restriction averages the children;
-// prolongation is piecewise constant.  The V-cycle is a fixed linear map, so
-// it serves as a right preconditioner of BiCGStab.
+// prolongation is piecewise constant.
+//
+// A few cut cells have a high-order diagonal that is weak (below half of the
+// 7-point one), zero or positive: the row is dominated by its neighbours, the
+// 7-point model is wrong there, and BiCGStab preconditioned by the V-cycle
+// alone goes through long near-breakdown phases (at 256^3, 169 FP64
+// iterations instead of 17).  After the V-cycle the preconditioner therefore
+// solves the high-order operator exactly on the 3x3(x3) block of cells around
+// each such cell (a multiplicative Schwarz step: z += A_BB^-1 (r - A z)_B,
+// blocks precomputed by Gauss-Jordan in FP64).  The whole map is fixed and
+// linear, so it serves as a right preconditioner of BiCGStab.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "eb_internal.cuh"
 #include "eb_mg.cuh"
+#include "eb_tables.cuh"
 
 namespace eb {
 
@@ -35,7 +48,7 @@ __global__ void k_mg_fine(int dim, int nx, int ny, int nz, double h, const uint8
                           const uint8_t* ff0, const uint8_t* ff1, const uint8_t* ff2, const int32_t* cf0,
                           const int32_t* cf1, const int32_t* cf2, const double* fm0, const double* fm1,
                           const double* fm2, int KFS, const double* __restrict__ dinv_high, float* cp0, float* cp1,
-                          float* cp2, float* diag) {
+                          float* cp2, float* diag, uint8_t* weak) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t ncell = (int64_t)nx * ny * nz;
   if (c >= ncell) return;
@@ -62,10 +75,12 @@ __global__ void k_mg_fine(int dim, int nx, int ny, int nz, double h, const uint8
       if (side) cp[d][c] = (float)(wall ? 0.0 : a * ih2);
     }
   }
+  weak[c] = 0;
   if (flag[c] == 0) { diag[c] = 0.0f; return; }
   double dg = -sum * ih2;
-  if (flag[c] == 2 && dinv_high[c] != 0.0) {
-    double dh = 1.0 / dinv_high[c];  // diagonal of the high-order kappa-weighted operator
+  if (flag[c] == 2) {
+    const double dh = dinv_high[c] != 0.0 ? 1.0 / dinv_high[c] : 0.0;  // diagonal of the high-order operator
+    weak[c] = dh > 0.5 * dg;         // weaker than half the 7-point diagonal, zero or positive
     if (dh < dg) dg = dh;            // add a non-negative EB term e_v
   }
   diag[c] = (float)dg;
@@ -159,32 +174,42 @@ __device__ __forceinline__ T mg_apply_at(int dim, int nx, int ny, int nz, int64_
   return s;
 }
 
+// Level kernels run on a 3-D grid of (32 x 4)-thread blocks over (x, y) rows and z planes, so that a
+// thread's cell coordinates need no integer division.
+constexpr int MG_BX = 32, MG_BY = 4;
+
+__device__ __forceinline__ bool mg_cell(int nx, int ny, int* p, int64_t* c) {
+  p[0] = blockIdx.x * MG_BX + threadIdx.x;
+  p[1] = blockIdx.y * MG_BY + threadIdx.y;
+  p[2] = blockIdx.z;
+  if (p[0] >= nx || p[1] >= ny) return false;
+  *c = (int64_t)p[0] + (int64_t)nx * ((int64_t)p[1] + (int64_t)ny * p[2]);
+  return true;
+}
+
 // weighted Jacobi: out = x + w (b - M x) / diag   (x == null: out = w b / diag)
 template <typename T>
-__global__ void k_mg_jacobi(int dim, int nx, int ny, int nz, const float* cp0, const float* cp1, const float* cp2,
-                            const float* dg, const T* __restrict__ b, const T* x, T* out, float w) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = (int64_t)nx * ny * nz;
-  if (c >= n) return;
+__global__ void __launch_bounds__(MG_BX * MG_BY) k_mg_jacobi(int dim, int nx, int ny, int nz, const float* cp0,
+                                                             const float* cp1, const float* cp2, const float* dg,
+                                                             const T* __restrict__ b, const T* x, T* out, float w) {
+  int p[3];
+  int64_t c;
+  if (!mg_cell(nx, ny, p, &c)) return;
   float d = dg[c];
   if (d == 0.0f) { out[c] = (T)0; return; }
   if (!x) { out[c] = (T)w * b[c] / (T)d; return; }
-  int p[3];
-  xyz_of(c, nx, ny, p);
   T r = b[c] - mg_apply_at<T>(dim, nx, ny, nz, c, p, cp0, cp1, cp2, dg, x);
   out[c] = x[c] + (T)w * r / (T)d;
 }
 
 // coarse right-hand side: average of the children's residuals b - M x
 template <typename T>
-__global__ void k_mg_restrict(int dim, int nxf, int nyf, int nzf, int nxc, int nyc, int nzc, const float* cp0,
+__global__ void __launch_bounds__(MG_BX * MG_BY) k_mg_restrict(int dim, int nxf, int nyf, int nzf, int nxc, int nyc, int nzc, const float* cp0,
                               const float* cp1, const float* cp2, const float* dg, const T* __restrict__ b,
                               const T* __restrict__ x, T* bc) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t ncc = (int64_t)nxc * nyc * nzc;
-  if (c >= ncc) return;
   int X[3];
-  xyz_of(c, nxc, nyc, X);
+  int64_t c;
+  if (!mg_cell(nxc, nyc, X, &c)) return;
   int nf[3] = {nxf, nyf, nzf};
   const int nch = 1 << dim;
   T acc = (T)0;
@@ -205,14 +230,12 @@ __global__ void k_mg_restrict(int dim, int nxf, int nyf, int nzf, int nxc, int n
 
 // x_f += x_c (piecewise constant) on volumes
 template <typename T>
-__global__ void k_mg_prolong(int dim, int nxf, int nyf, int nzf, int nxc, int nyc, const float* dg, const T* __restrict__ xc,
+__global__ void __launch_bounds__(MG_BX * MG_BY) k_mg_prolong(int dim, int nxf, int nyf, int nzf, int nxc, int nyc, const float* dg, const T* __restrict__ xc,
                              T* xf) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t n = (int64_t)nxf * nyf * nzf;
-  if (c >= n) return;
-  if (dg[c] == 0.0f) return;
   int p[3];
-  xyz_of(c, nxf, nyf, p);
+  int64_t c;
+  if (!mg_cell(nxf, nyf, p, &c)) return;
+  if (dg[c] == 0.0f) return;
   int64_t cc = (int64_t)(p[0] >> 1) + (int64_t)nxc * ((int64_t)(p[1] >> 1) + (int64_t)nyc * (dim == 3 ? (p[2] >> 1) : 0));
   xf[c] += xc[cc];
 }
@@ -316,9 +339,247 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(int dim, int nlev, const MgD
 
 static unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// ---------------------------------------------------------------- local block solves
+constexpr int BLK = 27;  // 3 x 3 x 3 cells around a weak-diagonal cut cell
+constexpr int MAX_BLOCKS = 8192;
+
+struct RowSrc {
+  const int32_t* irr_cell;
+  const int32_t* irr_row;
+  int64_t n_irr;
+  const uint8_t* kind;
+  const double* tmpl64;
+  const double* rows64;
+  const float* tmpl32;
+  const float* rows32;
+  int64_t n_rows;
+  int nfoot;
+  const int32_t* foot_off;
+  const int16_t* lut;
+  int L, S, nx, ny, nz;
+  int64_t ncell;
+};
+
+// canonical row of cell c (-1: the template row, -2: covered)
+__device__ int64_t row_of_cell(const RowSrc& a, int64_t c) {
+  if (a.kind[c] == 0) return -2;
+  if (a.kind[c] == 1) return -1;
+  int64_t lo = 0, hi = a.n_irr - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a.irr_cell[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return a.irr_row[lo];
+}
+
+template <typename T>
+__device__ __forceinline__ T coef_at(const RowSrc& a, int64_t row, int f);
+template <>
+__device__ __forceinline__ double coef_at<double>(const RowSrc& a, int64_t row, int f) {
+  return row == -1 ? a.tmpl64[f] : a.rows64[(int64_t)f * a.n_rows + row];
+}
+template <>
+__device__ __forceinline__ float coef_at<float>(const RowSrc& a, int64_t row, int f) {
+  return row == -1 ? a.tmpl32[f] : a.rows32[(int64_t)f * a.n_rows + row];
+}
+
+// A_BB of every block (FP64); padding entries get the identity
+__global__ void k_blk_assemble(RowSrc a, int nblk, const int32_t* __restrict__ cells, double* __restrict__ M) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nblk * BLK * BLK) return;
+  const int b = (int)(t / (BLK * BLK)), i = (int)(t / BLK % BLK), j = (int)(t % BLK);
+  const int32_t ci = cells[b * BLK + i], cj = cells[b * BLK + j];
+  double v = 0.0;
+  if (ci < 0 || cj < 0) {
+    v = i == j ? 1.0 : 0.0;
+  } else {
+    int xi[3], xj[3];
+    xyz_of(ci, a.nx, a.ny, xi);
+    xyz_of(cj, a.nx, a.ny, xj);
+    const int dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+    const int f = a.lut[(dx + a.L) + a.S * ((dy + a.L) + a.S * (dz + a.L))];
+    const int64_t row = row_of_cell(a, ci);
+    if (f >= 0 && row != -2) v = coef_at<double>(a, row, f);
+  }
+  M[t] = v;
+}
+
+// in-place Gauss-Jordan inverse with partial pivoting, one thread per block
+__global__ void k_blk_invert(int nblk, double* __restrict__ M, float* __restrict__ M32, int32_t* __restrict__ fail) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  double a[BLK][2 * BLK];
+  const double* src = M + (int64_t)b * BLK * BLK;
+  for (int i = 0; i < BLK; ++i)
+    for (int j = 0; j < BLK; ++j) {
+      a[i][j] = src[i * BLK + j];
+      a[i][BLK + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int k = 0; k < BLK; ++k) {
+    int p = k;
+    for (int i = k + 1; i < BLK; ++i)
+      if (fabs(a[i][k]) > fabs(a[p][k])) p = i;
+    if (a[p][k] == 0.0) { atomicExch(fail, 1); return; }
+    if (p != k)
+      for (int j = 0; j < 2 * BLK; ++j) { double t = a[k][j]; a[k][j] = a[p][j]; a[p][j] = t; }
+    const double inv = 1.0 / a[k][k];
+    for (int j = 0; j < 2 * BLK; ++j) a[k][j] *= inv;
+    for (int i = 0; i < BLK; ++i) {
+      if (i == k) continue;
+      const double m = a[i][k];
+      if (m == 0.0) continue;
+      for (int j = 0; j < 2 * BLK; ++j) a[i][j] -= m * a[k][j];
+    }
+  }
+  double* dst = M + (int64_t)b * BLK * BLK;
+  for (int i = 0; i < BLK; ++i)
+    for (int j = 0; j < BLK; ++j) {
+      dst[i * BLK + j] = a[i][BLK + j];
+      M32[(int64_t)b * BLK * BLK + i * BLK + j] = (float)a[i][BLK + j];
+    }
+}
+
+// res_i = r_ci - (A z)_ci for the cells of every block
+template <typename T>
+__global__ void k_blk_res(RowSrc a, int nblk, const int32_t* __restrict__ cells, const T* __restrict__ r,
+                          const T* __restrict__ z, T* __restrict__ res) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nblk * BLK) return;
+  const int32_t c = cells[t];
+  if (c < 0) { res[t] = (T)0; return; }
+  const int64_t row = row_of_cell(a, c);
+  if (row == -2) { res[t] = (T)0; return; }
+  T acc = (T)0;
+  const int64_t hi = a.ncell - 1;
+  for (int f = 0; f < a.nfoot; ++f) {
+    int64_t q = c + a.foot_off[f];
+    q = q < 0 ? 0 : (q > hi ? hi : q);  // out-of-domain entries have zero coefficients
+    acc = fma(coef_at<T>(a, row, f), z[q], acc);
+  }
+  res[t] = r[c] - acc;
+}
+
+// z_ci += sum_j inv(A_BB)_ij res_j (blocks may overlap: additive)
+template <typename T>
+__global__ void k_blk_corr(int nblk, const int32_t* __restrict__ cells, const T* __restrict__ inv,
+                           const T* __restrict__ res, T* z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nblk * BLK) return;
+  const int32_t c = cells[t];
+  if (c < 0) return;
+  const int64_t b = t / BLK, i = t % BLK;
+  const T* m = inv + (b * BLK + i) * BLK;
+  const T* rr = res + b * BLK;
+  T d = (T)0;
+  for (int j = 0; j < BLK; ++j) d = fma(m[j], rr[j], d);
+  atomicAdd(z + c, d);
+}
+
+static RowSrc row_src(const Multigrid& mg) {
+  RowSrc a;
+  a.irr_cell = mg.irr_cell;
+  a.irr_row = mg.irr_row;
+  a.n_irr = mg.n_irr;
+  a.kind = mg.kind;
+  a.tmpl64 = mg.tmpl64;
+  a.rows64 = mg.rows64;
+  a.tmpl32 = mg.tmpl32;
+  a.rows32 = mg.rows32;
+  a.n_rows = mg.n_rows;
+  a.nfoot = mg.nfoot;
+  a.foot_off = mg.foot_off;
+  a.lut = mg.foot_lut;
+  a.L = mg.R + 1;
+  a.S = 2 * mg.R + 3;
+  a.nx = mg.lev[0].n[0];
+  a.ny = mg.lev[0].n[1];
+  a.nz = mg.lev[0].n[2];
+  a.ncell = mg.lev[0].ncell;
+  return a;
+}
+
+// blocks around the weak-diagonal cut cells (3 x 3 x 3, or 3 x 3 in 2-D with the other entries padding):
+// cell lists on the host, A_BB and its inverse on the device
+static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const uint8_t* weak_d, cudaStream_t s) {
+  if (!in.irr_cell || in.n_irr == 0) return cudaSuccess;
+  const int nx = in.n[0], ny = in.n[1], nz = in.n[2];
+  const int64_t N = (int64_t)nx * ny * nz;
+  std::vector<uint8_t> weak(N), flag(N);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(weak.data(), weak_d, N, cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaMemcpyAsync(flag.data(), in.flag, N, cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  std::vector<int32_t> cells;
+  int nb = 0;
+  for (int64_t c = 0; c < N && nb < MAX_BLOCKS; ++c) {
+    if (!weak[c]) continue;
+    const int x = (int)(c % nx), y = (int)(c / nx % ny), z = (int)(c / ((int64_t)nx * ny));
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int X = x + dx, Y = y + dy, Z = z + dz;
+          int32_t v = -1;
+          if (X >= 0 && X < nx && Y >= 0 && Y < ny && Z >= 0 && Z < nz) {
+            const int64_t q = X + (int64_t)nx * (Y + (int64_t)ny * Z);
+            if (flag[q]) v = (int32_t)q;
+          }
+          cells.push_back(v);
+        }
+    ++nb;
+  }
+  // row lookup data
+  mg->irr_cell = in.irr_cell;
+  mg->irr_row = in.irr_row;
+  mg->n_irr = in.n_irr;
+  mg->kind = in.kind;
+  mg->tmpl64 = in.tmpl64;
+  mg->tmpl32 = in.tmpl32;
+  mg->rows64 = in.rows64;
+  mg->rows32 = in.rows32;
+  mg->n_rows = in.n_rows;
+  mg->nfoot = in.nfoot;
+  mg->foot_off = in.foot_off;
+  mg->R = in.R;
+  if (nb == 0) return cudaSuccess;
+  const int L = in.R + 1, S = 2 * L + 1;
+  std::vector<int16_t> lut(S * S * S, -1);
+  int nf = 0;
+  const int zr = in.dim == 3 ? L : 0;
+  for (int z = -zr; z <= zr; ++z)
+    for (int y = -L; y <= L; ++y)
+      for (int x = -L; x <= L; ++x)
+        if (in_footprint(x, y, z, in.R, in.box)) lut[(x + L) + S * ((y + L) + S * (z + L))] = (int16_t)nf++;
+  if (nf != in.nfoot) return cudaErrorInvalidValue;
+  if ((e = cudaMalloc(&mg->foot_lut, lut.size() * 2))) return e;
+  if ((e = cudaMalloc(&mg->blk_cells, cells.size() * 4))) return e;
+  if ((e = cudaMalloc(&mg->blk_inv64, (size_t)nb * BLK * BLK * 8))) return e;
+  if ((e = cudaMalloc(&mg->blk_inv32, (size_t)nb * BLK * BLK * 4))) return e;
+  if ((e = cudaMalloc(&mg->blk_res, (size_t)nb * BLK * 8))) return e;
+  if ((e = cudaMemcpyAsync(mg->foot_lut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(mg->blk_cells, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice, s))) return e;
+  mg->nblk = nb;
+  RowSrc a = row_src(*mg);
+  const int64_t nm = (int64_t)nb * BLK * BLK;
+  k_blk_assemble<<<nb256(nm), 256, 0, s>>>(a, nb, mg->blk_cells, mg->blk_inv64);
+  int32_t* fail;
+  if ((e = cudaMalloc(&fail, 4))) return e;
+  cudaMemsetAsync(fail, 0, 4, s);
+  k_blk_invert<<<(nb + 31) / 32, 32, 0, s>>>(nb, mg->blk_inv64, mg->blk_inv32, fail);
+  eb::count_launches(2);
+  int32_t hf = 0;
+  cudaMemcpyAsync(&hf, fail, 4, cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  cudaFree(fail);
+  if (e) return e;
+  if (hf) mg->nblk = 0;  // a singular block: no local solves
+  return cudaGetLastError();
+}
+
 cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
   mg->dim = in.dim;
   mg->nlev = 0;
+  uint8_t* weak = nullptr;  // fine-level cut cells with a weak high-order diagonal
   int n[3] = {in.n[0], in.n[1], in.n[2]};
   cudaError_t e;
   for (int l = 0; l < MG_MAXLEV; ++l) {
@@ -337,9 +598,10 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
       if ((e = cudaMalloc(&L.v64[k], nc * 8))) return e;
     mg->nlev = l + 1;
     if (l == 0) {
+      if ((e = cudaMalloc(&weak, nc))) return e;
       k_mg_fine<<<nb256(nc), 256, 0, s>>>(in.dim, n[0], n[1], n[2], in.h, in.flag, in.ff[0], in.ff[1], in.ff[2],
                                           in.cf[0], in.cf[1], in.cf[2], in.fm[0], in.fm[1], in.fm[2], in.KFS,
-                                          in.dinv_high, L.cp[0], L.cp[1], L.cp[2], L.dg);
+                                          in.dinv_high, L.cp[0], L.cp[1], L.cp[2], L.dg, weak);
       eb::count_launch();
     } else {
       MgLevel& F = mg->lev[l - 1];
@@ -352,6 +614,11 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
     if (in.dim == 3 && n[2] < mn) mn = n[2];
     if (mn <= 4) break;
     for (int d = 0; d < in.dim; ++d) n[d] = (n[d] + 1) / 2;
+  }
+  if (weak) {
+    e = blocks_setup(in, mg, weak, s);
+    cudaFree(weak);
+    if (e) return e;
   }
   // device descriptors of every level for the single-CTA coarse cycle
   MgDev<float> h32[MG_MAXLEV];
@@ -371,6 +638,17 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
 }
 
 void mg_free(Multigrid* mg) {
+  cudaFree(mg->blk_cells);
+  cudaFree(mg->blk_inv64);
+  cudaFree(mg->blk_inv32);
+  cudaFree(mg->blk_res);
+  cudaFree(mg->foot_lut);
+  mg->blk_cells = nullptr;
+  mg->blk_inv64 = nullptr;
+  mg->blk_inv32 = nullptr;
+  mg->blk_res = nullptr;
+  mg->foot_lut = nullptr;
+  mg->nblk = 0;
   if (mg->dev32) cudaFree(mg->dev32);
   if (mg->dev64) cudaFree(mg->dev64);
   mg->dev32 = mg->dev64 = nullptr;
@@ -398,52 +676,56 @@ double* vbuf<double>(MgLevel& L, int k) { return L.v64[k]; }
 // z = V(b) on level l; b and z live in the level's buffers (0: b, 1: x, 2: work)
 constexpr int64_t MG_CTA_CELLS = 4096;  // levels at most this large run inside one CTA
 
+static dim3 mg_grid(const int* n) {
+  return dim3((unsigned)((n[0] + MG_BX - 1) / MG_BX), (unsigned)((n[1] + MG_BY - 1) / MG_BY), (unsigned)n[2]);
+}
+
 template <typename T>
 static cudaError_t vcycle(const Multigrid& mgc, int l, cudaStream_t s) {
   Multigrid& mg = const_cast<Multigrid&>(mgc);
   MgLevel& L = mg.lev[l];
-  const int D = mg.dim;
   if (L.ncell <= MG_CTA_CELLS) {
+    const int D = mg.dim;
     MgDev<T>* dev = sizeof(T) == 4 ? (MgDev<T>*)mg.dev32 : (MgDev<T>*)mg.dev64;
     k_mg_coarse<T><<<1, 1024, 0, s>>>(D, mg.nlev - l, dev + l, 0.8f, MG_NU, 24);
     eb::count_launch();
     return cudaGetLastError();
   }
   T* b = vbuf<T>(L, 0);
-  T* x = vbuf<T>(L, 1);
-  T* w = vbuf<T>(L, 2);
-  const int64_t n = L.ncell;
-  const float om = D == 3 ? 0.8f : 0.8f;
+  const int D = mg.dim;
+  const float om = 0.8f;
   const bool coarsest = l == mg.nlev - 1;
   const int pre = coarsest ? 24 : MG_NU;
+  const int post = coarsest ? 0 : MG_NU;
+  // the level's result ends in buffer 1: the first smoothing step writes buffer 1 or 2 by the parity
+  // of the sweeps that follow it
+  T* x = vbuf<T>(L, (pre - 1 + post) % 2 == 0 ? 1 : 2);
+  T* w = vbuf<T>(L, (pre - 1 + post) % 2 == 0 ? 2 : 1);
+  const dim3 blk(MG_BX, MG_BY), grd = mg_grid(L.n);
   // smoothing: x = w b / d, then sweeps ping-ponging x <-> w
-  k_mg_jacobi<T><<<nb256(n), 256, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, nullptr, x, om);
+  k_mg_jacobi<T><<<grd, blk, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, nullptr, x, om);
   eb::count_launch();
   for (int it = 1; it < pre; ++it) {
-    k_mg_jacobi<T><<<nb256(n), 256, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, x, w, om);
+    k_mg_jacobi<T><<<grd, blk, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, x, w, om);
     eb::count_launch();
     T* t = x; x = w; w = t;
   }
   if (!coarsest) {
     MgLevel& C = mg.lev[l + 1];
-    k_mg_restrict<T><<<nb256(C.ncell), 256, 0, s>>>(D, L.n[0], L.n[1], L.n[2], C.n[0], C.n[1], C.n[2], L.cp[0], L.cp[1],
-                                                   L.cp[2], L.dg, b, x, vbuf<T>(C, 0));
+    k_mg_restrict<T><<<mg_grid(C.n), blk, 0, s>>>(D, L.n[0], L.n[1], L.n[2], C.n[0], C.n[1], C.n[2], L.cp[0], L.cp[1],
+                                                 L.cp[2], L.dg, b, x, vbuf<T>(C, 0));
     eb::count_launch();
     cudaError_t e = vcycle<T>(mg, l + 1, s);
     if (e) return e;
-    k_mg_prolong<T><<<nb256(n), 256, 0, s>>>(D, L.n[0], L.n[1], L.n[2], C.n[0], C.n[1], L.dg, vbuf<T>(C, 1), x);
+    k_mg_prolong<T><<<grd, blk, 0, s>>>(D, L.n[0], L.n[1], L.n[2], C.n[0], C.n[1], L.dg, vbuf<T>(C, 1), x);
     eb::count_launch();
-    for (int it = 0; it < MG_NU; ++it) {
-      k_mg_jacobi<T><<<nb256(n), 256, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, x, w, om);
+    for (int it = 0; it < post; ++it) {
+      k_mg_jacobi<T><<<grd, blk, 0, s>>>(D, L.n[0], L.n[1], L.n[2], L.cp[0], L.cp[1], L.cp[2], L.dg, b, x, w, om);
       eb::count_launch();
       T* t = x; x = w; w = t;
     }
   }
-  // the level's result must end in buffer 1
-  if (x != vbuf<T>(L, 1)) {
-    cudaError_t e = cudaMemcpyAsync(vbuf<T>(L, 1), x, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    if (e) return e;
-  }
+  if (x != vbuf<T>(L, 1)) return cudaErrorUnknown;  // parity bookkeeping above
   return cudaGetLastError();
 }
 
@@ -476,7 +758,18 @@ cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
   if ((e = cudaMemcpyAsync(vbuf<T>(L, 0), r, L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s))) return e;
   if ((e = cudaGraphLaunch(mg.exec[k], s))) return e;
   eb::count_launches(mg.nodes[k]);
-  return cudaMemcpyAsync(z, vbuf<T>(L, 1), L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  if ((e = cudaMemcpyAsync(z, vbuf<T>(L, 1), L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s))) return e;
+  if (mg.nblk > 0) {
+    RowSrc a = row_src(mg);
+    const int64_t nt = (int64_t)mg.nblk * BLK;
+    const T* inv;
+    if constexpr (sizeof(T) == 4) inv = mg.blk_inv32;
+    else inv = mg.blk_inv64;
+    k_blk_res<T><<<nb256(nt), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
+    k_blk_corr<T><<<nb256(nt), 256, 0, s>>>(mg.nblk, mg.blk_cells, inv, (const T*)mg.blk_res, z);
+    eb::count_launches(2);
+  }
+  return cudaGetLastError();
 }
 
 template cudaError_t mg_precond<float>(const Multigrid&, const float*, float*, cudaStream_t);

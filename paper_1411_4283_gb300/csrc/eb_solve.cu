@@ -1,10 +1,11 @@
 // Linear solve of the kappa-weighted system kappa L phi = kappa (rho - B g)
 // (the paper uses PETSc GMRES + algebraic multigrid, Sec. 3.2; here a
-// Jacobi-preconditioned BiCGStab written for the GPU):
+// BiCGStab written for the GPU, preconditioned by a geometric multigrid
+// V-cycle (eb_mg.cu) or by Jacobi):
 //   mixed: FP32 BiCGStab inner solves on the FP32 operator copy, wrapped in
 //          FP64 iterative refinement whose residual uses the FP64 operator;
 //   plain: FP64 BiCGStab throughout.
-// Dot products accumulate in FP64 whatever the vector precision.
+// Dot products are summed across threads in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -236,6 +237,10 @@ static cudaError_t timed_apply(const ApplyArgs<T>& A, cudaStream_t s) {
   return e;
 }
 
+// The iteration kernels' dot products: per-thread partial sums accumulate in the vector precision
+// (a thread handles at most a few dozen elements), the block and grid sums in FP64.  FP64
+// arithmetic is slow on this GPU, so FP32 vectors keep their per-element work in FP32.
+
 // Device-resident BiCGStab scalars (FP64): slots of the running dot products
 enum { SC_RHO0 = 0, SC_RHO1 = 1, SC_RV = 2, SC_TS = 3, SC_TT = 4, SC_RR = 5, SC_BB = 6, SC_N = 8 };
 
@@ -258,7 +263,7 @@ __global__ void k_bs_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T pi = first ? r[i] : r[i] + (T)beta * (p[i] - (T)omega * v[i]);
     p[i] = pi;
-    ph[i] = dinv[i] * pi;
+    if (dinv) ph[i] = dinv[i] * pi;  // Jacobi; the multigrid preconditioner writes ph itself
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_RV] = 0.0;
 }
@@ -267,10 +272,10 @@ __global__ void k_bs_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* 
 template <typename T>
 __global__ void k_bs_dot_rv(int64_t n, const T* rh, const T* v, double* sc) {
   __shared__ double sh[32];
-  double a = 0.0;
+  T a = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    a += (double)rh[i] * (double)v[i];
-  block_accumulate(a, sc + SC_RV, sh);
+    a = fma(rh[i], v[i], a);
+  block_accumulate((double)a, sc + SC_RV, sh);
 }
 
 // alpha = rho_i / (rhat, v); s = r - alpha v; shat = dinv s.  Clears the slots filled later this iteration.
@@ -281,7 +286,7 @@ __global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T si = r[i] - (T)alpha * v[i];
     s[i] = si;
-    shv[i] = dinv[i] * si;
+    if (dinv) shv[i] = dinv[i] * si;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ao[0] = alpha;
@@ -296,15 +301,15 @@ __global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T*
 template <typename T>
 __global__ void k_bs_dot_ts(int64_t n, const T* t, const T* s, double* sc) {
   __shared__ double sh[32];
-  double a = 0.0, b = 0.0;
+  T a = 0, b = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double ti = (double)t[i];
-    a += ti * (double)s[i];
-    b += ti * ti;
+    const T ti = t[i];
+    a = fma(ti, s[i], a);
+    b = fma(ti, ti, b);
   }
-  block_accumulate(a, sc + SC_TS, sh);
+  block_accumulate((double)a, sc + SC_TS, sh);
   __syncthreads();
-  block_accumulate(b, sc + SC_TT, sh);
+  block_accumulate((double)b, sc + SC_TT, sh);
 }
 
 // omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t; rho_{i+1} = (rhat, r); (r, r)
@@ -314,17 +319,17 @@ __global__ void k_bs_x(int64_t n, T* x, const T* ph, const T* shv, T* r, const T
   __shared__ double sh[32];
   double alpha = ao[0];
   double omega = sc[SC_TT] > 0.0 ? sc[SC_TS] / sc[SC_TT] : 0.0;
-  double a = 0.0, b = 0.0;
+  T a = 0, b = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += (T)alpha * ph[i] + (T)omega * shv[i];
     T ri = s[i] - (T)omega * t[i];
     r[i] = ri;
-    a += (double)rh[i] * (double)ri;
-    b += (double)ri * (double)ri;
+    a = fma(rh[i], ri, a);
+    b = fma(ri, ri, b);
   }
-  block_accumulate(a, sc + (1 - q), sh);
+  block_accumulate((double)a, sc + (1 - q), sh);
   __syncthreads();
-  block_accumulate(b, sc + SC_RR, sh);
+  block_accumulate((double)b, sc + SC_RR, sh);
   if (blockIdx.x == 0 && threadIdx.x == 0) ao[1] = omega;
 }
 
@@ -381,13 +386,13 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
   if (*relres <= tol) { *iters = 0; return cudaSuccess; }
   for (it = 1; it <= maxit; ++it) {
     int q = (it - 1) & 1;
-    k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, dinv, sc, q, it == 1, ao); eb::count_launch();
+    k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, mg ? nullptr : dinv, sc, q, it == 1, ao); eb::count_launch();
     if (mg && (e = mg_precond<T>(*mg, p, ph, s))) return e;  // phat = V-cycle(p) instead of Jacobi
     A.phi = ph;
     A.y = v;
     if ((e = timed_apply<T>(A, s))) return e;
     k_bs_dot_rv<T><<<G, VB, 0, s>>>(n, rh, v, sc); eb::count_launch();
-    k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, dinv, sc, q, ao); eb::count_launch();
+    k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, mg ? nullptr : dinv, sc, q, ao); eb::count_launch();
     if (mg && (e = mg_precond<T>(*mg, sv, shv, s))) return e;
     A.phi = shv;
     A.y = t;

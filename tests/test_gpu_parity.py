@@ -126,26 +126,66 @@ def test_sampled_stencils_3d():
     compare_stencils(st, o, sample_faces(o, 60, seed=2))
 
 
-def test_apply_fp64_3d_sampled_rows():
+def _row_sample_cells(g, order, rng):
+    """Cut cells, full cells next to the EB, interior cells, cells in the wall layers and cells next to
+    the first and last grid rows (the clamped path of the irregular pass)."""
+    n = g.N
+    R = 3 if order == 4 else 2
+    L = R + 1
+    full = np.nonzero(g.flag == 1)[0]
+    x, y, z = full % n, (full // n) % n, full // (n * n)
+    wall = full[(np.minimum(np.minimum(x, y), z) < L + 1) | (np.maximum(np.maximum(x, y), z) > n - L - 2)]
+    edge = full[((y <= L) & (z <= L) & (x < L)) | ((y >= n - 1 - L) & (z >= n - 1 - L) & (x > n - 1 - L))]
+    interior = full[(np.minimum(np.minimum(x, y), z) > L + 1) & (np.maximum(np.maximum(x, y), z) < n - L - 2)]
+    cut = set(int(c) for c in g.cut_cells)
+    near = [int(c) for c in interior if any((int(c) + d) in cut for d in (1, -1, n, -n, n * n, -n * n))]
+    pick = []
+    for pool, k in ((g.cut_cells, 8), (near, 6), (interior, 4), (wall, 8), (edge, 4)):
+        pool = np.asarray(pool)
+        if len(pool):
+            pick += [int(c) for c in rng.choice(pool, min(k, len(pool)), replace=False)]
+    return sorted(set(pick))
+
+
+@pytest.mark.parametrize("order", [4, 2])
+def test_apply_3d_sampled_rows(order):
     """Operator rows at sampled cells: (L phi)_v assembled by the oracle from the cell's own face
-    stencils, against the GPU apply of the whole field."""
+    stencils, against the GPU apply of the whole field (FP64 at 1e-12, FP32 at 1e-5 of the row scale)."""
     import torch
     import paper_1411_4283_gb300 as P
     g = E.sphere_box_config(20)
-    o = Oracle(g, Params(order=4))
-    st, _ = build_gpu(g)
+    o = Oracle(g, Params(order=order))
+    st, _ = build_gpu(g, order=order)
     phi = E.seeded_field(21, g.ncell) * (g.flag > 0)
     y = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
     P.eb_apply(st, to_dev(phi), y, kappa_weighted=True)
     yg = y.cpu().numpy()
-    rng = np.random.default_rng(4)
-    cells = list(rng.choice(g.cut_cells, 6, replace=False)) + list(rng.choice(np.nonzero(g.flag == 1)[0], 6))
-    for c in cells:
-        c = int(c)
+    y32 = torch.empty(g.ncell, dtype=torch.float32, device="cuda")
+    P.eb_apply(st, to_dev(phi, torch.float32), y32, kappa_weighted=True)
+    yg32 = y32.cpu().numpy().astype(np.float64)
+    scale = np.abs(yg).max()
+    for c in _row_sample_cells(g, order, np.random.default_rng(4)):
         acc = 0.0
         for fid, sg in o.cell_flux_faces(c):
             cols, s = o.stencil(fid)
             vm = cols >= 0
             acc += sg * float(s[vm] @ phi[cols[vm]])
         acc /= g.h ** 2
-        assert abs(yg[c] - acc) <= 1e-12 * max(abs(acc), np.abs(yg).max() * 1e-3), (c, yg[c], acc)
+        assert abs(yg[c] - acc) <= 1e-12 * max(abs(acc), scale * 1e-3), (c, yg[c], acc)
+        assert abs(yg32[c] - acc) <= 1e-5 * scale, (c, yg32[c], acc)
+
+
+def test_apply_q2_2d():
+    """Second-order (Q = 2, R_n = 2) operator in 2-D against the oracle's assembled operator."""
+    import torch
+    import paper_1411_4283_gb300 as P
+    g = E.circle_config(32, center=(0.51, 0.49), r=0.3)
+    man = E.Manufactured(g, E.sin_product("config2d"))
+    ref = run_problem(g, man, Params(order=2))
+    st, _ = build_gpu(g, order=2)
+    phi = E.seeded_field(12, g.ncell) * (g.flag > 0)
+    y = torch.empty(g.ncell, dtype=torch.float64, device="cuda")
+    P.eb_apply(st, to_dev(phi), y, kappa_weighted=True)
+    yo = (ref["L"] @ phi) * g.kappa
+    yg = y.cpu().numpy()
+    assert np.linalg.norm(yg - yo) <= 1e-12 * np.linalg.norm(yo)
