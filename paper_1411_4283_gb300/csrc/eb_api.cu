@@ -760,7 +760,7 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   la.scratch = scratch;
   la.ftab = ftab;
   la.wtab = wtab;
-  if (n_slots > 0) k_lsq<<<(unsigned)nblocks, LS_WARPS * 32, ls_smem, s>>>(la); eb::count_launch();
+  if (n_slots > 0) k_lsq<<<(unsigned)nblocks, LS_WARPS * 32, ls_smem, s>>>(la, T); eb::count_launch();
   EB_CUDA(cudaGetLastError());
   EB_CUDA(cudaEventRecord(ev[3], s));
   {

@@ -433,12 +433,16 @@ __device__ void shift_moments(const Tables& T, const double* __restrict__ in, co
   }
 }
 
-// One weighted LS row (Sec. 2.2.1 rows, Sec. 2.4 weights) written to row[];
-// x0s: x0 offset from the base cell centre in units of h.  Returns the weight.
-__device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, const int* base, const double* x0s,
-                            double* row, double* tmp, int* bad) {
+// One weighted LS row (Sec. 2.2.1 rows, Sec. 2.4 weights) in row[]; x0s: x0 offset from the base cell
+// centre in units of h.  Returns the weight.  Rows of full cells come from the offset table; a row
+// whose moments must be shifted to x0 is left pending (*pend = 1) with its source pointer, offset
+// and weight recorded in row[0..4], so that the warp can shift all pending rows of a chunk with
+// every lane busy (row_finish).  Wall rows over a cut face are shifted here.
+__device__ double row_prepare(const LsArgs& a, const Tables& T, uint32_t desc, const int* base, const double* x0s,
+                              double* row, double* tmp, int* bad, int* pend) {
   const Dims& dm = a.dm;
   const int K = T.K;
+  *pend = 0;
   int kind = rd_kind(desc);
   int c[3], dl[3];
   for (int d = 0; d < 3; ++d) {
@@ -456,14 +460,18 @@ __device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, con
     int fx[3] = {c[0], c[1], c[2]};
     if (ws) fx[wd] += 1;
     int32_t cf = a.cutface_of[wd][face_local(dm, wd, fx)];
-    if (cf >= 0) {
-      const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
-      for (int i = 0; i < K; ++i) row[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
-      src = row;
-    } else src = T.full_face[wd];
     double r2 = 0.0;
     for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
     w = weight_of(dm, r2);
+    if (cf >= 0) {
+      const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
+      for (int i = 0; i < K; ++i) row[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
+      shift_moments(T, row, delta, row, tmp);
+      double sc = w / row[0];
+      for (int i = 0; i < K; ++i) row[i] *= sc;
+      return w;
+    }
+    src = T.full_face[wd];
   } else {
     int ti = tab_index(delta);
     if (ti >= 0) w = a.wtab[ti];
@@ -483,10 +491,23 @@ __device__ double build_row(const LsArgs& a, const Tables& T, uint32_t desc, con
       src = a.eb_mom + (int64_t)cut * dm.KS;
     } else src = cut >= 0 ? a.vol_mom + (int64_t)cut * dm.KS : T.full_vol;
   }
-  shift_moments(T, src, delta, row, tmp);
-  double sc = w / row[0];
-  for (int i = 0; i < K; ++i) row[i] *= sc;
+  row[0] = __longlong_as_double((long long)(uintptr_t)src);
+  row[1] = delta[0];
+  row[2] = delta[1];
+  row[3] = delta[2];
+  row[4] = w;
+  *pend = 1;
   return w;
+}
+
+// the moment shift and weighting of a pending row (record in row[0..4])
+__device__ void row_finish(const Tables& T, double* row, double* tmp) {
+  const double* src = reinterpret_cast<const double*>((uintptr_t)__double_as_longlong(row[0]));
+  const double delta[3] = {row[1], row[2], row[3]};
+  const double w = row[4];
+  shift_moments(T, src, delta, row, tmp);
+  const double sc = w / row[0];
+  for (int i = 0; i < T.K; ++i) row[i] *= sc;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -494,36 +515,44 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Column sums of P[0..32)[c0 .. c0+mm) (mm <= 32 columns): g lanes per column
-// each sum 32/g partials with independent accumulators, then a shuffle tree.
-// Returns the sum in the first lane of each group; *col is the column (or -1).
-__device__ __forceinline__ double column_sums(const double* P, int c0, int mm, int lane, int* col) {
-  int g = 1;
-  while (g * 2 * mm <= 32) g *= 2;
-  int cl = lane / g, part = lane % g, L = 32 / g;
+// Column sums of P[0..32)[c0 .. c0+mm) (mm <= 32/G columns): G lanes per column each sum 32/G
+// partials with independent accumulators, then a shuffle tree.  Returns the sum in the first lane
+// of each group; *col is the column (or -1).
+template <int G>
+__device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int lane, int* col) {
+  constexpr int L = 32 / G;
+  const int cl = lane / G, part = lane % G;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   if (cl < mm) {
     const double* p = P + (part * L) * KST + c0 + cl;
-    int l = 0;
-    for (; l + 4 <= L; l += 4) {
-      a0 += p[(l + 0) * KST];
-      a1 += p[(l + 1) * KST];
-      a2 += p[(l + 2) * KST];
-      a3 += p[(l + 3) * KST];
+#pragma unroll
+    for (int l = 0; l < L; l += 4) {
+      a0 += p[l * KST];
+      if (l + 1 < L) a1 += p[(l + 1) * KST];
+      if (l + 2 < L) a2 += p[(l + 2) * KST];
+      if (l + 3 < L) a3 += p[(l + 3) * KST];
     }
-    for (; l < L; ++l) a0 += p[l * KST];
   }
   double s = (a0 + a1) + (a2 + a3);
-  for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+#pragma unroll
+  for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   *col = (cl < mm && part == 0) ? cl : -1;
   return s;
 }
 
-__global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
+__device__ __forceinline__ double column_sums(const double* P, int c0, int mm, int lane, int* col) {
+  if (mm > 16) return colsum_g<1>(P, c0, mm, lane, col);
+  if (mm > 8) return colsum_g<2>(P, c0, mm, lane, col);
+  if (mm > 4) return colsum_g<4>(P, c0, mm, lane, col);
+  if (mm > 2) return colsum_g<8>(P, c0, mm, lane, col);
+  if (mm > 1) return colsum_g<16>(P, c0, mm, lane, col);
+  return colsum_g<32>(P, c0, mm, lane, col);
+}
+
+__global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid_constant__ Tables T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   LsWarpSmem& S = reinterpret_cast<LsWarpSmem*>(smem_raw)[warp];
-  const Tables& T = *a.T;
   const int K = T.K;
   const int gw = blockIdx.x * LS_WARPS + warp;
   double* scr = a.scratch + (int64_t)gw * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
@@ -563,66 +592,78 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
     __syncwarp();
     // ---- row-streamed Householder QR of B = W A: R accumulates the triangular factor
     for (int c0 = 0; c0 < n; c0 += CH) {
+      // rows of the chunk: table rows directly, shifted rows queued (one ballot mask per row slot)
+      unsigned pend[RPL];
+      int npend = 0;
+#pragma unroll
       for (int r = 0; r < RPL; ++r) {
         int li = lane + 32 * r, i = c0 + li;
         double* dst = S.C + li * KST;
+        int pd = 0;
         if (i < n) {
-          double w = build_row(a, T, a.row_desc[p0 + i], base, x0s, dst, S.P + lane * KST, &bad);
-          for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = dst[k];
-          scr_w[i] = w;
+          scr_w[i] = row_prepare(a, T, a.row_desc[p0 + i], base, x0s, dst, S.P + lane * KST, &bad, &pd);
         } else {
           for (int k = 0; k < K; ++k) dst[k] = 0.0;
         }
+        pend[r] = __ballot_sync(0xffffffffu, pd);
+        npend += __popc(pend[r]);
       }
       __syncwarp();
+      for (int q0 = 0; q0 < npend; q0 += 32) {  // pending rows, 32 at a time
+        int q = q0 + lane;
+        if (q < npend) {
+          int r = 0;
+          while (q >= __popc(pend[r])) {
+            q -= __popc(pend[r]);
+            ++r;
+          }
+          unsigned mk = pend[r];
+          for (int t = 0; t < q; ++t) mk &= mk - 1;  // drop the q lowest set bits
+          const int l = __ffs(mk) - 1;
+          row_finish(T, S.C + (l + 32 * r) * KST, S.P + lane * KST);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        int li = lane + 32 * r, i = c0 + li;
+        if (i < n) {
+          const double* src = S.C + li * KST;
+          for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = src[k];
+        }
+      }
       // rows of this chunk per lane (the last chunk is short: skip its empty row slots)
       const int nr = (min(CH, n - c0) + 31) >> 5;
-      for (int k = 0; k < K; ++k) {
-        double ck[RPL];
-        double ss = 0.0;
+      // Householder steps k = 0..K-1 on [R; C].  The update of step k and the partial dot products of
+      // step k+1 share one pass over the chunk: column k+1 is updated first (it is step k+1's
+      // Householder vector), then every later column is loaded, updated, stored and dotted with it.
+      double ck[RPL];
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-          ck[r] = r < nr ? S.C[(lane + 32 * r) * KST + k] : 0.0;
-          ss = fma(ck[r], ck[r], ss);
-        }
-        ss = warp_sum(ss);
-        if (ss == 0.0) continue;
-        const double alpha = S.R[k * K + k];
-        const double sigma = sqrt(fma(alpha, alpha, ss));
-        const double beta = alpha > 0.0 ? -sigma : sigma;
-        const double v0 = alpha - beta;
-        const double gamma = -1.0 / (beta * v0);
-        const int m = K - k - 1;
-        const double* Cl = S.C + lane * KST + k + 1;
+      for (int r = 0; r < RPL; ++r) ck[r] = r < nr ? S.C[(lane + 32 * r) * KST] : 0.0;
+      {  // partial dots of column 0 with columns 1..K-1
+        const double* Cl = S.C + lane * KST + 1;
         double* Pl = S.P + lane * KST;
-        // partial dots of column k with the later columns over this lane's rows; four columns at a
-        // time keep four independent FMA chains in flight
-        int jj = 0;
-        for (; jj + 4 <= m; jj += 4) {
-          double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            if (r < nr) {
-              const double* c = Cl + 32 * r * KST + jj;
-              p0 = fma(ck[r], c[0], p0);
-              p1 = fma(ck[r], c[1], p1);
-              p2 = fma(ck[r], c[2], p2);
-              p3 = fma(ck[r], c[3], p3);
-            }
-          }
-          Pl[jj] = p0;
-          Pl[jj + 1] = p1;
-          Pl[jj + 2] = p2;
-          Pl[jj + 3] = p3;
-        }
-        for (; jj < m; ++jj) {
+        for (int jj = 0; jj < K - 1; ++jj) {
           double p0 = 0.0;
 #pragma unroll
           for (int r = 0; r < RPL; ++r)
             if (r < nr) p0 = fma(ck[r], Cl[32 * r * KST + jj], p0);
           Pl[jj] = p0;
         }
-        __syncwarp();
+      }
+      for (int k = 0; k < K; ++k) {
+        double ss = 0.0;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) ss = fma(ck[r], ck[r], ss);
+        ss = warp_sum(ss);
+        const int m = K - k - 1;
+        const bool refl = ss != 0.0;  // a zero chunk column needs no reflection
+        const double alpha = S.R[k * K + k];
+        const double sigma = refl ? sqrt(fma(alpha, alpha, ss)) : 0.0;
+        const double beta = alpha > 0.0 ? -sigma : sigma;
+        const double v0 = alpha - beta;
+        const double gamma = refl ? -1.0 / (beta * v0) : 0.0;
+        __syncwarp();  // P holds the partial dots of column k with the later columns
         for (int c1 = 0; c1 < m; c1 += 32) {
           int mm = m - c1 < 32 ? m - c1 : 32;
           int col;
@@ -631,34 +672,71 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a) {
             int jc = c1 + col, j = k + 1 + jc;
             double rkj = S.R[k * K + j];
             double t = gamma * fma(v0, rkj, sum);
-            S.R[k * K + j] = fma(-t, v0, rkj);
+            if (refl) S.R[k * K + j] = fma(-t, v0, rkj);
             tau[jc] = t;
           }
         }
         __syncwarp();
-        double* Cw = S.C + lane * KST + k + 1;
-        jj = 0;
-        for (; jj + 4 <= m; jj += 4) {
-          const double t0 = tau[jj], t1 = tau[jj + 1], t2 = tau[jj + 2], t3 = tau[jj + 3];
+        if (m > 0) {
+          // column k+1: update, keep as the next Householder vector
+          const double t1 = tau[0];
+          double ck1[RPL];
 #pragma unroll
           for (int r = 0; r < RPL; ++r) {
+            double* c = S.C + (lane + 32 * r) * KST + k + 1;
+            ck1[r] = 0.0;
             if (r < nr) {
-              double* c = Cw + 32 * r * KST + jj;
-              double a0 = c[0], a1 = c[1], a2 = c[2], a3 = c[3];
-              c[0] = fma(-t0, ck[r], a0);
-              c[1] = fma(-t1, ck[r], a1);
-              c[2] = fma(-t2, ck[r], a2);
-              c[3] = fma(-t3, ck[r], a3);
+              ck1[r] = fma(-t1, ck[r], *c);
+              *c = ck1[r];
             }
           }
-        }
-        for (; jj < m; ++jj) {
-          const double t0 = tau[jj];
+          // columns k+2..K-1: update and dot with column k+1 (four columns per pass)
+          const int m2 = m - 1;
+          double* Cw = S.C + lane * KST + k + 2;
+          double* Pl = S.P + lane * KST;
+          int jj = 0;
+          for (; jj + 4 <= m2; jj += 4) {
+            const double t0 = tau[jj + 1], tt1 = tau[jj + 2], t2 = tau[jj + 3], t3 = tau[jj + 4];
+            double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
 #pragma unroll
-          for (int r = 0; r < RPL; ++r)
-            if (r < nr) Cw[32 * r * KST + jj] = fma(-t0, ck[r], Cw[32 * r * KST + jj]);
+            for (int r = 0; r < RPL; ++r) {
+              if (r < nr) {
+                double* c = Cw + 32 * r * KST + jj;
+                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[1]);
+                const double a2 = fma(-t2, ck[r], c[2]), a3 = fma(-t3, ck[r], c[3]);
+                c[0] = a0;
+                c[1] = a1;
+                c[2] = a2;
+                c[3] = a3;
+                p0 = fma(ck1[r], a0, p0);
+                p1 = fma(ck1[r], a1, p1);
+                p2 = fma(ck1[r], a2, p2);
+                p3 = fma(ck1[r], a3, p3);
+              }
+            }
+            Pl[jj] = p0;
+            Pl[jj + 1] = p1;
+            Pl[jj + 2] = p2;
+            Pl[jj + 3] = p3;
+          }
+          for (; jj < m2; ++jj) {
+            const double t0 = tau[jj + 1];
+            double p0 = 0.0;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              if (r < nr) {
+                double* c = Cw + 32 * r * KST + jj;
+                const double a0 = fma(-t0, ck[r], c[0]);
+                c[0] = a0;
+                p0 = fma(ck1[r], a0, p0);
+              }
+            }
+            Pl[jj] = p0;
+          }
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) ck[r] = ck1[r];
         }
-        if (lane == 0) S.R[k * K + k] = beta;
+        if (lane == 0 && refl) S.R[k * K + k] = beta;
         __syncwarp();
       }
     }
