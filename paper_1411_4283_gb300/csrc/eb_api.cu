@@ -71,22 +71,22 @@ bool make_tables(int dim, int order, int mdeg, Tables* t) {
     for (int d = 0; d < 3; ++d) t->mon[i][d] = d < dim ? (int8_t)mon[i][d] : 0;
   }
   for (int d = 0; d < dim; ++d) {
-    int e = 0;
+    // lines of the shift along d: start from each monomial with exponent 0 along d
+    int nl = 0;
     for (int i = 0; i < t->K; ++i) {
-      for (int j = 0; j <= mon[i][d]; ++j) {
-        std::vector<int> q = mon[i];
-        q[d] = j;
-        if (e >= MAXSH) return false;
-        t->sh_out[d][e] = (uint8_t)i;
-        t->sh_in[d][e] = (uint8_t)idx[q];
-        t->sh_pw[d][e] = (uint8_t)(mon[i][d] - j);
-        double c = 1.0;
-        for (int k = 1; k <= j; ++k) c = c * (mon[i][d] - j + k) / k;  // C(p_d, j)
-        t->sh_c[d][e] = c;
-        ++e;
+      if (mon[i][d] != 0) continue;
+      int len = 0;
+      std::vector<int> q = mon[i];
+      while (true) {
+        auto it = idx.find(q);
+        if (it == idx.end()) break;
+        if (len >= MAXLN) return false;
+        t->ln_idx[d][nl][len++] = (uint8_t)it->second;
+        q[d] += 1;
       }
+      t->ln_len[d][nl++] = (uint8_t)len;
     }
-    t->nsh[d] = e;
+    t->nln[d] = nl;
     for (int i = 0; i < t->K; ++i) {
       if (mon[i][d] == 0) { t->lower[d][i] = -1; continue; }
       std::vector<int> q = mon[i];

@@ -416,20 +416,41 @@ __global__ void k_full_rows(Dims dm, const Tables* __restrict__ T, double* __res
   }
 }
 
-// (x + delta)^p moments from x^p moments, separable passes (binomial expansion)
-__device__ void shift_moments(const Tables& T, const double* __restrict__ in, const double* delta, double* out,
-                              double* tmp) {
+// Moments of (x + delta)^p from the moments of x^p, one dimension at a time.  Along a line of
+// monomials (exponents 0..N-1 in dimension d, the others fixed) the new moments are
+// m'_p = sum_{j <= p} C(p, j) delta^(p-j) m_j; N-1 sweeps of m_j += delta m_{j-1} (j descending)
+// build the binomial sums without forming binomials or powers (Horner's scheme for the Taylor
+// shift of a polynomial), N(N-1)/2 FMAs per line.
+template <int N>
+__device__ __forceinline__ void shift_line(double* out, const uint8_t* idx, double dl) {
+  double a[N];
+#pragma unroll
+  for (int p = 0; p < N; ++p) a[p] = out[idx[p]];
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+#pragma unroll
+    for (int j = N - 1; j >= i; --j) a[j] = fma(dl, a[j - 1], a[j]);
+#pragma unroll
+  for (int p = 1; p < N; ++p) out[idx[p]] = a[p];
+}
+
+__device__ void shift_moments(const Tables& T, const double* __restrict__ in, const double* delta, double* out) {
   const int K = T.K;
-  for (int i = 0; i < K; ++i) out[i] = in[i];
+  if (in != out)
+    for (int i = 0; i < K; ++i) out[i] = in[i];
   for (int d = 0; d < T.dim; ++d) {
-    double dl = delta[d];
+    const double dl = delta[d];
     if (dl == 0.0) continue;
-    double pw[8];
-    pw[0] = 1.0;
-    for (int e = 1; e < 8; ++e) pw[e] = pw[e - 1] * dl;
-    for (int i = 0; i < K; ++i) tmp[i] = 0.0;
-    for (int e = 0; e < T.nsh[d]; ++e) tmp[T.sh_out[d][e]] += T.sh_c[d][e] * pw[T.sh_pw[d][e]] * out[T.sh_in[d][e]];
-    for (int i = 0; i < K; ++i) out[i] = tmp[i];
+    for (int l = 0; l < T.nln[d]; ++l) {
+      const uint8_t* ix = T.ln_idx[d][l];
+      switch (T.ln_len[d][l]) {
+        case 2: shift_line<2>(out, ix, dl); break;
+        case 3: shift_line<3>(out, ix, dl); break;
+        case 4: shift_line<4>(out, ix, dl); break;
+        case 5: shift_line<5>(out, ix, dl); break;
+        default: break;
+      }
+    }
   }
 }
 
@@ -439,7 +460,7 @@ __device__ void shift_moments(const Tables& T, const double* __restrict__ in, co
 // and weight recorded in row[0..4], so that the warp can shift all pending rows of a chunk with
 // every lane busy (row_finish).  Wall rows over a cut face are shifted here.
 __device__ double row_prepare(const LsArgs& a, const Tables& T, uint32_t desc, const int* base, const double* x0s,
-                              double* row, double* tmp, int* bad, int* pend) {
+                              double* row, int* bad, int* pend) {
   const Dims& dm = a.dm;
   const int K = T.K;
   *pend = 0;
@@ -466,7 +487,7 @@ __device__ double row_prepare(const LsArgs& a, const Tables& T, uint32_t desc, c
     if (cf >= 0) {
       const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
       for (int i = 0; i < K; ++i) row[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
-      shift_moments(T, row, delta, row, tmp);
+      shift_moments(T, row, delta, row);
       double sc = w / row[0];
       for (int i = 0; i < K; ++i) row[i] *= sc;
       return w;
@@ -501,11 +522,11 @@ __device__ double row_prepare(const LsArgs& a, const Tables& T, uint32_t desc, c
 }
 
 // the moment shift and weighting of a pending row (record in row[0..4])
-__device__ void row_finish(const Tables& T, double* row, double* tmp) {
+__device__ void row_finish(const Tables& T, double* row) {
   const double* src = reinterpret_cast<const double*>((uintptr_t)__double_as_longlong(row[0]));
   const double delta[3] = {row[1], row[2], row[3]};
   const double w = row[4];
-  shift_moments(T, src, delta, row, tmp);
+  shift_moments(T, src, delta, row);
   const double sc = w / row[0];
   for (int i = 0; i < T.K; ++i) row[i] *= sc;
 }
@@ -601,7 +622,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         double* dst = S.C + li * KST;
         int pd = 0;
         if (i < n) {
-          scr_w[i] = row_prepare(a, T, a.row_desc[p0 + i], base, x0s, dst, S.P + lane * KST, &bad, &pd);
+          scr_w[i] = row_prepare(a, T, a.row_desc[p0 + i], base, x0s, dst, &bad, &pd);
         } else {
           for (int k = 0; k < K; ++k) dst[k] = 0.0;
         }
@@ -620,7 +641,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
           unsigned mk = pend[r];
           for (int t = 0; t < q; ++t) mk &= mk - 1;  // drop the q lowest set bits
           const int l = __ffs(mk) - 1;
-          row_finish(T, S.C + (l + 32 * r) * KST, S.P + lane * KST);
+          row_finish(T, S.C + (l + 32 * r) * KST);
         }
       }
       __syncwarp();

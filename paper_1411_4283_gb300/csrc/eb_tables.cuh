@@ -12,17 +12,18 @@
 
 namespace eb {
 
-constexpr int MAXSH = 128;  // entries of one separable shift pass (K=35 needs 70)
 constexpr int MAXD = 3;
+constexpr int MAXLN = 5;    // monomials on one line of the shift (exponents 0..4)
 
 struct Tables {
   int dim, K, KS, KFS;
   int8_t mon[MAXK][3];          // exponents of monomial i
-  // separable shift (x + delta)^p = sum_j C(p_d, j) delta_d^(p_d - j) x^(p with p_d -> j),
-  // applied for d = 0..dim-1: entry e of pass d: out[sh_out] += C * delta^sh_pw * in[sh_in]
-  int nsh[MAXD];
-  uint8_t sh_out[MAXD][MAXSH], sh_in[MAXD][MAXSH], sh_pw[MAXD][MAXSH];
-  double sh_c[MAXD][MAXSH];
+  // separable moment shift along d: the monomials whose other exponents agree form a line
+  // ln_idx[d][l][0..ln_len-1] ordered by the exponent along d (0, 1, ...); the shifted moments of a
+  // line are m'_p = sum_{j <= p} C(p, j) delta^(p-j) m_j, evaluated by repeated synthetic steps
+  int nln[MAXD];
+  uint8_t ln_len[MAXD][MAXK];
+  uint8_t ln_idx[MAXD][MAXK][MAXLN];
   // lower[d][i] = index of p_i - e_d (or -1 when p_d = 0)
   int8_t lower[MAXD][MAXK];
   // tangential map for faces normal to d: tang[d][i] = index of p_t in the (D-1)-dim stored
