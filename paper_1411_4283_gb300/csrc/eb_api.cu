@@ -23,7 +23,7 @@
 
 namespace eb {
 
-constexpr int LS_SMEM_PER_WARP = (int)sizeof(LsWarpSmem);
+constexpr int LS_SMEM_PER_SYS = (int)sizeof(LsSysSmem);
 
 // ------------------------------------------------------------------ errors
 
@@ -719,12 +719,12 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   int dev = 0, nsm = 0;
   EB_CUDA(cudaGetDevice(&dev));
   EB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  size_t ls_smem = (size_t)LS_WARPS * LS_SMEM_PER_WARP;
+  size_t ls_smem = (size_t)LS_SYS * LS_SMEM_PER_SYS;
   EB_CUDA(cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
-  int64_t nblocks = std::min<int64_t>(nsm, (n_slots + LS_WARPS - 1) / LS_WARPS);
+  int64_t nblocks = std::min<int64_t>(nsm, (n_slots + LS_SYS - 1) / LS_SYS);
   if (nblocks < 1) nblocks = 1;
   double* scratch;
-  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_WARPS * MAXROWS * (MAXK + 2)));
+  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_SYS * MAXROWS * (MAXK + 2)));
   double *ftab, *wtab;
   EB_TRY(tmp.get(&ftab, (size_t)TAB_N * MAXK));
   EB_TRY(tmp.get(&wtab, TAB_N));
@@ -733,7 +733,6 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   EB_TRY(tmp.get(&next, 1));
   EB_TRY(tmp.get(&status, n_slots));
   EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
-  EB_CUDA(cudaEventRecord(ev[2], s));
 
   LsArgs la;
   memset(&la, 0, sizeof(la));
@@ -760,9 +759,20 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   la.scratch = scratch;
   la.ftab = ftab;
   la.wtab = wtab;
+  int32_t* lerr;
+  EB_TRY(tmp.get(&lerr, 1));
+  EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
+  la.err = lerr;
+  EB_CUDA(cudaEventRecord(ev[2], s));
   if (n_slots > 0) k_lsq<<<(unsigned)nblocks, LS_WARPS * 32, ls_smem, s>>>(la, T); eb::count_launch();
   EB_CUDA(cudaGetLastError());
   EB_CUDA(cudaEventRecord(ev[3], s));
+  {
+    int32_t h = 0;
+    EB_CUDA(cudaMemcpyAsync(&h, lerr, 4, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    if (h) { set_error("a bounded device wait gave up in the least-squares kernel"); return EB_ERR_TIMEOUT; }
+  }
   {
     std::vector<int32_t> hs(n_slots);
     EB_CUDA(cudaMemcpyAsync(hs.data(), status, n_slots * 4, cudaMemcpyDeviceToHost, s));

@@ -536,16 +536,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Column sums of P[0..32)[c0 .. c0+mm) (mm <= 32/G columns): G lanes per column each sum 32/G
-// partials with independent accumulators, then a shuffle tree.  Returns the sum in the first lane
-// of each group; *col is the column (or -1).
-template <int G>
+// Column sums of P[0..32)[c0 + STR*c] for c < mm (mm <= 32/G columns): G lanes per column each sum
+// 32/G partials with independent accumulators, then a shuffle tree.  Returns the sum in the first
+// lane of each group; *col is the column number c (or -1).
+template <int G, int STR>
 __device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int lane, int* col) {
   constexpr int L = 32 / G;
   const int cl = lane / G, part = lane % G;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   if (cl < mm) {
-    const double* p = P + (part * L) * KST + c0 + cl;
+    const double* p = P + (part * L) * KST + c0 + STR * cl;
 #pragma unroll
     for (int l = 0; l < L; l += 4) {
       a0 += p[l * KST];
@@ -561,22 +561,57 @@ __device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int 
   return s;
 }
 
+template <int STR>
 __device__ __forceinline__ double column_sums(const double* P, int c0, int mm, int lane, int* col) {
-  if (mm > 16) return colsum_g<1>(P, c0, mm, lane, col);
-  if (mm > 8) return colsum_g<2>(P, c0, mm, lane, col);
-  if (mm > 4) return colsum_g<4>(P, c0, mm, lane, col);
-  if (mm > 2) return colsum_g<8>(P, c0, mm, lane, col);
-  if (mm > 1) return colsum_g<16>(P, c0, mm, lane, col);
-  return colsum_g<32>(P, c0, mm, lane, col);
+  if (mm > 16) return colsum_g<1, STR>(P, c0, mm, lane, col);
+  if (mm > 8) return colsum_g<2, STR>(P, c0, mm, lane, col);
+  if (mm > 4) return colsum_g<4, STR>(P, c0, mm, lane, col);
+  if (mm > 2) return colsum_g<8, STR>(P, c0, mm, lane, col);
+  if (mm > 1) return colsum_g<16, STR>(P, c0, mm, lane, col);
+  return colsum_g<32, STR>(P, c0, mm, lane, col);
 }
 
+constexpr uint32_t PAIR_WAIT_LIMIT = 1000000u;
+
+// Barrier of the two warps of one system: every lane arrives on the system's mbarrier (64 arrivals
+// complete a phase; arrive releases, the wait acquires), then waits for the phase.  The wait is
+// bounded: when it gives up it sets the error word and returns false, and the caller leaves the
+// kernel (its partner then gives up at its next barrier), so the kernel cannot hang on it.
+__device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& phase, int32_t* err) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+  bool ok = false;
+  for (uint32_t i = 0; i < PAIR_WAIT_LIMIT; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (done) { ok = true; break; }
+  }
+  if (!ok) atomicExch(err, 1);
+  phase ^= 1u;
+  return __all_sync(0xffffffffu, ok);
+}
+
+#define PAIR_SYNC()                                    \
+  do {                                                 \
+    if (!pair_sync(&S.bar, phase, a.err)) return;      \
+  } while (0)
+
+// One system (face) per pair of warps.  Both warps hold the chunk's rows (lane l: rows l + 32 r) and
+// the current Householder vector; warp h owns the columns j with j % 2 == h: their partial dots,
+// column sums, taus, R entries and updates.  Per Householder step the only exchange is column k+1
+// (the next vector), updated by its owner and read by the other warp after a pair barrier.
 __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid_constant__ Tables T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  LsWarpSmem& S = reinterpret_cast<LsWarpSmem*>(smem_raw)[warp];
+  const int sys = warp >> 1, h = warp & 1;
+  LsSysSmem& S = reinterpret_cast<LsSysSmem*>(smem_raw)[sys];
   const int K = T.K;
-  const int gw = blockIdx.x * LS_WARPS + warp;
-  double* scr = a.scratch + (int64_t)gw * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
+  const int gs = blockIdx.x * LS_SYS + sys;
+  double* scr = a.scratch + (int64_t)gs * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
   double* scr_w = scr + (int64_t)MAXROWS * MAXK;
   double* scr_t = scr_w + MAXROWS;
   const Dims& dm = a.dm;
@@ -585,10 +620,18 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
   double* z = S.vec + 2 * MAXK;
   double* tau = S.vec + 3 * MAXK;
   double* rinv = S.vec + 4 * MAXK;
+  if (h == 0 && lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.bar)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
   while (true) {
-    int s = 0;
-    if (lane == 0) s = atomicAdd(a.next, 1);
-    s = __shfl_sync(0xffffffffu, s, 0);
+    if (h == 0 && lane == 0) S.slot = atomicAdd(a.next, 1);
+    PAIR_SYNC();
+    const int s = S.slot;
     if (s >= a.n_slots) break;
     const int64_t p0 = a.row_ptr[s];
     const int n = (int)(a.row_ptr[s + 1] - p0);
@@ -609,16 +652,16 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
       x0s[dface] = -0.5;
     }
     int bad = 0;
-    for (int i = lane; i < K * K; i += 32) S.R[i] = 0.0;
-    __syncwarp();
+    for (int i = lane + 32 * h; i < K * K; i += 64) S.R[i] = 0.0;
     // ---- row-streamed Householder QR of B = W A: R accumulates the triangular factor
     for (int c0 = 0; c0 < n; c0 += CH) {
-      // rows of the chunk: table rows directly, shifted rows queued (one ballot mask per row slot)
-      unsigned pend[RPL];
+      // rows of the chunk (warp h builds the row slots 2h, 2h+1): table rows directly, shifted rows
+      // queued (one ballot mask per row slot) and shifted with every lane busy
+      unsigned pend[2];
       int npend = 0;
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        int li = lane + 32 * r, i = c0 + li;
+      for (int rr = 0; rr < 2; ++rr) {
+        const int li = lane + 32 * (2 * h + rr), i = c0 + li;
         double* dst = S.C + li * KST;
         int pd = 0;
         if (i < n) {
@@ -626,50 +669,51 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         } else {
           for (int k = 0; k < K; ++k) dst[k] = 0.0;
         }
-        pend[r] = __ballot_sync(0xffffffffu, pd);
-        npend += __popc(pend[r]);
+        pend[rr] = __ballot_sync(0xffffffffu, pd);
+        npend += __popc(pend[rr]);
       }
       __syncwarp();
-      for (int q0 = 0; q0 < npend; q0 += 32) {  // pending rows, 32 at a time
+      for (int q0 = 0; q0 < npend; q0 += 32) {
         int q = q0 + lane;
         if (q < npend) {
-          int r = 0;
-          while (q >= __popc(pend[r])) {
-            q -= __popc(pend[r]);
-            ++r;
+          int rr = 0;
+          if (q >= __popc(pend[0])) {
+            q -= __popc(pend[0]);
+            rr = 1;
           }
-          unsigned mk = pend[r];
+          unsigned mk = pend[rr];
           for (int t = 0; t < q; ++t) mk &= mk - 1;  // drop the q lowest set bits
           const int l = __ffs(mk) - 1;
-          row_finish(T, S.C + (l + 32 * r) * KST);
+          row_finish(T, S.C + (l + 32 * (2 * h + rr)) * KST);
         }
       }
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        int li = lane + 32 * r, i = c0 + li;
+      for (int rr = 0; rr < 2; ++rr) {
+        const int li = lane + 32 * (2 * h + rr), i = c0 + li;
         if (i < n) {
           const double* src = S.C + li * KST;
           for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = src[k];
         }
       }
+      PAIR_SYNC();  // the chunk's rows are complete
       // rows of this chunk per lane (the last chunk is short: skip its empty row slots)
       const int nr = (min(CH, n - c0) + 31) >> 5;
       // Householder steps k = 0..K-1 on [R; C].  The update of step k and the partial dot products of
-      // step k+1 share one pass over the chunk: column k+1 is updated first (it is step k+1's
-      // Householder vector), then every later column is loaded, updated, stored and dotted with it.
+      // step k+1 share one pass: column k+1 is updated first by its owner (it is step k+1's Householder
+      // vector), then each warp loads, updates, stores and dots its own later columns.
       double ck[RPL];
 #pragma unroll
       for (int r = 0; r < RPL; ++r) ck[r] = r < nr ? S.C[(lane + 32 * r) * KST] : 0.0;
-      {  // partial dots of column 0 with columns 1..K-1
-        const double* Cl = S.C + lane * KST + 1;
-        double* Pl = S.P + lane * KST;
-        for (int jj = 0; jj < K - 1; ++jj) {
+      double* Pl = S.P + lane * KST;
+      {  // partial dots of column 0 with the own columns j >= 1
+        const double* Cl = S.C + lane * KST;
+        for (int j = 1 + (h == 0 ? 1 : 0); j < K; j += 2) {
           double p0 = 0.0;
 #pragma unroll
           for (int r = 0; r < RPL; ++r)
-            if (r < nr) p0 = fma(ck[r], Cl[32 * r * KST + jj], p0);
-          Pl[jj] = p0;
+            if (r < nr) p0 = fma(ck[r], Cl[32 * r * KST + j], p0);
+          Pl[j] = p0;
         }
       }
       for (int k = 0; k < K; ++k) {
@@ -677,129 +721,115 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
 #pragma unroll
         for (int r = 0; r < RPL; ++r) ss = fma(ck[r], ck[r], ss);
         ss = warp_sum(ss);
-        const int m = K - k - 1;
         const bool refl = ss != 0.0;  // a zero chunk column needs no reflection
         const double alpha = S.R[k * K + k];
         const double sigma = refl ? sqrt(fma(alpha, alpha, ss)) : 0.0;
         const double beta = alpha > 0.0 ? -sigma : sigma;
         const double v0 = alpha - beta;
         const double gamma = refl ? -1.0 / (beta * v0) : 0.0;
-        __syncwarp();  // P holds the partial dots of column k with the later columns
-        for (int c1 = 0; c1 < m; c1 += 32) {
-          int mm = m - c1 < 32 ? m - c1 : 32;
+        __syncwarp();  // P holds the partial dots of column k with the own later columns
+        const int jf = k + 1 + (((k + 1) & 1) != h ? 1 : 0);  // first own column after k
+        const int mown = jf < K ? (K - 1 - jf) / 2 + 1 : 0;
+        for (int c1 = 0; c1 < mown; c1 += 32) {
+          const int mm = mown - c1 < 32 ? mown - c1 : 32;
           int col;
-          double sum = column_sums(S.P, c1, mm, lane, &col);
+          const double sum = column_sums<2>(S.P, jf + 2 * c1, mm, lane, &col);
           if (col >= 0) {
-            int jc = c1 + col, j = k + 1 + jc;
-            double rkj = S.R[k * K + j];
-            double t = gamma * fma(v0, rkj, sum);
+            const int j = jf + 2 * (c1 + col);
+            const double rkj = S.R[k * K + j];
+            const double t = gamma * fma(v0, rkj, sum);
             if (refl) S.R[k * K + j] = fma(-t, v0, rkj);
-            tau[jc] = t;
+            tau[j] = t;
           }
         }
         __syncwarp();
-        if (m > 0) {
-          // column k+1: update, keep as the next Householder vector
-          const double t1 = tau[0];
+        if (k + 1 < K) {
+          const int owner = (k + 1) & 1;
           double ck1[RPL];
+          if (h == owner) {  // column k+1: update, keep as the next Householder vector
+            const double t1 = tau[k + 1];
 #pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            double* c = S.C + (lane + 32 * r) * KST + k + 1;
-            ck1[r] = 0.0;
-            if (r < nr) {
-              ck1[r] = fma(-t1, ck[r], *c);
-              *c = ck1[r];
+            for (int r = 0; r < RPL; ++r) {
+              double* c = S.C + (lane + 32 * r) * KST + k + 1;
+              ck1[r] = 0.0;
+              if (r < nr) {
+                ck1[r] = fma(-t1, ck[r], *c);
+                *c = ck1[r];
+              }
             }
           }
-          // columns k+2..K-1: update and dot with column k+1 (four columns per pass)
-          const int m2 = m - 1;
-          double* Cw = S.C + lane * KST + k + 2;
-          double* Pl = S.P + lane * KST;
-          int jj = 0;
-          for (; jj + 4 <= m2; jj += 4) {
-            const double t0 = tau[jj + 1], tt1 = tau[jj + 2], t2 = tau[jj + 3], t3 = tau[jj + 4];
+          PAIR_SYNC();
+          if (h != owner) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) ck1[r] = r < nr ? S.C[(lane + 32 * r) * KST + k + 1] : 0.0;
+          }
+          // own columns j >= k+2: update and dot with column k+1 (four columns per pass)
+          int j = k + 2 + (((k + 2) & 1) != h ? 1 : 0);
+          for (; j + 6 < K; j += 8) {
+            const double t0 = tau[j], tt1 = tau[j + 2], t2 = tau[j + 4], t3 = tau[j + 6];
             double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               if (r < nr) {
-                double* c = Cw + 32 * r * KST + jj;
-                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[1]);
-                const double a2 = fma(-t2, ck[r], c[2]), a3 = fma(-t3, ck[r], c[3]);
+                double* c = S.C + (lane + 32 * r) * KST + j;
+                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[2]);
+                const double a2 = fma(-t2, ck[r], c[4]), a3 = fma(-t3, ck[r], c[6]);
                 c[0] = a0;
-                c[1] = a1;
-                c[2] = a2;
-                c[3] = a3;
+                c[2] = a1;
+                c[4] = a2;
+                c[6] = a3;
                 p0 = fma(ck1[r], a0, p0);
                 p1 = fma(ck1[r], a1, p1);
                 p2 = fma(ck1[r], a2, p2);
                 p3 = fma(ck1[r], a3, p3);
               }
             }
-            Pl[jj] = p0;
-            Pl[jj + 1] = p1;
-            Pl[jj + 2] = p2;
-            Pl[jj + 3] = p3;
+            Pl[j] = p0;
+            Pl[j + 2] = p1;
+            Pl[j + 4] = p2;
+            Pl[j + 6] = p3;
           }
-          for (; jj < m2; ++jj) {
-            const double t0 = tau[jj + 1];
+          for (; j < K; j += 2) {
+            const double t0 = tau[j];
             double p0 = 0.0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               if (r < nr) {
-                double* c = Cw + 32 * r * KST + jj;
+                double* c = S.C + (lane + 32 * r) * KST + j;
                 const double a0 = fma(-t0, ck[r], c[0]);
                 c[0] = a0;
                 p0 = fma(ck1[r], a0, p0);
               }
             }
-            Pl[jj] = p0;
+            Pl[j] = p0;
           }
 #pragma unroll
           for (int r = 0; r < RPL; ++r) ck[r] = ck1[r];
         }
-        if (lane == 0 && refl) S.R[k * K + k] = beta;
+        if (h == 0 && lane == 0 && refl) S.R[k * K + k] = beta;
         __syncwarp();
       }
+      PAIR_SYNC();  // both warps are done with the chunk and with R
     }
-    __syncwarp();
     // ---- rank check (|R_kk| <= 1e-12 max |R_jj| counts as rank deficient)
+    const int anyb = __any_sync(0xffffffffu, bad);
+    if (lane == 0) S.bad[h] = anyb;
+    PAIR_SYNC();
+    bad = (S.bad[0] || S.bad[1]) ? 2 : 0;
     double dmax = 0.0, dmin = INFINITY;
     for (int k = 0; k < K; ++k) {
       double v = fabs(S.R[k * K + k]);
       dmax = fmax(dmax, v);
       dmin = fmin(dmin, v);
     }
-    bad = __any_sync(0xffffffffu, bad) ? 2 : 0;
     if (!bad && !(dmin > 1e-12 * dmax)) bad = 1;
     if (bad) {
-      if (lane == 0) a.status[s] = bad;
-      for (int i = lane; i < n; i += 32) a.row_val[p0 + i] = 0.0;
-      __syncwarp();
+      if (h == 0 && lane == 0) a.status[s] = bad;
+      for (int i = lane + 32 * h; i < n; i += 64) a.row_val[p0 + i] = 0.0;
+      PAIR_SYNC();
       continue;
     }
-    for (int k = lane; k < K; k += 32) rinv[k] = 1.0 / S.R[k * K + k];
-    // ---- F_hat (Sec. 2.2.1): grid face: p_d m_f^{p-e_d}; EB face: sum_d p_d m_{d,f}^{p-e_d}
-    for (int i = lane; i < K; i += 32) {
-      double f = 0.0;
-      if (cut_self >= 0) {
-        for (int d = 0; d < dm.dim; ++d) {
-          const double* nm = a.eb_nmom + ((int64_t)cut_self * dm.dim + d) * dm.KS;
-          if (T.lower[d][i] >= 0) f += (double)T.mon[i][d] * nm[T.lower[d][i]];
-        }
-      } else {
-        int q = T.lower[dface][i];
-        if (q >= 0) {
-          int32_t cf = a.cutface_of[dface][flocal];
-          double mq;
-          if (cf >= 0) mq = T.tang[dface][q] >= 0 ? a.face_mom[dface][(int64_t)cf * dm.KFS + T.tang[dface][q]] : 0.0;
-          else mq = T.full_face[dface][q];
-          f = (double)T.mon[i][dface] * mq;
-        }
-      }
-      F[i] = f;
-    }
-    __syncwarp();
-    // ---- z = R^-1 R^-T rhs (two triangular solves, lanes own columns)
+    // ---- z = R^-1 R^-T rhs (two triangular solves, lanes own columns), by warp 0
     auto solve_rtr = [&](const double* rhs, double* outz) {
       for (int j = lane; j < K; j += 32) y[j] = rhs[j];
       __syncwarp();
@@ -820,32 +850,64 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         __syncwarp();
       }
     };
-    solve_rtr(F, z);
+    if (h == 0) {
+      for (int k = lane; k < K; k += 32) rinv[k] = 1.0 / S.R[k * K + k];
+      // ---- F_hat (Sec. 2.2.1): grid face: p_d m_f^{p-e_d}; EB face: sum_d p_d m_{d,f}^{p-e_d}
+      for (int i = lane; i < K; i += 32) {
+        double f = 0.0;
+        if (cut_self >= 0) {
+          for (int d = 0; d < dm.dim; ++d) {
+            const double* nm = a.eb_nmom + ((int64_t)cut_self * dm.dim + d) * dm.KS;
+            if (T.lower[d][i] >= 0) f += (double)T.mon[i][d] * nm[T.lower[d][i]];
+          }
+        } else {
+          int q = T.lower[dface][i];
+          if (q >= 0) {
+            int32_t cf = a.cutface_of[dface][flocal];
+            double mq;
+            if (cf >= 0) mq = T.tang[dface][q] >= 0 ? a.face_mom[dface][(int64_t)cf * dm.KFS + T.tang[dface][q]] : 0.0;
+            else mq = T.full_face[dface][q];
+            f = (double)T.mon[i][dface] * mq;
+          }
+        }
+        F[i] = f;
+      }
+      __syncwarp();
+      solve_rtr(F, z);
+    }
+    PAIR_SYNC();
     // ---- corrected semi-normal equations: t1 = B z, r = F - B^T t1, t = t1 + B R^-1 R^-T r
-    for (int k = 0; k < K; ++k) S.P[lane * KST + k] = 0.0;
-    for (int i = lane; i < n; i += 32) {
+    // (rows split between the warps; warp 1 accumulates B^T t1 in the free chunk buffer)
+    double* Pw = h == 0 ? S.P : S.C;
+    for (int k = 0; k < K; ++k) Pw[lane * KST + k] = 0.0;
+    for (int i = lane + 32 * h; i < n; i += 64) {
       double t1 = 0.0;
       for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
       scr_t[i] = t1;
-      for (int k = 0; k < K; ++k) S.P[lane * KST + k] = fma(scr[(int64_t)k * MAXROWS + i], t1, S.P[lane * KST + k]);
+      for (int k = 0; k < K; ++k) Pw[lane * KST + k] = fma(scr[(int64_t)k * MAXROWS + i], t1, Pw[lane * KST + k]);
     }
     __syncwarp();
     for (int c1 = 0; c1 < K; c1 += 32) {
       int mm = K - c1 < 32 ? K - c1 : 32;
       int col;
-      double sum = column_sums(S.P, c1, mm, lane, &col);
-      if (col >= 0) tau[c1 + col] = F[c1 + col] - sum;
+      double sum = column_sums<1>(Pw, c1, mm, lane, &col);
+      if (col >= 0) S.xch[h * MAXK + c1 + col] = sum;
     }
-    __syncwarp();
-    double* z2 = S.C;  // chunk buffer is free now
-    solve_rtr(tau, z2);
-    for (int i = lane; i < n; i += 32) {
+    PAIR_SYNC();
+    double* z2 = S.C + CH * KST - 2 * MAXK;  // the chunk buffer's tail is free after the exchange
+    if (h == 0) {
+      for (int c = lane; c < K; c += 32) tau[c] = F[c] - (S.xch[c] + S.xch[MAXK + c]);
+      __syncwarp();
+      solve_rtr(tau, z2);
+    }
+    PAIR_SYNC();
+    for (int i = lane + 32 * h; i < n; i += 64) {
       double t = scr_t[i];
       for (int k = 0; k < K; ++k) t = fma(scr[(int64_t)k * MAXROWS + i], z2[k], t);
       a.row_val[p0 + i] = scr_w[i] * t;  // s_hat = W t
     }
-    if (lane == 0) a.status[s] = 0;
-    __syncwarp();
+    if (h == 0 && lane == 0) a.status[s] = 0;
+    PAIR_SYNC();
   }
 }
 

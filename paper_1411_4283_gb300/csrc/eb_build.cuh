@@ -27,18 +27,24 @@ struct GatherArgs {
   int32_t* too_many;         // capacity flag
 };
 
-constexpr int LS_WARPS = 4;
+constexpr int LS_SYS = 4;              // systems in flight per CTA (shared memory bound)
+constexpr int LS_WARPS = 2 * LS_SYS;   // two warps per system: 8 warps per SM, 2 per scheduler
 constexpr int RPL = 4;        // rows per lane per chunk
 constexpr int CH = 32 * RPL;  // rows per chunk
 constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
 
-struct LsWarpSmem {
+struct LsSysSmem {
   double R[MAXK * MAXK];  // triangular factor, row-major
   double C[CH * KST];     // current chunk of weighted rows
-  double P[32 * KST];     // partial dot products / per-lane scratch
+  double P[32 * KST];     // partial dot products, column j in P[lane][j] (each column owned by one warp)
   double vec[5 * MAXK];   // F, y, z, tau, 1/R_kk
+  double xch[2 * MAXK];   // the two warps' partial sums (corrected semi-normal equations)
+  unsigned long long bar; // pair barrier (mbarrier, two arrivals per phase)
+  int32_t slot;           // system being solved
+  int32_t bad[2];         // per-warp row flags
+  int32_t pad[3];
 };
-static_assert(sizeof(LsWarpSmem) % 16 == 0, "per-warp blocks stay 16-byte aligned");
+static_assert(sizeof(LsSysSmem) % 16 == 0, "per-system blocks stay 16-byte aligned");
 
 // offsets in units of h/2 span [-11, 11] on each axis (volume, EB and wall rows)
 constexpr int TAB_S = 23;
@@ -63,7 +69,8 @@ struct LsArgs {
   int64_t n_slots;
   int32_t* next;       // work counter
   int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row
-  double* scratch;     // per warp: MAXROWS * (K + 2) doubles, column-major rows
+  double* scratch;     // per system slot: MAXROWS * (K + 2) doubles, column-major rows
+  int32_t* err;        // set when a bounded wait between the two warps of a system gives up
   const double* ftab;  // [TAB_N][MAXK] weighted rows of full cells, by offset
   const double* wtab;  // [TAB_N] weights, by offset
 };
