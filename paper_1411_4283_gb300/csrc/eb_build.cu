@@ -716,17 +716,29 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
           Pl[j] = p0;
         }
       }
-      for (int k = 0; k < K; ++k) {
+      // Householder scalars of step k from its vector (chunk part c, R part alpha = R_kk)
+      auto hscalars = [&](const double* c, int k, double* out) {
         double ss = 0.0;
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) ss = fma(ck[r], ck[r], ss);
+        for (int r = 0; r < RPL; ++r) ss = fma(c[r], c[r], ss);
         ss = warp_sum(ss);
         const bool refl = ss != 0.0;  // a zero chunk column needs no reflection
         const double alpha = S.R[k * K + k];
         const double sigma = refl ? sqrt(fma(alpha, alpha, ss)) : 0.0;
-        const double beta = alpha > 0.0 ? -sigma : sigma;
-        const double v0 = alpha - beta;
-        const double gamma = refl ? -1.0 / (beta * v0) : 0.0;
+        out[0] = alpha > 0.0 ? -sigma : sigma;        // beta
+        out[1] = alpha - out[0];                       // v0
+        out[2] = refl ? -1.0 / (out[0] * out[1]) : 0.0;  // gamma
+        out[3] = refl ? 1.0 : 0.0;
+      };
+      double hk[4];
+      hscalars(ck, 0, hk);  // step 0: both warps (the vector is column 0)
+      for (int k = 0; k < K; ++k) {
+        if (k > 0) {  // step k's scalars: computed once by the owner of column k during step k-1
+#pragma unroll
+          for (int q = 0; q < 4; ++q) hk[q] = S.hs[k & 1][q];
+        }
+        const double beta = hk[0], v0 = hk[1], gamma = hk[2];
+        const bool refl = hk[3] != 0.0;
         __syncwarp();  // P holds the partial dots of column k with the own later columns
         const int jf = k + 1 + (((k + 1) & 1) != h ? 1 : 0);  // first own column after k
         const int mown = jf < K ? (K - 1 - jf) / 2 + 1 : 0;
@@ -756,6 +768,12 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
                 ck1[r] = fma(-t1, ck[r], *c);
                 *c = ck1[r];
               }
+            }
+            double hn[4];
+            hscalars(ck1, k + 1, hn);  // R_{k+1,k+1} is not touched by step k
+            if (lane == 0) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) S.hs[(k + 1) & 1][q] = hn[q];
             }
           }
           PAIR_SYNC();

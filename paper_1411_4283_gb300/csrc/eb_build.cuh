@@ -39,6 +39,7 @@ struct LsSysSmem {
   double P[32 * KST];     // partial dot products, column j in P[lane][j] (each column owned by one warp)
   double vec[5 * MAXK];   // F, y, z, tau, 1/R_kk
   double xch[2 * MAXK];   // the two warps' partial sums (corrected semi-normal equations)
+  double hs[2][4];        // Householder scalars (beta, v0, gamma, reflect) of step k in hs[k % 2]
   unsigned long long bar; // pair barrier (mbarrier, two arrivals per phase)
   int32_t slot;           // system being solved
   int32_t bad[2];         // per-warp row flags
