@@ -625,9 +625,11 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
                  "r"(64)
                  : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.hs_seq[0] = S.hs_seq[1] = -1;
   }
   __syncthreads();
   uint32_t phase = 0;
+  int32_t stepno = 0;  // Householder steps taken by this pair (same count in both warps)
   while (true) {
     if (h == 0 && lane == 0) S.slot = atomicAdd(a.next, 1);
     PAIR_SYNC();
@@ -730,12 +732,26 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         out[2] = refl ? -1.0 / (out[0] * out[1]) : 0.0;  // gamma
         out[3] = refl ? 1.0 : 0.0;
       };
-      double hk[4];
+      double hk[4], hnext[4] = {0.0, 0.0, 0.0, 0.0};
       hscalars(ck, 0, hk);  // step 0: both warps (the vector is column 0)
-      for (int k = 0; k < K; ++k) {
-        if (k > 0) {  // step k's scalars: computed once by the owner of column k during step k-1
+      for (int k = 0; k < K; ++k, ++stepno) {
+        if (k > 0 && h != (k & 1)) {
+          // step k's scalars, computed once by the owner of column k during step k-1 and posted with the
+          // step number after the values (bounded wait; giving up sets the error word and leaves)
+          volatile int32_t* seq = &S.hs_seq[k & 1];
+          uint32_t it = 0;
+          while (*seq != stepno && ++it < PAIR_WAIT_LIMIT) {
+          }
+          if (it >= PAIR_WAIT_LIMIT) {
+            atomicExch(a.err, 1);
+            return;
+          }
+          __threadfence_block();
 #pragma unroll
           for (int q = 0; q < 4; ++q) hk[q] = S.hs[k & 1][q];
+        } else if (k > 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) hk[q] = hnext[q];  // this warp computed them in step k-1
         }
         const double beta = hk[0], v0 = hk[1], gamma = hk[2];
         const bool refl = hk[3] != 0.0;
@@ -769,17 +785,23 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
                 *c = ck1[r];
               }
             }
-            double hn[4];
-            hscalars(ck1, k + 1, hn);  // R_{k+1,k+1} is not touched by step k
-            if (lane == 0) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) S.hs[(k + 1) & 1][q] = hn[q];
-            }
           }
           PAIR_SYNC();
           if (h != owner) {
 #pragma unroll
             for (int r = 0; r < RPL; ++r) ck1[r] = r < nr ? S.C[(lane + 32 * r) * KST + k + 1] : 0.0;
+          } else {
+            // step k+1's scalars, off the other warp's path: it picks them up at the start of step k+1
+            double hn[4];
+            hscalars(ck1, k + 1, hn);  // R_{k+1,k+1} is not touched by step k
+            if (lane == 0) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) S.hs[(k + 1) & 1][q] = hn[q];
+              __threadfence_block();
+              *(volatile int32_t*)&S.hs_seq[(k + 1) & 1] = stepno + 1;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hnext[q] = hn[q];
           }
           // own columns j >= k+2: update and dot with column k+1 (four columns per pass)
           int j = k + 2 + (((k + 2) & 1) != h ? 1 : 0);

@@ -43,7 +43,8 @@ struct LsSysSmem {
   unsigned long long bar; // pair barrier (mbarrier, two arrivals per phase)
   int32_t slot;           // system being solved
   int32_t bad[2];         // per-warp row flags
-  int32_t pad[3];
+  int32_t hs_seq[2];      // step number whose scalars hs[k % 2] holds (posted after the values)
+  int32_t pad;
 };
 static_assert(sizeof(LsSysSmem) % 16 == 0, "per-system blocks stay 16-byte aligned");
 
