@@ -600,14 +600,15 @@ __device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& pha
     if (!pair_sync(&S.bar, phase, a.err)) return;      \
   } while (0)
 
-// One system (face) per pair of warps.  Both warps hold the chunk's rows (lane l: rows l + 32 r) and
-// the current Householder vector; warp h owns the columns j with j % 2 == h: their partial dots,
-// column sums, taus, R entries and updates.  Per Householder step the only exchange is column k+1
-// (the next vector), updated by its owner and read by the other warp after a pair barrier.
+// One system (face) per group of LS_NW warps.  Every warp holds the chunk's rows (lane l: rows
+// l + 32 r) and the current Householder vector; warp h owns the columns j with j % LS_NW == h: their
+// partial dots, column sums, taus, R entries and updates.  Per Householder step the exchanges are
+// column k+1 (the next vector, updated by its owner and read by the others after a group barrier)
+// and its scalars (posted by the owner with a sequence flag and read at the start of the next step).
 __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid_constant__ Tables T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sys = warp >> 1, h = warp & 1;
+  const int sys = warp / LS_NW, h = warp % LS_NW;
   LsSysSmem& S = reinterpret_cast<LsSysSmem*>(smem_raw)[sys];
   const int K = T.K;
   const int gs = blockIdx.x * LS_SYS + sys;
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
   double* rinv = S.vec + 4 * MAXK;
   if (h == 0 && lane == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.bar)),
-                 "r"(64)
+                 "r"(32 * LS_NW)
                  : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.hs_seq[0] = S.hs_seq[1] = -1;
@@ -654,16 +655,20 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
       x0s[dface] = -0.5;
     }
     int bad = 0;
-    for (int i = lane + 32 * h; i < K * K; i += 64) S.R[i] = 0.0;
+    for (int i = lane + 32 * h; i < K * K; i += 32 * LS_NW) S.R[i] = 0.0;
     // ---- row-streamed Householder QR of B = W A: R accumulates the triangular factor
     for (int c0 = 0; c0 < n; c0 += CH) {
-      // rows of the chunk (warp h builds the row slots 2h, 2h+1): table rows directly, shifted rows
-      // queued (one ballot mask per row slot) and shifted with every lane busy
-      unsigned pend[2];
+      // rows of the chunk (warp h builds the row slots r with r % LS_NW == h): table rows directly,
+      // shifted rows queued (one ballot mask per row slot) and shifted with every lane busy
+      constexpr int NSLOT = (RPL + LS_NW - 1) / LS_NW;
+      unsigned pend[NSLOT];
       int npend = 0;
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int li = lane + 32 * (2 * h + rr), i = c0 + li;
+      for (int rr = 0; rr < NSLOT; ++rr) {
+        const int r = h + LS_NW * rr;
+        pend[rr] = 0u;
+        if (r >= RPL) continue;
+        const int li = lane + 32 * r, i = c0 + li;
         double* dst = S.C + li * KST;
         int pd = 0;
         if (i < n) {
@@ -679,20 +684,22 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         int q = q0 + lane;
         if (q < npend) {
           int rr = 0;
-          if (q >= __popc(pend[0])) {
-            q -= __popc(pend[0]);
-            rr = 1;
+          while (q >= __popc(pend[rr])) {
+            q -= __popc(pend[rr]);
+            ++rr;
           }
           unsigned mk = pend[rr];
           for (int t = 0; t < q; ++t) mk &= mk - 1;  // drop the q lowest set bits
           const int l = __ffs(mk) - 1;
-          row_finish(T, S.C + (l + 32 * (2 * h + rr)) * KST);
+          row_finish(T, S.C + (l + 32 * (h + LS_NW * rr)) * KST);
         }
       }
       __syncwarp();
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int li = lane + 32 * (2 * h + rr), i = c0 + li;
+      for (int rr = 0; rr < NSLOT; ++rr) {
+        const int r = h + LS_NW * rr;
+        if (r >= RPL) continue;
+        const int li = lane + 32 * r, i = c0 + li;
         if (i < n) {
           const double* src = S.C + li * KST;
           for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = src[k];
@@ -710,7 +717,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
       double* Pl = S.P + lane * KST;
       {  // partial dots of column 0 with the own columns j >= 1
         const double* Cl = S.C + lane * KST;
-        for (int j = 1 + (h == 0 ? 1 : 0); j < K; j += 2) {
+        for (int j = 1 + (h + LS_NW - 1) % LS_NW; j < K; j += LS_NW) {
           double p0 = 0.0;
 #pragma unroll
           for (int r = 0; r < RPL; ++r)
@@ -735,7 +742,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
       double hk[4], hnext[4] = {0.0, 0.0, 0.0, 0.0};
       hscalars(ck, 0, hk);  // step 0: both warps (the vector is column 0)
       for (int k = 0; k < K; ++k, ++stepno) {
-        if (k > 0 && h != (k & 1)) {
+        if (k > 0 && h != k % LS_NW) {
           // step k's scalars, computed once by the owner of column k during step k-1 and posted with the
           // step number after the values (bounded wait; giving up sets the error word and leaves)
           volatile int32_t* seq = &S.hs_seq[k & 1];
@@ -756,14 +763,14 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         const double beta = hk[0], v0 = hk[1], gamma = hk[2];
         const bool refl = hk[3] != 0.0;
         __syncwarp();  // P holds the partial dots of column k with the own later columns
-        const int jf = k + 1 + (((k + 1) & 1) != h ? 1 : 0);  // first own column after k
-        const int mown = jf < K ? (K - 1 - jf) / 2 + 1 : 0;
+        const int jf = k + 1 + (h + LS_NW - (k + 1) % LS_NW) % LS_NW;  // first own column after k
+        const int mown = jf < K ? (K - 1 - jf) / LS_NW + 1 : 0;
         for (int c1 = 0; c1 < mown; c1 += 32) {
           const int mm = mown - c1 < 32 ? mown - c1 : 32;
           int col;
-          const double sum = column_sums<2>(S.P, jf + 2 * c1, mm, lane, &col);
+          const double sum = column_sums<LS_NW>(S.P, jf + LS_NW * c1, mm, lane, &col);
           if (col >= 0) {
-            const int j = jf + 2 * (c1 + col);
+            const int j = jf + LS_NW * (c1 + col);
             const double rkj = S.R[k * K + j];
             const double t = gamma * fma(v0, rkj, sum);
             if (refl) S.R[k * K + j] = fma(-t, v0, rkj);
@@ -772,7 +779,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
         }
         __syncwarp();
         if (k + 1 < K) {
-          const int owner = (k + 1) & 1;
+          const int owner = (k + 1) % LS_NW;
           double ck1[RPL];
           if (h == owner) {  // column k+1: update, keep as the next Householder vector
             const double t1 = tau[k + 1];
@@ -804,20 +811,21 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
             for (int q = 0; q < 4; ++q) hnext[q] = hn[q];
           }
           // own columns j >= k+2: update and dot with column k+1 (four columns per pass)
-          int j = k + 2 + (((k + 2) & 1) != h ? 1 : 0);
-          for (; j + 6 < K; j += 8) {
-            const double t0 = tau[j], tt1 = tau[j + 2], t2 = tau[j + 4], t3 = tau[j + 6];
+          constexpr int W = LS_NW;
+          int j = k + 2 + (h + W - (k + 2) % W) % W;
+          for (; j + 3 * W < K; j += 4 * W) {
+            const double t0 = tau[j], tt1 = tau[j + W], t2 = tau[j + 2 * W], t3 = tau[j + 3 * W];
             double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               if (r < nr) {
                 double* c = S.C + (lane + 32 * r) * KST + j;
-                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[2]);
-                const double a2 = fma(-t2, ck[r], c[4]), a3 = fma(-t3, ck[r], c[6]);
+                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[W]);
+                const double a2 = fma(-t2, ck[r], c[2 * W]), a3 = fma(-t3, ck[r], c[3 * W]);
                 c[0] = a0;
-                c[2] = a1;
-                c[4] = a2;
-                c[6] = a3;
+                c[W] = a1;
+                c[2 * W] = a2;
+                c[3 * W] = a3;
                 p0 = fma(ck1[r], a0, p0);
                 p1 = fma(ck1[r], a1, p1);
                 p2 = fma(ck1[r], a2, p2);
@@ -825,11 +833,11 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
               }
             }
             Pl[j] = p0;
-            Pl[j + 2] = p1;
-            Pl[j + 4] = p2;
-            Pl[j + 6] = p3;
+            Pl[j + W] = p1;
+            Pl[j + 2 * W] = p2;
+            Pl[j + 3 * W] = p3;
           }
-          for (; j < K; j += 2) {
+          for (; j < K; j += W) {
             const double t0 = tau[j];
             double p0 = 0.0;
 #pragma unroll
@@ -855,7 +863,11 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
     const int anyb = __any_sync(0xffffffffu, bad);
     if (lane == 0) S.bad[h] = anyb;
     PAIR_SYNC();
-    bad = (S.bad[0] || S.bad[1]) ? 2 : 0;
+    {
+      int any = 0;
+      for (int q = 0; q < LS_NW; ++q) any |= S.bad[q];
+      bad = any ? 2 : 0;
+    }
     double dmax = 0.0, dmin = INFINITY;
     for (int k = 0; k < K; ++k) {
       double v = fabs(S.R[k * K + k]);
@@ -865,7 +877,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
     if (!bad && !(dmin > 1e-12 * dmax)) bad = 1;
     if (bad) {
       if (h == 0 && lane == 0) a.status[s] = bad;
-      for (int i = lane + 32 * h; i < n; i += 64) a.row_val[p0 + i] = 0.0;
+      for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) a.row_val[p0 + i] = 0.0;
       PAIR_SYNC();
       continue;
     }
@@ -917,10 +929,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
     }
     PAIR_SYNC();
     // ---- corrected semi-normal equations: t1 = B z, r = F - B^T t1, t = t1 + B R^-1 R^-T r
-    // (rows split between the warps; warp 1 accumulates B^T t1 in the free chunk buffer)
-    double* Pw = h == 0 ? S.P : S.C;
+    // (rows split between the warps; warps h > 0 accumulate B^T t1 in the free chunk buffer)
+    double* Pw = h == 0 ? S.P : S.C + (h - 1) * 32 * KST;
     for (int k = 0; k < K; ++k) Pw[lane * KST + k] = 0.0;
-    for (int i = lane + 32 * h; i < n; i += 64) {
+    for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
       double t1 = 0.0;
       for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
       scr_t[i] = t1;
@@ -936,12 +948,16 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
     PAIR_SYNC();
     double* z2 = S.C + CH * KST - 2 * MAXK;  // the chunk buffer's tail is free after the exchange
     if (h == 0) {
-      for (int c = lane; c < K; c += 32) tau[c] = F[c] - (S.xch[c] + S.xch[MAXK + c]);
+      for (int c = lane; c < K; c += 32) {
+        double sx = 0.0;
+        for (int q = 0; q < LS_NW; ++q) sx += S.xch[q * MAXK + c];
+        tau[c] = F[c] - sx;
+      }
       __syncwarp();
       solve_rtr(tau, z2);
     }
     PAIR_SYNC();
-    for (int i = lane + 32 * h; i < n; i += 64) {
+    for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
       double t = scr_t[i];
       for (int k = 0; k < K; ++k) t = fma(scr[(int64_t)k * MAXROWS + i], z2[k], t);
       a.row_val[p0 + i] = scr_w[i] * t;  // s_hat = W t

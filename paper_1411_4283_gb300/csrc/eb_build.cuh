@@ -28,23 +28,23 @@ struct GatherArgs {
 };
 
 constexpr int LS_SYS = 4;              // systems in flight per CTA (shared memory bound)
-constexpr int LS_WARPS = 2 * LS_SYS;   // two warps per system: 8 warps per SM, 2 per scheduler
+constexpr int LS_NW = 2;               // warps per system (each owns the columns j with j % LS_NW == its rank)
+constexpr int LS_WARPS = LS_NW * LS_SYS;
 constexpr int RPL = 4;        // rows per lane per chunk
 constexpr int CH = 32 * RPL;  // rows per chunk
 constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
 
-struct LsSysSmem {
-  double R[MAXK * MAXK];  // triangular factor, row-major
-  double C[CH * KST];     // current chunk of weighted rows
-  double P[32 * KST];     // partial dot products, column j in P[lane][j] (each column owned by one warp)
-  double vec[5 * MAXK];   // F, y, z, tau, 1/R_kk
-  double xch[2 * MAXK];   // the two warps' partial sums (corrected semi-normal equations)
-  double hs[2][4];        // Householder scalars (beta, v0, gamma, reflect) of step k in hs[k % 2]
-  unsigned long long bar; // pair barrier (mbarrier, two arrivals per phase)
-  int32_t slot;           // system being solved
-  int32_t bad[2];         // per-warp row flags
-  int32_t hs_seq[2];      // step number whose scalars hs[k % 2] holds (posted after the values)
-  int32_t pad;
+struct __align__(16) LsSysSmem {
+  double R[MAXK * MAXK];     // triangular factor, row-major
+  double C[CH * KST];        // current chunk of weighted rows
+  double P[32 * KST];        // partial dot products, column j in P[lane][j] (each column owned by one warp)
+  double vec[5 * MAXK];      // F, y, z, tau, 1/R_kk
+  double xch[LS_NW * MAXK];  // the warps' partial sums (corrected semi-normal equations)
+  double hs[2][4];           // Householder scalars (beta, v0, gamma, reflect) of step k in hs[k % 2]
+  unsigned long long bar;    // barrier of the system's warps (mbarrier, 32 * LS_NW arrivals per phase)
+  int32_t slot;              // system being solved
+  int32_t bad[LS_NW];        // per-warp row flags
+  int32_t hs_seq[2];         // step number whose scalars hs[k % 2] holds (posted after the values)
 };
 static_assert(sizeof(LsSysSmem) % 16 == 0, "per-system blocks stay 16-byte aligned");
 
