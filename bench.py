@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cut-face LS stencils/s; EB Laplacian apply GB/s (% HBM); solve s at fixed error"
-LSQ_DRAM_BYTES_PER_SYSTEM = 815.65e6 / 90123
+LSQ_DRAM_BYTES_PER_SYSTEM = 911.65e6 / 90123
 
 
 def parse():
@@ -301,7 +301,7 @@ def main():
     lsq_share = lsq_ms / ms_step
     if lsq_share >= apply_share:
         # DRAM traffic of k_lsq: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 48^3
-        # sphere workload (815.6 MB for 90,123 systems), scaled by the systems of this launch
+        # sphere workload (911.6 MB for 90,123 systems), scaled by the systems of this launch
         traffic = LSQ_DRAM_BYTES_PER_SYSTEM * (bi["n_unique_faces"] + bi["n_classes"]) if args.order == 4 else None
         roof = {"kernel": "k_lsq (FP64 weighted least squares)", "bound": "alu", "achieved": lsq_tflops,
                 "peak": fp64_pk, "unit": "TFLOP/s", "frac": lsq_tflops / fp64_pk, "traffic": traffic,

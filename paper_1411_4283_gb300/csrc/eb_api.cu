@@ -1298,10 +1298,16 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
     EB_TRY(tmp.get(&x32, n));
     ApplyArgs<float> A32 = apply_args<float>(st, 1);
     int total = 0;
+    bool phi_nonzero = true;  // a zero initial guess needs no FP64 apply for the first residual
+    EB_CUDA(any_nonzero64(n, phi, reinterpret_cast<int32_t*>(dscr), &phi_nonzero, s));
     for (int sweep = 0;; ++sweep) {
-      A64.phi = phi;
-      A64.y = y64;
-      EB_CUDA(launch_apply<double>(A64, s));
+      if (sweep > 0 || phi_nonzero) {
+        A64.phi = phi;
+        A64.y = y64;
+        EB_CUDA(launch_apply<double>(A64, s));
+      } else {
+        EB_CUDA(vec_fill64(n, y64, 0.0, s));
+      }
       EB_CUDA(resid64(n, rhs, y64, r64, s));
       double rn = 0.0;
       EB_CUDA(norm2_64(n, r64, dscr, &rn, s));

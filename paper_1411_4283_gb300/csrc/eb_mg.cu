@@ -48,7 +48,7 @@ __global__ void k_mg_fine(int dim, int nx, int ny, int nz, double h, const uint8
                           const uint8_t* ff0, const uint8_t* ff1, const uint8_t* ff2, const int32_t* cf0,
                           const int32_t* cf1, const int32_t* cf2, const double* fm0, const double* fm1,
                           const double* fm2, int KFS, const double* __restrict__ dinv_high, float* cp0, float* cp1,
-                          float* cp2, float* diag, uint8_t* weak) {
+                          float* cp2, float* diag, int32_t* weak, int32_t* nweak, int cap) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t ncell = (int64_t)nx * ny * nz;
   if (c >= ncell) return;
@@ -75,12 +75,14 @@ __global__ void k_mg_fine(int dim, int nx, int ny, int nz, double h, const uint8
       if (side) cp[d][c] = (float)(wall ? 0.0 : a * ih2);
     }
   }
-  weak[c] = 0;
   if (flag[c] == 0) { diag[c] = 0.0f; return; }
   double dg = -sum * ih2;
   if (flag[c] == 2) {
     const double dh = dinv_high[c] != 0.0 ? 1.0 / dinv_high[c] : 0.0;  // diagonal of the high-order operator
-    weak[c] = dh > 0.5 * dg;         // weaker than half the 7-point diagonal, zero or positive
+    if (dh > 0.5 * dg) {             // weaker than half the 7-point diagonal, zero or positive
+      const int q = atomicAdd(nweak, 1);
+      if (q < cap) weak[q] = (int32_t)c;
+    }
     if (dh < dg) dg = dh;            // add a non-negative EB term e_v
   }
   diag[c] = (float)dg;
@@ -501,32 +503,37 @@ static RowSrc row_src(const Multigrid& mg) {
 
 // blocks around the weak-diagonal cut cells (3 x 3 x 3, or 3 x 3 in 2-D with the other entries padding):
 // cell lists on the host, A_BB and its inverse on the device
-static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const uint8_t* weak_d, cudaStream_t s) {
+// cells of the block around weak cell list[b]: the 3x3x3 box (in the domain, not covered), -1 elsewhere
+__global__ void k_blk_cells(const int32_t* __restrict__ list, int nb, int nx, int ny, int nz,
+                            const uint8_t* __restrict__ flag, int32_t* __restrict__ cells) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nb * BLK) return;
+  const int b = (int)(t / BLK), k = (int)(t % BLK);
+  int p[3];
+  xyz_of(list[b], nx, ny, p);
+  const int X = p[0] + k % 3 - 1, Y = p[1] + k / 3 % 3 - 1, Z = p[2] + k / 9 - 1;
+  int32_t v = -1;
+  if (X >= 0 && X < nx && Y >= 0 && Y < ny && Z >= 0 && Z < nz) {
+    const int64_t q = X + (int64_t)nx * (Y + (int64_t)ny * Z);
+    if (flag[q]) v = (int32_t)q;
+  }
+  cells[t] = v;
+}
+
+static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const int32_t* weak_d, const int32_t* nweak_d,
+                                cudaStream_t s) {
   if (!in.irr_cell || in.n_irr == 0) return cudaSuccess;
   const int nx = in.n[0], ny = in.n[1], nz = in.n[2];
-  const int64_t N = (int64_t)nx * ny * nz;
-  std::vector<uint8_t> weak(N), flag(N);
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(weak.data(), weak_d, N, cudaMemcpyDeviceToHost, s))) return e;
-  if ((e = cudaMemcpyAsync(flag.data(), in.flag, N, cudaMemcpyDeviceToHost, s))) return e;
+  int32_t nw = 0;
+  if ((e = cudaMemcpyAsync(&nw, nweak_d, 4, cudaMemcpyDeviceToHost, s))) return e;
   if ((e = cudaStreamSynchronize(s))) return e;
-  std::vector<int32_t> cells;
-  int nb = 0;
-  for (int64_t c = 0; c < N && nb < MAX_BLOCKS; ++c) {
-    if (!weak[c]) continue;
-    const int x = (int)(c % nx), y = (int)(c / nx % ny), z = (int)(c / ((int64_t)nx * ny));
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int X = x + dx, Y = y + dy, Z = z + dz;
-          int32_t v = -1;
-          if (X >= 0 && X < nx && Y >= 0 && Y < ny && Z >= 0 && Z < nz) {
-            const int64_t q = X + (int64_t)nx * (Y + (int64_t)ny * Z);
-            if (flag[q]) v = (int32_t)q;
-          }
-          cells.push_back(v);
-        }
-    ++nb;
+  const int nb = nw < MAX_BLOCKS ? nw : MAX_BLOCKS;
+  std::vector<int32_t> list(nb > 0 ? nb : 1);
+  if (nb > 0) {
+    if ((e = cudaMemcpyAsync(list.data(), weak_d, (size_t)nb * 4, cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    std::sort(list.begin(), list.begin() + nb);  // appended in any order: make the blocks deterministic
   }
   // row lookup data
   mg->irr_cell = in.irr_cell;
@@ -552,12 +559,16 @@ static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const uint
         if (in_footprint(x, y, z, in.R, in.box)) lut[(x + L) + S * ((y + L) + S * (z + L))] = (int16_t)nf++;
   if (nf != in.nfoot) return cudaErrorInvalidValue;
   if ((e = cudaMalloc(&mg->foot_lut, lut.size() * 2))) return e;
-  if ((e = cudaMalloc(&mg->blk_cells, cells.size() * 4))) return e;
+  if ((e = cudaMalloc(&mg->blk_cells, (size_t)nb * BLK * 4))) return e;
   if ((e = cudaMalloc(&mg->blk_inv64, (size_t)nb * BLK * BLK * 8))) return e;
   if ((e = cudaMalloc(&mg->blk_inv32, (size_t)nb * BLK * BLK * 4))) return e;
   if ((e = cudaMalloc(&mg->blk_res, (size_t)nb * BLK * 8))) return e;
   if ((e = cudaMemcpyAsync(mg->foot_lut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, s))) return e;
-  if ((e = cudaMemcpyAsync(mg->blk_cells, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice, s))) return e;
+  int32_t* dl;
+  if ((e = cudaMalloc(&dl, (size_t)nb * 4))) return e;
+  if ((e = cudaMemcpyAsync(dl, list.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, s))) { cudaFree(dl); return e; }
+  k_blk_cells<<<nb256((int64_t)nb * BLK), 256, 0, s>>>(dl, nb, nx, ny, nz, in.flag, mg->blk_cells);
+  eb::count_launch();
   mg->nblk = nb;
   RowSrc a = row_src(*mg);
   const int64_t nm = (int64_t)nb * BLK * BLK;
@@ -571,6 +582,7 @@ static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const uint
   cudaMemcpyAsync(&hf, fail, 4, cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   cudaFree(fail);
+  cudaFree(dl);
   if (e) return e;
   if (hf) mg->nblk = 0;  // a singular block: no local solves
   return cudaGetLastError();
@@ -579,7 +591,7 @@ static cudaError_t blocks_setup(const MgFineInput& in, Multigrid* mg, const uint
 cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
   mg->dim = in.dim;
   mg->nlev = 0;
-  uint8_t* weak = nullptr;  // fine-level cut cells with a weak high-order diagonal
+  int32_t* weak = nullptr;  // fine-level cut cells with a weak high-order diagonal (list, count after it)
   int n[3] = {in.n[0], in.n[1], in.n[2]};
   cudaError_t e;
   for (int l = 0; l < MG_MAXLEV; ++l) {
@@ -598,10 +610,12 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
       if ((e = cudaMalloc(&L.v64[k], nc * 8))) return e;
     mg->nlev = l + 1;
     if (l == 0) {
-      if ((e = cudaMalloc(&weak, nc))) return e;
+      if ((e = cudaMalloc(&weak, (MAX_BLOCKS + 1) * 4))) return e;
+      if ((e = cudaMemsetAsync(weak + MAX_BLOCKS, 0, 4, s))) return e;
       k_mg_fine<<<nb256(nc), 256, 0, s>>>(in.dim, n[0], n[1], n[2], in.h, in.flag, in.ff[0], in.ff[1], in.ff[2],
                                           in.cf[0], in.cf[1], in.cf[2], in.fm[0], in.fm[1], in.fm[2], in.KFS,
-                                          in.dinv_high, L.cp[0], L.cp[1], L.cp[2], L.dg, weak);
+                                          in.dinv_high, L.cp[0], L.cp[1], L.cp[2], L.dg, weak, weak + MAX_BLOCKS,
+                                          MAX_BLOCKS);
       eb::count_launch();
     } else {
       MgLevel& F = mg->lev[l - 1];
@@ -616,7 +630,7 @@ cudaError_t mg_setup(const MgFineInput& in, Multigrid* mg, cudaStream_t s) {
     for (int d = 0; d < in.dim; ++d) n[d] = (n[d] + 1) / 2;
   }
   if (weak) {
-    e = blocks_setup(in, mg, weak, s);
+    e = blocks_setup(in, mg, weak, weak + MAX_BLOCKS, s);
     cudaFree(weak);
     if (e) return e;
   }

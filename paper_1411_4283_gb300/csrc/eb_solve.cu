@@ -430,6 +430,26 @@ cudaError_t fill32(int64_t n, float* x, float v, cudaStream_t s) {
   k_fill<float><<<grid_for(n), VB, 0, s>>>(n, x, v); eb::count_launch();
   return cudaGetLastError();
 }
+// *nz = 1 when some a[i] != 0 (exact test, no reduction arithmetic)
+__global__ void k_any_nonzero(int64_t n, const double* __restrict__ a, int32_t* nz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != 0.0) {
+      *nz = 1;
+      return;
+    }
+}
+
+cudaError_t any_nonzero64(int64_t n, const double* a, int32_t* dflag, bool* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(dflag, 0, 4, s);
+  if (e) return e;
+  k_any_nonzero<<<grid_for(n), VB, 0, s>>>(n, a, dflag); eb::count_launch();
+  int32_t h = 0;
+  if ((e = cudaMemcpyAsync(&h, dflag, 4, cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  *out = h != 0;
+  return cudaGetLastError();
+}
+
 cudaError_t norm2_64(int64_t n, const double* a, double* dscr, double* out, cudaStream_t s) {
   double h[3];
   cudaError_t e = dots<double>(n, a, a, nullptr, nullptr, nullptr, nullptr, dscr, h, 1, s);

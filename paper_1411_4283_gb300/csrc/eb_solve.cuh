@@ -23,6 +23,7 @@ cudaError_t to32(int64_t n, const double* a, double scale, float* o, cudaStream_
 cudaError_t add32(int64_t n, double* x, double scale, const float* d, cudaStream_t s);
 cudaError_t fill32(int64_t n, float* x, float v, cudaStream_t s);
 cudaError_t norm2_64(int64_t n, const double* a, double* dscr, double* out, cudaStream_t s);
+cudaError_t any_nonzero64(int64_t n, const double* a, int32_t* dflag, bool* out, cudaStream_t s);
 void set_apply_timer(void* t);
 void* new_apply_timer();
 void free_apply_timer(void* p, double* ms, long long* n);
