@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 GPU solve timed once")
     p.add_argument("--out", default=None)
-    p.add_argument("--mode", default="step", choices=["step", "build", "apply"],
+    p.add_argument("--batch", type=int, default=256, help="geometries of --mode batch")
+    p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch"],
                    help="build: one stencil build and exit; apply: build plus 3 FP32 applies (profiling cases)")
     return p.parse_args()
 
@@ -210,6 +211,9 @@ def main():
     import paper_1411_4283_gb300 as P
     ws, rank, local = dist_setup(args)
     hbm_peak, peak_kind, sm_max = peaks()
+    if args.mode == "batch":
+        run_batch(args, P, torch)
+        return
     g, man, rho_h, Phi_h, geb_h, gw_h, t_geom = make_problem(args.n)
     dev = torch.device("cuda")
     dg = P.DeviceGeometry.from_geometry(g)
@@ -359,6 +363,58 @@ def main():
         print(json.dumps(line))
         if args.out:
             json.dump(line, open(args.out, "w"), indent=1)
+
+
+def run_batch(args, P, torch):
+    """Many-instance batch: --batch seeded 2-D geometries (the unit square minus a circle, centre
+    0.5 + U[-0.1, 0.1)^2, radius U[0.2, 0.3), grid sizes 2^k with k ~ U{5..9}, i.e. 32^2..512^2, all from
+    SplitMix64(11)), built with one least-squares launch against one build per geometry.  Reports LS
+    systems per second for both (each system a face's weighted LS solve)."""
+    import eb_inputs as E
+    from eb_inputs.rng import SplitMix64
+    rng = SplitMix64(11)
+    gs = []
+    for i in range(args.batch):
+        k = 5 + int(rng.next_u64() % 5)
+        cx, cy = 0.4 + 0.2 * rng.next_double(), 0.4 + 0.2 * rng.next_double()
+        r = 0.2 + 0.1 * rng.next_double()
+        gs.append(E.circle_config(2 ** k, center=(cx, cy), r=r))
+    dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+    torch.cuda.synchronize()
+
+    def sequential():
+        out = [P.eb_build_stencils(dg, order=args.order) for dg in dgs]
+        torch.cuda.synchronize()
+        return out
+
+    def batched():
+        out = P.eb_build_stencils_batch(dgs, order=args.order)
+        torch.cuda.synchronize()
+        return out
+
+    for _ in range(max(1, args.warmup)):
+        del_ = sequential()
+        del del_
+        del_ = batched()
+        del del_
+    ts, tb = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = sequential()
+        ts.append(time.perf_counter() - t0)
+        systems = sum(st.info["n_unique_faces"] + st.info["n_classes"] for st in out)
+        del out
+        t0 = time.perf_counter()
+        out = batched()
+        tb.append(time.perf_counter() - t0)
+        del out
+    ms, mb = float(np.median(ts)), float(np.median(tb))
+    sizes = [g.N for g in gs]
+    print(json.dumps({"mode": "batch", "metric": "LS systems/s (many-instance batch, 2-D)", "unit": "systems/s",
+                      "geometries": len(gs), "grid_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
+                      "systems_per_pass": systems, "batch_value": systems / mb, "batch_seconds": mb,
+                      "sequential_value": systems / ms, "sequential_seconds": ms, "speedup": ms / mb,
+                      "steps": args.steps, "order": args.order, "data": "synthetic"}))
 
 
 def template_faces(g, order):

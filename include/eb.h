@@ -116,6 +116,19 @@ typedef struct eb_build_info {
 eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_stencils** out, eb_build_info* info,
                             eb_stream_t stream);
 
+/* Build the stencils of n_geom geometries (Sec. 2.2-2.4 for each) with one
+ * least-squares launch: the LS systems of all geometries share one work
+ * queue, each system carrying its geometry.  geoms: host array of n_geom
+ * descriptors (device arrays as for eb_build_stencils), all of the same
+ * dimension; params apply to all.  out: host array of n_geom handles, each
+ * destroyed with eb_stencils_destroy; infos: optional host array of n_geom
+ * (ms_lsq is the shared launch's time in every entry).  The results equal
+ * those of n calls of eb_build_stencils.  On any failure every handle is
+ * NULL, nothing is left allocated, and the status is the first failure's
+ * (EB_ERR_INVALID also for n_geom < 1 or mixed dimensions). */
+eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb_params* params, eb_stencils** out,
+                                  eb_build_info* infos, eb_stream_t stream);
+
 /* y = L phi (kappa_weighted = 0) or kappa .* (L phi) (kappa_weighted = 1):
  * the homogeneous part of the discrete Laplacian (boundary values zero;
  * Sec. 2.3).  phi, y: [ncell] of dtype EB_F32 or EB_F64; covered cells of y

@@ -95,6 +95,7 @@ def load():
     P = ctypes.POINTER
     sig = {
         "eb_build_stencils": (i32, [P(EbGeom), P(EbParams), P(_vp), P(EbBuildInfo), _vp]),
+        "eb_build_stencils_batch": (i32, [P(EbGeom), i32, P(EbParams), P(_vp), P(EbBuildInfo), _vp]),
         "eb_apply": (i32, [_vp, _vp, _vp, i32, i32, _vp]),
         "eb_bc_rhs": (i32, [_vp, _vp, _vp, _vp, i32, _vp]),
         "eb_solve": (i32, [_vp, _vp, _vp, _vp, dbl, P(EbSolveOpts), _vp, P(EbSolveInfo), _vp]),
@@ -216,6 +217,19 @@ def eb_build_stencils(geom: DeviceGeometry, order=4, path_radius=0, nbr_metric=E
     _check(lib.eb_build_stencils(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h), ctypes.byref(info),
                                  _stream(stream)))
     return Stencils(h, info, geom)
+
+
+def eb_build_stencils_batch(geoms, order=4, path_radius=0, nbr_metric=EB_NBR_BOX, weighted=True,
+                            w_threshold=0.5, w_power=5.0, stream=None) -> list:
+    """Stencils of several geometries (same dimension) with one least-squares launch."""
+    lib = load()
+    n = len(geoms)
+    gs = (EbGeom * n)(*[geom.struct() for geom in geoms])
+    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power)
+    hs = (ctypes.c_void_p * n)()
+    infos = (EbBuildInfo * n)()
+    _check(lib.eb_build_stencils_batch(gs, n, ctypes.byref(p), hs, infos, _stream(stream)))
+    return [Stencils(ctypes.c_void_p(hs[i]), infos[i], geoms[i]) for i in range(n)]
 
 
 def eb_apply(st: Stencils, phi, y, kappa_weighted=True, stream=None):

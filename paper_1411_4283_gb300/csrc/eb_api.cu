@@ -397,8 +397,35 @@ eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n) {
   return EB_OK;
 }
 
-static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils* st, eb_build_info* info,
-                            cudaStream_t s);
+// State of one build between its phases: before the least-squares launch (classification, gather,
+// LS inputs), the launch itself (one geometry, or several sharing one launch), and after it
+// (status check, operator rows, boundary matrix, apply plan, info).
+struct BuildCtx {
+  const eb_geom* g = nullptr;
+  const eb_params* prm = nullptr;
+  eb_stencils* st = nullptr;
+  eb_build_info* info = nullptr;
+  cudaStream_t s = nullptr;
+  eb_params P;
+  int R = 0, D = 0, nsm = 0;
+  int64_t N = 0, n_slots = 0, n_unique = 0;
+  Tables T;
+  Tables* dT = nullptr;
+  Tmp tmp;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n_ev = 0;
+  int32_t tmpl_slot_h[3] = {-1, -1, -1};
+  double* invk = nullptr;
+  LsArgs la;            // least-squares inputs (scratch, work counter and error word set per launch)
+  int32_t* status = nullptr;
+  ~BuildCtx() {
+    for (int i = 0; i < n_ev; ++i) cudaEventDestroy(ev[i]);
+  }
+};
+
+static eb_status build_pre(BuildCtx& c);
+static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s);
+static eb_status build_post(BuildCtx& c);
 
 eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_stencils** out, eb_build_info* info,
                             eb_stream_t stream) {
@@ -408,7 +435,19 @@ eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_ste
   eb_stencils* st = new eb_stencils();
   eb_build_info local;
   memset(&local, 0, sizeof(local));
-  eb_status r = build_impl(geom, params, st, info ? info : &local, (cudaStream_t)stream);
+  eb_status r;
+  {
+    BuildCtx c;
+    c.g = geom;
+    c.prm = params;
+    c.st = st;
+    c.info = info ? info : &local;
+    c.s = (cudaStream_t)stream;
+    BuildCtx* cp = &c;
+    r = build_pre(c);
+    if (r == EB_OK) r = build_ls(&cp, 1, c.s);
+    if (r == EB_OK) r = build_post(c);
+  }
   if (r != EB_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     eb_stencils_destroy(st);
@@ -416,6 +455,37 @@ eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_ste
   }
   *out = st;
   return EB_OK;
+}
+
+eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb_params* params, eb_stencils** out,
+                                  eb_build_info* infos, eb_stream_t stream) {
+  if (!out || !geoms || n_geom < 1) { set_error("bad batch arguments"); return EB_ERR_INVALID; }
+  for (int32_t i = 0; i < n_geom; ++i) out[i] = nullptr;
+  g_bad_faces.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<BuildCtx*> cs(n_geom, nullptr);
+  std::vector<eb_build_info> local(n_geom);
+  eb_status r = EB_OK;
+  for (int32_t i = 0; i < n_geom; ++i) {
+    cs[i] = new BuildCtx();
+    BuildCtx& c = *cs[i];
+    c.g = &geoms[i];
+    c.prm = params;
+    c.st = new eb_stencils();
+    memset(&local[i], 0, sizeof(eb_build_info));
+    c.info = infos ? &infos[i] : &local[i];
+    c.s = s;
+  }
+  for (int32_t i = 0; i < n_geom && r == EB_OK; ++i) r = build_pre(*cs[i]);
+  if (r == EB_OK) r = build_ls(cs.data(), n_geom, s);
+  for (int32_t i = 0; i < n_geom && r == EB_OK; ++i) r = build_post(*cs[i]);
+  if (r != EB_OK) cudaStreamSynchronize(s);
+  for (int32_t i = 0; i < n_geom; ++i) {
+    if (r == EB_OK) out[i] = cs[i]->st;
+    else eb_stencils_destroy(cs[i]->st);
+    delete cs[i];
+  }
+  return r;
 }
 
 // apply order of the footprint for the quad layout (eb_apply_quad.cuh): groups of four wide segments,
@@ -489,8 +559,11 @@ static eb_status build_quad_plan(eb_stencils* st, ApplyPlan* pl, int R, cudaStre
   return EB_OK;
 }
 
-static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils* st, eb_build_info* info,
-                            cudaStream_t s) {
+static eb_status build_pre(BuildCtx& c) {
+  const eb_geom* g = c.g;
+  const eb_params* prm = c.prm;
+  eb_stencils* st = c.st;
+  cudaStream_t s = c.s;
   if (!g) { set_error("geometry descriptor is NULL"); return EB_ERR_INVALID; }
   eb_params P = {4, 0, EB_NBR_BOX, 1, 0.5, 5.0};
   if (prm) P = *prm;
@@ -529,26 +602,23 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
     set_error("missing geometry arrays");
     return EB_ERR_INVALID;
   }
-  Tables T;
+  Tables& T = c.T;
   if (!make_tables(g->dim, P.order, g->moment_degree, &T)) { set_error("table construction failed"); return EB_ERR_INVALID; }
   dm.K = T.K;
   dm.KS = T.KS;
   dm.KFS = T.KFS;
   const int D = g->dim;
   const int64_t N = dm.ncell;
-  Tmp tmp;
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) EB_CUDA(cudaEventCreate(&ev[i]));
-  struct EvGuard {
-    cudaEvent_t* e;
-    ~EvGuard() {
-      for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
-    }
-  } evg{ev};
+  Tmp& tmp = c.tmp;
+  cudaEvent_t* ev = c.ev;
+  for (int i = 0; i < 5; ++i) {
+    EB_CUDA(cudaEventCreate(&ev[i]));
+    c.n_ev = i + 1;
+  }
   EB_CUDA(cudaEventRecord(ev[0], s));
 
   // ---- library-owned copies of the geometry
-  Tables* dT;
+  Tables*& dT = c.dT;
   EB_TRY(dalloc(st, &dT, 1));
   EB_CUDA(cudaMemcpyAsync(dT, &T, sizeof(T), cudaMemcpyHostToDevice, s));
   EB_TRY(dalloc(st, &st->flag, N));
@@ -585,7 +655,7 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
     }
   }
   EB_TRY(dalloc(st, &st->kappa, N));
-  double* invk;
+  double*& invk = c.invk;
   EB_TRY(dalloc(st, &invk, N));
   k_kappa<<<nblk(N, 256), 256, 0, s>>>(N, st->flag, st->cut_of_cell, st->vol_mom, T.KS, st->kappa, invk); eb::count_launch();
   EB_CUDA(cudaGetLastError());
@@ -627,7 +697,7 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   int64_t n_unique = n_unique_grid + nc;
   std::vector<int32_t> h_class_slot(nkeys, -1);
   std::vector<int64_t> class_faces;
-  int32_t tmpl_slot_h[3] = {-1, -1, -1};
+  int32_t* tmpl_slot_h = c.tmpl_slot_h;
   for (int64_t k = 0; k < nkeys; ++k) {
     if (h_rep[k] == -1) continue;
     h_class_slot[k] = (int32_t)(n_unique + class_faces.size());
@@ -715,26 +785,17 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   ga.row_desc = st->row_desc;
   k_gather<<<nblk(n_slots, 128), 128, 0, s>>>(ga, n_slots, st->cut_cell); eb::count_launch();
   EB_CUDA(cudaGetLastError());
-  // ---- 4. weighted least squares (FP64): scratch first, so that the timed phase is the kernel
+  // ---- 4. weighted least squares (FP64): inputs here, the launch in build_ls
   int dev = 0, nsm = 0;
   EB_CUDA(cudaGetDevice(&dev));
   EB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  size_t ls_smem = (size_t)LS_SYS * LS_SMEM_PER_SYS;
-  EB_CUDA(cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
-  int64_t nblocks = std::min<int64_t>(nsm, (n_slots + LS_SYS - 1) / LS_SYS);
-  if (nblocks < 1) nblocks = 1;
-  double* scratch;
-  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_SYS * MAXROWS * (MAXK + 2)));
   double *ftab, *wtab;
   EB_TRY(tmp.get(&ftab, (size_t)TAB_N * MAXK));
   EB_TRY(tmp.get(&wtab, TAB_N));
   k_full_rows<<<nblk(TAB_N, 128), 128, 0, s>>>(dm, dT, ftab, wtab); eb::count_launch();
-  int32_t *next, *status;
-  EB_TRY(tmp.get(&next, 1));
-  EB_TRY(tmp.get(&status, n_slots));
-  EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
-
-  LsArgs la;
+  int32_t* status;
+  EB_TRY(tmp.get(&status, std::max<int64_t>(n_slots, 1)));
+  LsArgs& la = c.la;
   memset(&la, 0, sizeof(la));
   la.dm = dm;
   la.T = dT;
@@ -754,25 +815,87 @@ static eb_status build_impl(const eb_geom* g, const eb_params* prm, eb_stencils*
   la.row_desc = st->row_desc;
   la.row_val = st->row_val;
   la.n_slots = n_slots;
-  la.next = next;
   la.status = status;
-  la.scratch = scratch;
   la.ftab = ftab;
   la.wtab = wtab;
-  int32_t* lerr;
-  EB_TRY(tmp.get(&lerr, 1));
-  EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
-  la.err = lerr;
-  EB_CUDA(cudaEventRecord(ev[2], s));
-  if (n_slots > 0) k_lsq<<<(unsigned)nblocks, LS_WARPS * 32, ls_smem, s>>>(la, T); eb::count_launch();
-  EB_CUDA(cudaGetLastError());
-  EB_CUDA(cudaEventRecord(ev[3], s));
-  {
-    int32_t h = 0;
-    EB_CUDA(cudaMemcpyAsync(&h, lerr, 4, cudaMemcpyDeviceToHost, s));
-    EB_CUDA(cudaStreamSynchronize(s));
-    if (h) { set_error("a bounded device wait gave up in the least-squares kernel"); return EB_ERR_TIMEOUT; }
+  c.P = P;
+  c.R = R;
+  c.D = D;
+  c.N = N;
+  c.nsm = nsm;
+  c.n_slots = n_slots;
+  c.n_unique = n_unique;
+  c.status = status;
+  return EB_OK;
+}
+
+// The least-squares launch for n builds (one launch; n > 1: the systems of all geometries share one
+// work counter, each system finding its geometry from the prefix sums of the systems per build).
+static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
+  BuildCtx& c0 = *cs[0];
+  int64_t total = 0;
+  std::vector<int64_t> base(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    if (cs[i]->T.K != c0.T.K || cs[i]->D != c0.D) { set_error("a batch mixes dimensions or orders"); return EB_ERR_INVALID; }
+    base[i] = total;
+    total += cs[i]->n_slots;
   }
+  base[n] = total;
+  Tmp tmp;
+  size_t ls_smem = (size_t)LS_SYS * LS_SMEM_PER_SYS;
+  EB_CUDA(lsq_prepare(ls_smem));
+  int64_t nblocks = std::min<int64_t>(c0.nsm, (total + LS_SYS - 1) / LS_SYS);
+  if (nblocks < 1) nblocks = 1;
+  double* scratch;
+  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_SYS * MAXROWS * (MAXK + 2)));
+  int32_t *next, *lerr;
+  EB_TRY(tmp.get(&next, 1));
+  EB_TRY(tmp.get(&lerr, 1));
+  EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
+  EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
+  LsArgs a0 = c0.la;
+  a0.n_slots = total;
+  a0.next = next;
+  a0.err = lerr;
+  a0.scratch = scratch;
+  LsArgs* dbatch = nullptr;
+  int64_t* dbase = nullptr;
+  if (n > 1) {
+    std::vector<LsArgs> hb(n);
+    for (int i = 0; i < n; ++i) hb[i] = cs[i]->la;
+    EB_TRY(tmp.get(&dbatch, n));
+    EB_TRY(tmp.get(&dbase, n + 1));
+    EB_CUDA(cudaMemcpyAsync(dbatch, hb.data(), n * sizeof(LsArgs), cudaMemcpyHostToDevice, s));
+    EB_CUDA(cudaMemcpyAsync(dbase, base.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s));
+  }
+  for (int i = 0; i < n; ++i) EB_CUDA(cudaEventRecord(cs[i]->ev[2], s));
+  if (total > 0) {
+    EB_CUDA(lsq_launch((unsigned)nblocks, ls_smem, s, a0, c0.T, n > 1 ? dbatch : nullptr, dbase, n));
+    eb::count_launch();
+  }
+  for (int i = 0; i < n; ++i) EB_CUDA(cudaEventRecord(cs[i]->ev[3], s));
+  int32_t h = 0;
+  EB_CUDA(cudaMemcpyAsync(&h, lerr, 4, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  if (h) { set_error("a bounded device wait gave up in the least-squares kernel"); return EB_ERR_TIMEOUT; }
+  return EB_OK;
+}
+
+static eb_status build_post(BuildCtx& c) {
+  const eb_geom* g = c.g;
+  eb_stencils* st = c.st;
+  eb_build_info* info = c.info;
+  cudaStream_t s = c.s;
+  Tmp& tmp = c.tmp;
+  cudaEvent_t* ev = c.ev;
+  Tables& T = c.T;
+  Dims& dm = st->dm;
+  const int R = c.R, D = c.D, nsm = c.nsm;
+  const int64_t N = c.N, n_slots = c.n_slots, n_unique = c.n_unique, nc = g->n_cut;
+  const int32_t* tmpl_slot_h = c.tmpl_slot_h;
+  int32_t* status = c.status;
+  double* invk = c.invk;
+  const int M = R + 3;
   {
     std::vector<int32_t> hs(n_slots);
     EB_CUDA(cudaMemcpyAsync(hs.data(), status, n_slots * 4, cudaMemcpyDeviceToHost, s));

@@ -597,7 +597,7 @@ __device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& pha
 
 #define PAIR_SYNC()                                    \
   do {                                                 \
-    if (!pair_sync(&S.bar, phase, a.err)) return;      \
+    if (!pair_sync(&S.bar, phase, a0.err)) return;     \
   } while (0)
 
 // One system (face) per group of LS_NW warps.  Every warp holds the chunk's rows (lane l: rows
@@ -605,17 +605,23 @@ __device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& pha
 // partial dots, column sums, taus, R entries and updates.  Per Householder step the exchanges are
 // column k+1 (the next vector, updated by its owner and read by the others after a group barrier)
 // and its scalars (posted by the owner with a sequence flag and read at the start of the next step).
-__global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid_constant__ Tables T) {
+//
+// BATCH: the systems of several geometries (same dimension and order) in one launch; the work counter,
+// the total system count, the scratch and the error word come from a0, each system's geometry data
+// from batch[g] with g found from the prefix sums of the systems per geometry (slot_base).
+template <bool BATCH>
+__global__ void __launch_bounds__(LS_WARPS * 32, 1)
+    k_lsq(const __grid_constant__ LsArgs a0, const __grid_constant__ Tables T, const LsArgs* __restrict__ batch,
+          const int64_t* __restrict__ slot_base, int n_geom) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sys = warp / LS_NW, h = warp % LS_NW;
   LsSysSmem& S = reinterpret_cast<LsSysSmem*>(smem_raw)[sys];
   const int K = T.K;
   const int gs = blockIdx.x * LS_SYS + sys;
-  double* scr = a.scratch + (int64_t)gs * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
+  double* scr = a0.scratch + (int64_t)gs * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
   double* scr_w = scr + (int64_t)MAXROWS * MAXK;
   double* scr_t = scr_w + MAXROWS;
-  const Dims& dm = a.dm;
   double* F = S.vec;
   double* y = S.vec + MAXK;
   double* z = S.vec + 2 * MAXK;
@@ -632,10 +638,23 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
   uint32_t phase = 0;
   int32_t stepno = 0;  // Householder steps taken by this pair (same count in both warps)
   while (true) {
-    if (h == 0 && lane == 0) S.slot = atomicAdd(a.next, 1);
+    if (h == 0 && lane == 0) S.slot = atomicAdd(a0.next, 1);
     PAIR_SYNC();
-    const int s = S.slot;
-    if (s >= a.n_slots) break;
+    int s = S.slot;
+    if (s >= a0.n_slots) break;
+    int g = 0;
+    if constexpr (BATCH) {  // the geometry of system s: last g with slot_base[g] <= s
+      int lo = 0, hi = n_geom - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (slot_base[mid] <= s) lo = mid;
+        else hi = mid - 1;
+      }
+      g = lo;
+      s -= (int)slot_base[g];
+    }
+    const LsArgs& a = BATCH ? batch[g] : a0;
+    const Dims& dm = a.dm;
     const int64_t p0 = a.row_ptr[s];
     const int n = (int)(a.row_ptr[s + 1] - p0);
     const int64_t gf = a.slot_face[s];
@@ -750,7 +769,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1) k_lsq(LsArgs a, const __grid
           while (*seq != stepno && ++it < PAIR_WAIT_LIMIT) {
           }
           if (it >= PAIR_WAIT_LIMIT) {
-            atomicExch(a.err, 1);
+            atomicExch(a0.err, 1);
             return;
           }
           __threadfence_block();
@@ -1079,6 +1098,23 @@ __global__ void k_assemble_b(AsmArgs a, const int32_t* __restrict__ cells, int64
     }
   }
   if (!bptr) cnt[t] = n;
+}
+
+}  // namespace eb
+
+namespace eb {
+
+cudaError_t lsq_prepare(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_lsq<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_lsq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t lsq_launch(unsigned blocks, size_t smem, cudaStream_t s, const LsArgs& a0, const Tables& T,
+                       const LsArgs* batch, const int64_t* slot_base, int n_geom) {
+  if (batch) k_lsq<true><<<blocks, LS_WARPS * 32, smem, s>>>(a0, T, batch, slot_base, n_geom);
+  else k_lsq<false><<<blocks, LS_WARPS * 32, smem, s>>>(a0, T, nullptr, nullptr, 1);
+  return cudaGetLastError();
 }
 
 }  // namespace eb

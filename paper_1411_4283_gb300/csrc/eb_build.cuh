@@ -105,7 +105,11 @@ __global__ void k_face_slots(Dims dm, int d, const int32_t* state, const int64_t
 __global__ void k_reach(Dims dm, const int32_t* cells, int64_t ncells, const uint8_t* flag, const uint8_t* ff0,
                         const uint8_t* ff1, const uint8_t* ff2, Mask* out);
 __global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* cut_cell);
-__global__ void k_lsq(LsArgs a, const __grid_constant__ Tables T);
+// k_lsq launchers (eb_build.cu): shared-memory attribute, then one launch over the systems of one
+// geometry (batch == null) or of several (batch[g] per geometry, slot_base prefix sums of their systems)
+cudaError_t lsq_prepare(size_t smem);
+cudaError_t lsq_launch(unsigned blocks, size_t smem, cudaStream_t s, const LsArgs& a0, const Tables& T,
+                       const LsArgs* batch, const int64_t* slot_base, int n_geom);
 __global__ void k_full_rows(Dims dm, const Tables* T, double* ftab, double* wtab);
 __global__ void k_assemble_rows(AsmArgs a, const int32_t* rep_cell, int64_t nrep, int64_t row0, int32_t* err);
 __global__ void k_assemble_b(AsmArgs a, const int32_t* cells, int64_t ncells, int64_t* cnt, const int64_t* bptr,

@@ -59,6 +59,9 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     P.load()
     h = ctypes.c_void_p()
     assert P._LIB.eb_build_stencils(None, None, ctypes.byref(h), None, None) == 1
+    hs = (ctypes.c_void_p * 2)()
+    assert P._LIB.eb_build_stencils_batch(None, 2, None, hs, None, None) == 1
+    assert P._LIB.eb_build_stencils_batch(None, 0, None, hs, None, None) == 1
     assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 15, 300, None, None, None) == 8
     assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 40, 10, None, None, None) == 1
 

@@ -1,0 +1,68 @@
+"""Many-instance batch: the stencils of several geometries built with one least-squares launch equal
+those of separate builds (and, through them, the oracle's)."""
+import numpy as np
+import pytest
+
+import eb_inputs as E
+from gpu_helpers import compare_stencils, sample_faces, to_dev
+from oracle.eb_oracle import Oracle, Params
+
+pytestmark = pytest.mark.gpu
+
+
+def _same_stencils(sa, sb, faces):
+    import paper_1411_4283_gb300 as P
+    for f in faces:
+        ca, va = P.eb_stencil_query(sa, int(f))
+        cb, vb = P.eb_stencil_query(sb, int(f))
+        assert np.array_equal(ca, cb), f
+        assert np.abs(va - vb).max() <= 1e-14 * max(np.abs(vb).max(), 1e-300), f
+
+
+def _geoms_2d():
+    return [E.circle_config(24), E.multi_circle_config(32, seed=3),
+            E.circle_config(40, center=(0.45, 0.55), r=0.2),
+            E.Geometry(2, 16, np.zeros((0, 3)), np.zeros(0), False, 4, name="box"),
+            E.multi_circle_config(48, seed=5)]
+
+
+def test_batch_equals_single_2d():
+    import torch
+    import paper_1411_4283_gb300 as P
+    gs = _geoms_2d()
+    dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+    batch = P.eb_build_stencils_batch(dgs, order=4)
+    for g, dg, sb in zip(gs, dgs, batch):
+        ss = P.eb_build_stencils(dg, order=4)
+        assert sb.info["n_unique_faces"] == ss.info["n_unique_faces"]
+        o = Oracle(g, Params(order=4))
+        _same_stencils(sb, ss, o.flux_faces())
+        phi = to_dev(E.seeded_field(7, g.ncell) * (g.flag > 0))
+        ya = torch.empty_like(phi)
+        yb = torch.empty_like(phi)
+        P.eb_apply(sb, phi, ya)
+        P.eb_apply(ss, phi, yb)
+        assert torch.equal(ya, yb)
+    # the chain closes at the oracle for one geometry of the batch
+    o = Oracle(gs[1], Params(order=4))
+    compare_stencils(batch[1], o, o.flux_faces())
+
+
+def test_batch_equals_single_3d():
+    import paper_1411_4283_gb300 as P
+    gs = [E.sphere_box_config(16), E.sphere_box_config(20)]
+    dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+    batch = P.eb_build_stencils_batch(dgs, order=4)
+    for g, dg, sb in zip(gs, dgs, batch):
+        ss = P.eb_build_stencils(dg, order=4)
+        o = Oracle(g, Params(order=4))
+        _same_stencils(sb, ss, sample_faces(o, 60, seed=4))
+    o = Oracle(gs[0], Params(order=4))
+    compare_stencils(batch[0], o, sample_faces(o, 30, seed=6))
+
+
+def test_batch_rejects_mixed_dimensions():
+    import paper_1411_4283_gb300 as P
+    dgs = [P.DeviceGeometry.from_geometry(E.circle_config(16)), P.DeviceGeometry.from_geometry(E.sphere_box_config(12))]
+    with pytest.raises(P.EbError):
+        P.eb_build_stencils_batch(dgs, order=4)
