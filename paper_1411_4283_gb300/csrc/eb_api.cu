@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -117,28 +118,63 @@ bool make_tables(int dim, int order, int mdeg, Tables* t) {
 
 static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Device memory of builds and solves comes from a library-owned stream-ordered pool per device that
+// keeps freed memory cached (no release threshold), so that the dozens of allocations of a build and
+// the temporaries of every solve cost neither a driver allocation nor a device-wide synchronisation.
+static cudaMemPool_t eb_pool() {
+  static std::mutex m;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(m);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    (void)cudaGetLastError();
+    pools[dev] = nullptr;
+    return nullptr;
+  }
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  pools[dev] = pool;
+  return pool;
+}
+
+static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = eb_pool();
+  if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, s);
+  return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 static eb_status dalloc(eb_stencils* st, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  cudaError_t e = pool_alloc((void**)p, count * sizeof(T), st->build_stream);
+  if (e != cudaSuccess) return cuda_status(e, "device allocation");
   st->allocs.push_back((void*)*p);
   return EB_OK;
 }
 
-// temporary allocations freed at scope exit
+// temporary allocations, freed in stream order at scope exit
 struct Tmp {
+  cudaStream_t s = nullptr;
   std::vector<void*> ptrs;
   ~Tmp() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, s);
   }
   template <typename T>
   eb_status get(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+    cudaError_t e = pool_alloc((void**)p, count * sizeof(T), s);
+    if (e != cudaSuccess) return cuda_status(e, "device allocation");
     ptrs.push_back((void*)*p);
     return EB_OK;
   }
@@ -386,6 +422,8 @@ void eb_stencils_destroy(eb_stencils* st) {
     mg_free(st->mg);
     delete st->mg;
   }
+  // pooled memory is freed without an implicit synchronisation: wait for work still using it
+  cudaDeviceSynchronize();
   for (void* p : st->allocs) cudaFree(p);
   delete st;
 }
@@ -564,6 +602,8 @@ static eb_status build_pre(BuildCtx& c) {
   const eb_params* prm = c.prm;
   eb_stencils* st = c.st;
   cudaStream_t s = c.s;
+  c.tmp.s = s;
+  st->build_stream = s;
   if (!g) { set_error("geometry descriptor is NULL"); return EB_ERR_INVALID; }
   eb_params P = {4, 0, EB_NBR_BOX, 1, 0.5, 5.0};
   if (prm) P = *prm;
@@ -842,6 +882,7 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   }
   base[n] = total;
   Tmp tmp;
+  tmp.s = s;
   size_t ls_smem = (size_t)LS_SYS * LS_SMEM_PER_SYS;
   EB_CUDA(lsq_prepare(ls_smem));
   int64_t nblocks = std::min<int64_t>(c0.nsm, (total + LS_SYS - 1) / LS_SYS);
@@ -1346,6 +1387,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = st->dm.ncell;
   Tmp tmp;
+  tmp.s = s;
   double *bg, *rhs, *y64, *r64, *dscr;
   EB_TRY(tmp.get(&bg, n));
   EB_TRY(tmp.get(&rhs, n));

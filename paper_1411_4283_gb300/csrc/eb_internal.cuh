@@ -118,7 +118,8 @@ struct eb_stencils {
   // scratch for solves
   void* work = nullptr;
   size_t work_bytes = 0;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;       // device arrays owned by the stencils (stream-ordered pool)
+  cudaStream_t build_stream = nullptr;  // stream the arrays are allocated in
 };
 
 namespace eb {
