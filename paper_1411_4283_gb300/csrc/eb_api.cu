@@ -350,6 +350,50 @@ __global__ void k_pack_quads(const T* __restrict__ rows, int64_t n_rows, const i
   qU[(((u >> 5) * nq + (e >> 2)) * 32 + (u & 31)) * 4 + (e & 3)] = v;
 }
 
+// start of an aligned x-run of four class cells of one class: x a multiple of 4 (nx is), and the
+// loaded window x-4 .. x+7 inside the grid row
+__global__ void k_run_mark(int64_t nC, const int32_t* cellC, const int32_t* classC, int nx, int32_t* gs) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nC) return;
+  const int32_t c = cellC[t];
+  const int x = c % nx;
+  bool ok = (nx & 3) == 0 && (x & 3) == 0 && x >= 4 && x + 8 <= nx && t + 3 < nC && cellC[t + 3] == c + 3;
+  if (ok) ok = classC[t + 1] == classC[t] && classC[t + 2] == classC[t] && classC[t + 3] == classC[t];
+  gs[t] = ok;
+}
+
+__global__ void k_run_rest(int64_t nC, const int32_t* gs, int32_t* rest) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nC) return;
+  bool in = gs[t] || (t >= 1 && gs[t - 1]) || (t >= 2 && gs[t - 2]) || (t >= 3 && gs[t - 3]);
+  rest[t] = !in;
+}
+
+__global__ void k_run_split(int64_t nC, const int32_t* cellC, const int32_t* classC, const int32_t* gs,
+                            const int32_t* rest, const int64_t* gpos, const int64_t* lpos, int32_t* cellG,
+                            int32_t* classG, int32_t* cellL, int32_t* classL) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nC) return;
+  if (gs[t]) {
+    cellG[gpos[t]] = cellC[t];
+    classG[gpos[t]] = classC[t];
+  }
+  if (rest[t]) {
+    cellL[lpos[t]] = cellC[t];
+    classL[lpos[t]] = classC[t];
+  }
+}
+
+// class rows, class-major: out[k * nfoot + i] = rows[i][k]
+template <typename T>
+__global__ void k_class_major(const T* __restrict__ rows, int64_t n_rows, int64_t n_class, int nfoot,
+                              T* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_class * nfoot) return;
+  const int64_t k = t / nfoot, i = t % nfoot;
+  out[t] = rows[i * n_rows + k];
+}
+
 __global__ void k_diag_inv(int64_t ncell, const uint8_t* kind, const int32_t* irr_map_unused, const double* tmpl,
                            int center, double* dinv64, float* dinv32) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -591,8 +635,37 @@ static eb_status build_quad_plan(eb_stencils* st, ApplyPlan* pl, int R, cudaStre
     k_pack_quads<double><<<grid, 256, 0, s>>>(st->rows64, st->n_rows, dperm, nq, n_class, pl->qU64);
     eb::count_launch();
   }
+  if (nC > 0) {
+    // wall-layer class cells: aligned x-runs of four with one class, and the rest per cell
+    int32_t *gs, *rest;
+    int64_t *gpos, *lpos;
+    int64_t nG = 0, nL = 0;
+    EB_TRY(tmp.get(&gs, nC));
+    EB_TRY(tmp.get(&rest, nC));
+    EB_TRY(tmp.get(&gpos, nC));
+    EB_TRY(tmp.get(&lpos, nC));
+    k_run_mark<<<nblk(nC, 256), 256, 0, s>>>(nC, pl->cellC, pl->classC, pl->nx, gs); eb::count_launch();
+    k_run_rest<<<nblk(nC, 256), 256, 0, s>>>(nC, gs, rest); eb::count_launch();
+    EB_TRY(scan<int32_t>(gs, nC, gpos, &nG, s, tmp));
+    EB_TRY(scan<int32_t>(rest, nC, lpos, &nL, s, tmp));
+    if (4 * nG + nL != nC) { set_error("wall-layer runs do not partition the class cells"); return EB_ERR_INVALID; }
+    pl->nG = nG;
+    pl->nL = nL;
+    EB_TRY(dalloc(st, &pl->cellG, std::max<int64_t>(nG, 1)));
+    EB_TRY(dalloc(st, &pl->classG, std::max<int64_t>(nG, 1)));
+    EB_TRY(dalloc(st, &pl->cellL, std::max<int64_t>(nL, 1)));
+    EB_TRY(dalloc(st, &pl->classL, std::max<int64_t>(nL, 1)));
+    k_run_split<<<nblk(nC, 256), 256, 0, s>>>(nC, pl->cellC, pl->classC, gs, rest, gpos, lpos, pl->cellG, pl->classG,
+                                              pl->cellL, pl->classL); eb::count_launch();
+    const int64_t nk = n_class * (int64_t)st->nfoot;
+    EB_TRY(dalloc(st, &pl->rowsK32, nk));
+    EB_TRY(dalloc(st, &pl->rowsK64, nk));
+    k_class_major<float><<<nblk(nk, 256), 256, 0, s>>>(st->rows32, st->n_rows, n_class, st->nfoot, pl->rowsK32);
+    eb::count_launch();
+    k_class_major<double><<<nblk(nk, 256), 256, 0, s>>>(st->rows64, st->n_rows, n_class, st->nfoot, pl->rowsK64);
+    eb::count_launch();
+  }
   EB_CUDA(cudaGetLastError());
-  EB_CUDA(cudaStreamSynchronize(s));  // the plan outlives the temporaries
   pl->quad = 1;
   return EB_OK;
 }

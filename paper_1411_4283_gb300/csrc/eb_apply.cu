@@ -12,6 +12,7 @@
 #include "eb_internal.cuh"
 #include "eb_apply_tma.cuh"
 #include "eb_apply_quad.cuh"
+#include "eb_apply_wall.cuh"
 
 #include <cuda.h>
 
@@ -130,6 +131,37 @@ __global__ void __launch_bounds__(256) k_apply_irregular_seg(ApplyArgs<T> a, int
   a.y[c] = acc;
 }
 
+// wall-layer x-runs need 16-byte aligned phi for their vector loads
+template <typename T>
+static bool use_runs(const ApplyArgs<T>& a) {
+  const ApplyPlan* pl = a.plan;
+  return pl && pl->quad && pl->nG > 0 && ((uintptr_t)a.phi & 15u) == 0;
+}
+
+template <typename T>
+static cudaError_t launch_runs(const ApplyArgs<T>& a, cudaStream_t st) {
+  const ApplyPlan* pl = a.plan;
+  XqArgs<T> x;
+  x.nG = pl->nG;
+  x.cellG = pl->cellG;
+  x.classG = pl->classG;
+  if constexpr (sizeof(T) == 4) x.rowsK = pl->rowsK32;
+  else x.rowsK = pl->rowsK64;
+  x.nfoot = a.nfoot;
+  x.phi = a.phi;
+  x.y = a.y;
+  x.inv_kappa = a.inv_kappa;
+  x.kappa_weighted = a.kappa_weighted;
+  x.nx = pl->nx;
+  x.ny = pl->ny;
+  x.nz = pl->nz;
+  const unsigned nb = (unsigned)((pl->nG + 127) / 128);
+  if (pl->R == 3) k_class_xquad<T, 3><<<nb, 128, 0, st>>>(x);
+  else k_class_xquad<T, 2><<<nb, 128, 0, st>>>(x);
+  eb::count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
   const ApplyPlan* pl = a.plan;
@@ -144,12 +176,14 @@ static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
       else k_irr_quad<T, 2, ApplyEpi><<<(unsigned)bu, 128, 0, st>>>(a, q, ApplyEpi());
       eb::count_launch();
     }
-    if (pl->nC > 0) {
+    const bool runs = use_runs(a);  // the x-runs go on the template pass's stream
+    const int64_t nrest = runs ? pl->nL : pl->nC;
+    if (nrest > 0) {
       ApplyArgs<T> c = a;
-      c.n_irr = pl->nC;
-      c.irr_cell = pl->cellC;
-      c.irr_row = pl->classC;
-      const int64_t bc = (pl->nC + 255) / 256;
+      c.n_irr = nrest;
+      c.irr_cell = runs ? pl->cellL : pl->cellC;
+      c.irr_row = runs ? pl->classL : pl->classC;
+      const int64_t bc = (nrest + 255) / 256;
       if (pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
       else k_apply_irregular_seg<T, 2, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
       eb::count_launch();
@@ -276,6 +310,9 @@ cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
     if ((e = launch_irregular<T>(a, fork ? pl->side : s))) return e;
   }
   if ((e = launch_template_pass<T>(a, s))) return e;
+  if (a.n_irr > 0 && use_runs(a)) {
+    if ((e = launch_runs<T>(a, s))) return e;
+  }
   if (fork) {
     if ((e = cudaEventRecord(pl->join, pl->side))) return e;
     if ((e = cudaStreamWaitEvent(s, pl->join, 0))) return e;

@@ -41,6 +41,14 @@ struct ApplyPlan {
   int32_t* classC = nullptr;     // [nC] their class row
   float* qU32 = nullptr;         // unique rows in the quad layout
   double* qU64 = nullptr;
+  // class cells split into aligned x-runs of four with one class (eb_apply_wall.cuh) and the rest
+  int64_t nG = 0, nL = 0;
+  int32_t* cellG = nullptr;      // [nG] first cell of each run
+  int32_t* classG = nullptr;     // [nG] class row of the run
+  int32_t* cellL = nullptr;      // [nL] class cells outside the runs, ascending
+  int32_t* classL = nullptr;     // [nL] their class row
+  float* rowsK32 = nullptr;      // [n_class][nfoot] class rows, class-major
+  double* rowsK64 = nullptr;
   std::vector<float> cube32;     // dense (2R+3)^3 template coefficients
   std::vector<double> cube64;
   int zsym = 0;                  // template symmetric in z (to a few ulps): z-folded template pass

@@ -127,8 +127,9 @@ def test_sampled_stencils_3d():
 
 
 def _row_sample_cells(g, order, rng):
-    """Cut cells, full cells next to the EB, interior cells, cells in the wall layers and cells next to
-    the first and last grid rows (the clamped path of the irregular pass)."""
+    """Cut cells, full cells next to the EB, interior cells, cells in the wall layers (among them cells
+    of the aligned x-runs of the wall-layer pass) and cells next to the first and last grid rows (the
+    clamped path of the irregular pass)."""
     n = g.N
     R = 3 if order == 4 else 2
     L = R + 1
@@ -139,8 +140,10 @@ def _row_sample_cells(g, order, rng):
     interior = full[(np.minimum(np.minimum(x, y), z) > L + 1) & (np.maximum(np.maximum(x, y), z) < n - L - 2)]
     cut = set(int(c) for c in g.cut_cells)
     near = [int(c) for c in interior if any((int(c) + d) in cut for d in (1, -1, n, -n, n * n, -n * n))]
+    wx = wall % n
+    runs = wall[(wx >= 8) & (wx <= n - 9)]
     pick = []
-    for pool, k in ((g.cut_cells, 8), (near, 6), (interior, 4), (wall, 8), (edge, 4)):
+    for pool, k in ((g.cut_cells, 8), (near, 6), (interior, 4), (wall, 8), (edge, 4), (runs, 8)):
         pool = np.asarray(pool)
         if len(pool):
             pick += [int(c) for c in rng.choice(pool, min(k, len(pool)), replace=False)]
