@@ -538,23 +538,32 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Column sums of P[0..32)[c0 + STR*c] for c < mm (mm <= 32/G columns): G lanes per column each sum
 // 32/G partials with independent accumulators, then a shuffle tree.  Returns the sum in the first
-// lane of each group; *col is the column number c (or -1).
+// lane of each group; *col is the column number c (or -1).  The accumulators start from the first
+// partials (no additions of zero: the FP64 pipe is the kernel's bound, and an add costs it as much
+// as an FMA).
 template <int G, int STR>
 __device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int lane, int* col) {
   constexpr int L = 32 / G;
   const int cl = lane / G, part = lane % G;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double s = 0.0;
   if (cl < mm) {
     const double* p = P + (part * L) * KST + c0 + STR * cl;
+    if constexpr (L >= 4) {
+      double a0 = p[0], a1 = p[KST], a2 = p[2 * KST], a3 = p[3 * KST];
 #pragma unroll
-    for (int l = 0; l < L; l += 4) {
-      a0 += p[l * KST];
-      if (l + 1 < L) a1 += p[(l + 1) * KST];
-      if (l + 2 < L) a2 += p[(l + 2) * KST];
-      if (l + 3 < L) a3 += p[(l + 3) * KST];
+      for (int l = 4; l < L; l += 4) {
+        a0 += p[l * KST];
+        a1 += p[(l + 1) * KST];
+        a2 += p[(l + 2) * KST];
+        a3 += p[(l + 3) * KST];
+      }
+      s = (a0 + a1) + (a2 + a3);
+    } else if constexpr (L == 2) {
+      s = p[0] + p[KST];
+    } else {
+      s = p[0];
     }
   }
-  double s = (a0 + a1) + (a2 + a3);
 #pragma unroll
   for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   *col = (cl < mm && part == 0) ? cl : -1;
@@ -746,14 +755,16 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       }
       // Householder scalars of step k from its vector (chunk part c, R part alpha = R_kk)
       auto hscalars = [&](const double* c, int k, double* out) {
-        double ss = 0.0;
+        double ss = c[0] * c[0];
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) ss = fma(c[r], c[r], ss);
+        for (int r = 1; r < RPL; ++r) ss = fma(c[r], c[r], ss);
         ss = warp_sum(ss);
-        const bool refl = ss != 0.0;  // a zero chunk column needs no reflection
+        // sign and zero tests on the bit patterns (integer pipe; ss >= +0): a zero chunk column needs
+        // no reflection
+        const bool refl = __double_as_longlong(ss) != 0;
         const double alpha = S.R[k * K + k];
         const double sigma = refl ? sqrt(fma(alpha, alpha, ss)) : 0.0;
-        out[0] = alpha > 0.0 ? -sigma : sigma;        // beta
+        out[0] = __double_as_longlong(alpha) > 0 ? -sigma : sigma;  // beta
         out[1] = alpha - out[0];                       // v0
         out[2] = refl ? -1.0 / (out[0] * out[1]) : 0.0;  // gamma
         out[3] = refl ? 1.0 : 0.0;
@@ -780,7 +791,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
           for (int q = 0; q < 4; ++q) hk[q] = hnext[q];  // this warp computed them in step k-1
         }
         const double beta = hk[0], v0 = hk[1], gamma = hk[2];
-        const bool refl = hk[3] != 0.0;
+        const bool refl = __double_as_longlong(hk[3]) != 0;  // 1.0 or 0.0
         __syncwarp();  // P holds the partial dots of column k with the own later columns
         const int jf = k + 1 + (h + LS_NW - (k + 1) % LS_NW) % LS_NW;  // first own column after k
         const int mown = jf < K ? (K - 1 - jf) / LS_NW + 1 : 0;

@@ -442,24 +442,34 @@ __global__ void k_blk_invert(int nblk, double* __restrict__ M, float* __restrict
     }
 }
 
-// res_i = r_ci - (A z)_ci for the cells of every block
+// res_i = r_ci - (A z)_ci for the cells of every block; one warp per cell, the lanes splitting the
+// footprint (few cells, long rows: a thread per cell leaves the GPU idle behind 637 dependent loads)
 template <typename T>
 __global__ void k_blk_res(RowSrc a, int nblk, const int32_t* __restrict__ cells, const T* __restrict__ r,
                           const T* __restrict__ z, T* __restrict__ res) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
+  const int lane = threadIdx.x & 31;
   if (t >= (int64_t)nblk * BLK) return;
   const int32_t c = cells[t];
-  if (c < 0) { res[t] = (T)0; return; }
+  if (c < 0) {
+    if (lane == 0) res[t] = (T)0;
+    return;
+  }
   const int64_t row = row_of_cell(a, c);
-  if (row == -2) { res[t] = (T)0; return; }
+  if (row == -2) {
+    if (lane == 0) res[t] = (T)0;
+    return;
+  }
   T acc = (T)0;
   const int64_t hi = a.ncell - 1;
-  for (int f = 0; f < a.nfoot; ++f) {
+  for (int f = lane; f < a.nfoot; f += 32) {
     int64_t q = c + a.foot_off[f];
     q = q < 0 ? 0 : (q > hi ? hi : q);  // out-of-domain entries have zero coefficients
     acc = fma(coef_at<T>(a, row, f), z[q], acc);
   }
-  res[t] = r[c] - acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) res[t] = r[c] - acc;
 }
 
 // z_ci += sum_j inv(A_BB)_ij res_j (blocks may overlap: additive)
@@ -779,7 +789,7 @@ cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
     const T* inv;
     if constexpr (sizeof(T) == 4) inv = mg.blk_inv32;
     else inv = mg.blk_inv64;
-    k_blk_res<T><<<nb256(nt), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
+    k_blk_res<T><<<nb256(nt * 32), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
     k_blk_corr<T><<<nb256(nt), 256, 0, s>>>(mg.nblk, mg.blk_cells, inv, (const T*)mg.blk_res, z);
     eb::count_launches(2);
   }
