@@ -27,10 +27,17 @@ struct GatherArgs {
   int32_t* too_many;         // capacity flag
 };
 
-constexpr int LS_SYS = 4;              // systems in flight per CTA (shared memory bound)
+// LS kernel shape (compile-time; EB_LS_SYS / EB_LS_RPL override it for tuning builds)
+#ifndef EB_LS_SYS
+#define EB_LS_SYS 4
+#endif
+#ifndef EB_LS_RPL
+#define EB_LS_RPL 4
+#endif
+constexpr int LS_SYS = EB_LS_SYS;      // systems in flight per CTA (shared memory bound)
 constexpr int LS_NW = 2;               // warps per system (each owns the columns j with j % LS_NW == its rank)
 constexpr int LS_WARPS = LS_NW * LS_SYS;
-constexpr int RPL = 4;        // rows per lane per chunk
+constexpr int RPL = EB_LS_RPL;  // rows per lane per chunk
 constexpr int CH = 32 * RPL;  // rows per chunk
 constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
 
@@ -47,6 +54,7 @@ struct __align__(16) LsSysSmem {
   int32_t hs_seq[2];         // step number whose scalars hs[k % 2] holds (posted after the values)
 };
 static_assert(sizeof(LsSysSmem) % 16 == 0, "per-system blocks stay 16-byte aligned");
+static_assert(LS_SYS * sizeof(LsSysSmem) <= 232448, "the systems of a CTA fit in 227 KB of shared memory");
 
 // offsets in units of h/2 span [-11, 11] on each axis (volume, EB and wall rows)
 constexpr int TAB_S = 23;
