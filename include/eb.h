@@ -123,9 +123,13 @@ eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_ste
  * dimension; params apply to all.  out: host array of n_geom handles, each
  * destroyed with eb_stencils_destroy; infos: optional host array of n_geom
  * (ms_lsq is the shared launch's time in every entry).  The results equal
- * those of n calls of eb_build_stencils.  On any failure every handle is
- * NULL, nothing is left allocated, and the status is the first failure's
- * (EB_ERR_INVALID also for n_geom < 1 or mixed dimensions). */
+ * those of n calls of eb_build_stencils.  The per-geometry phases before and
+ * after the shared launch run on up to 8 library-owned host threads, each
+ * with its own stream ordered after `stream`; the call returns when all of
+ * them are done, with `stream` ordered after the work.  On any failure every
+ * handle is NULL, nothing is left allocated, and the status, message and
+ * faces are those of the lowest-numbered failing geometry (EB_ERR_INVALID
+ * also for n_geom < 1 or mixed dimensions). */
 eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb_params* params, eb_stencils** out,
                                   eb_build_info* infos, eb_stream_t stream);
 

@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "eb_apply.cuh"
@@ -142,6 +143,11 @@ static cudaMemPool_t eb_pool() {
   }
   uint64_t thr = UINT64_MAX;
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  // memory freed in one stream is reused by another only once the free has completed (or an event
+  // orders the two): never by making the allocating stream wait, which would serialise the streams of
+  // a batch's worker threads
+  int no = 0;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   pools[dev] = pool;
   return pool;
 }
@@ -152,19 +158,48 @@ static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
   return cudaMalloc(p, bytes);
 }
 
+// Bump allocation from chunks of pooled memory that grow geometrically (1 MB, 2 MB, ... 64 MB): a
+// build makes dozens of small arrays, and one pool allocation costs tens of microseconds of host time
+// when several threads allocate at once.  Arrays of 4 MB or more get their own allocation.  Blocks
+// are 256-byte aligned; the chunks and large arrays are recorded in `owned` for their release.
+static cudaError_t arena_alloc(Arena& a, void** p, size_t bytes, cudaStream_t s, std::vector<void*>& owned) {
+  constexpr size_t LARGE = (size_t)4 << 20, MAX_CHUNK = (size_t)64 << 20;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes >= LARGE) {
+    cudaError_t e = pool_alloc(p, bytes, s);
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+  }
+  if (bytes > a.left) {
+    void* c = nullptr;
+    const size_t sz = std::max(a.next, bytes);  // the chunk holds at least this request
+    cudaError_t e = pool_alloc(&c, sz, s);
+    if (e != cudaSuccess) return e;
+    owned.push_back(c);
+    a.cur = (char*)c;
+    a.left = sz;
+    if (a.next < MAX_CHUNK) a.next *= 2;
+  }
+  if (bytes > a.left) return cudaErrorMemoryAllocation;  // unreachable: the chunk was sized for it
+  *p = a.cur;
+  a.cur += bytes;
+  a.left -= bytes;
+  return cudaSuccess;
+}
+
 template <typename T>
 static eb_status dalloc(eb_stencils* st, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = pool_alloc((void**)p, count * sizeof(T), st->build_stream);
+  cudaError_t e = arena_alloc(st->arena, (void**)p, count * sizeof(T), st->build_stream, st->allocs);
   if (e != cudaSuccess) return cuda_status(e, "device allocation");
-  st->allocs.push_back((void*)*p);
   return EB_OK;
 }
 
 // temporary allocations, freed in stream order at scope exit
 struct Tmp {
   cudaStream_t s = nullptr;
+  Arena arena;
   std::vector<void*> ptrs;
   ~Tmp() {
     for (void* p : ptrs) cudaFreeAsync(p, s);
@@ -173,9 +208,8 @@ struct Tmp {
   eb_status get(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = pool_alloc((void**)p, count * sizeof(T), s);
+    cudaError_t e = arena_alloc(arena, (void**)p, count * sizeof(T), s, ptrs);
     if (e != cudaSuccess) return cuda_status(e, "device allocation");
-    ptrs.push_back((void*)*p);
     return EB_OK;
   }
 };
@@ -500,6 +534,9 @@ struct BuildCtx {
   double* invk = nullptr;
   LsArgs la;            // least-squares inputs (scratch, work counter and error word set per launch)
   int32_t* status = nullptr;
+  eb_status rc = EB_OK;  // a phase's failure in a batch worker thread, with its message and faces
+  std::string err;
+  std::vector<int64_t> bad;
   ~BuildCtx() {
     for (int i = 0; i < n_ev; ++i) cudaEventDestroy(ev[i]);
   }
@@ -539,15 +576,53 @@ eb_status eb_build_stencils(const eb_geom* geom, const eb_params* params, eb_ste
   return EB_OK;
 }
 
+// The per-geometry phases of a batch run on several host threads, each with its own stream, so that
+// their launches, small host reads and allocations overlap; the least-squares launch of all the
+// geometries runs on the caller's stream between the two phases.
+static constexpr int BATCH_MAX_THREADS = 8;
+
 eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb_params* params, eb_stencils** out,
                                   eb_build_info* infos, eb_stream_t stream) {
   if (!out || !geoms || n_geom < 1) { set_error("bad batch arguments"); return EB_ERR_INVALID; }
   for (int32_t i = 0; i < n_geom; ++i) out[i] = nullptr;
   g_bad_faces.clear();
   cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  EB_CUDA(cudaGetDevice(&dev));
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthr = (int)std::min<int64_t>(n_geom, std::min<unsigned>(BATCH_MAX_THREADS, hw));
+  std::vector<cudaStream_t> ws(nthr, nullptr);
+  std::vector<cudaEvent_t> wev(nthr, nullptr);
+  cudaEvent_t sev = nullptr;
   std::vector<BuildCtx*> cs(n_geom, nullptr);
   std::vector<eb_build_info> local(n_geom);
   eb_status r = EB_OK;
+  auto cleanup = [&](eb_status rr) {
+    if (rr != EB_OK) cudaStreamSynchronize(s);
+    for (int t = 0; t < nthr; ++t)
+      if (ws[t]) cudaStreamSynchronize(ws[t]);
+    for (int32_t i = 0; i < n_geom; ++i) {
+      if (!cs[i]) continue;
+      if (rr == EB_OK) out[i] = cs[i]->st;
+      else eb_stencils_destroy(cs[i]->st);
+      delete cs[i];  // returns its temporaries in its worker stream's order
+    }
+    for (int t = 0; t < nthr; ++t) {
+      if (wev[t]) cudaEventDestroy(wev[t]);
+      if (ws[t]) cudaStreamDestroy(ws[t]);
+    }
+    if (sev) cudaEventDestroy(sev);
+    return rr;
+  };
+  for (int t = 0; t < nthr; ++t) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ws[t], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&wev[t], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(cuda_status(e, "batch worker streams"));
+  }
+  {
+    cudaError_t e = cudaEventCreateWithFlags(&sev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(cuda_status(e, "batch events"));
+  }
   for (int32_t i = 0; i < n_geom; ++i) {
     cs[i] = new BuildCtx();
     BuildCtx& c = *cs[i];
@@ -556,18 +631,67 @@ eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb
     c.st = new eb_stencils();
     memset(&local[i], 0, sizeof(eb_build_info));
     c.info = infos ? &infos[i] : &local[i];
-    c.s = s;
+    c.s = ws[i % nthr];
   }
-  for (int32_t i = 0; i < n_geom && r == EB_OK; ++i) r = build_pre(*cs[i]);
-  if (r == EB_OK) r = build_ls(cs.data(), n_geom, s);
-  for (int32_t i = 0; i < n_geom && r == EB_OK; ++i) r = build_post(*cs[i]);
-  if (r != EB_OK) cudaStreamSynchronize(s);
-  for (int32_t i = 0; i < n_geom; ++i) {
-    if (r == EB_OK) out[i] = cs[i]->st;
-    else eb_stencils_destroy(cs[i]->st);
-    delete cs[i];
-  }
-  return r;
+  // worker streams start after the caller's stream (the geometry may come from it) and after the
+  // least-squares launch; the caller's stream waits for the workers before that launch and at the end
+  auto fork = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventRecord(sev, s);
+    for (int t = 0; t < nthr && e == cudaSuccess; ++t) e = cudaStreamWaitEvent(ws[t], sev, 0);
+    return e;
+  };
+  auto join = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < nthr && e == cudaSuccess; ++t) {
+      e = cudaEventRecord(wev[t], ws[t]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, wev[t], 0);
+    }
+    return e;
+  };
+  auto phase = [&](bool post) -> eb_status {
+    std::atomic<bool> failed(false);
+    auto work = [&](int t) {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        failed = true;
+        return;
+      }
+      for (int32_t i = t; i < n_geom && !failed; i += nthr) {
+        BuildCtx& c = *cs[i];
+        g_err.clear();
+        g_bad_faces.clear();
+        const eb_status ri = post ? build_post(c) : build_pre(c);
+        if (ri != EB_OK) {
+          c.rc = ri;
+          c.err = g_err;
+          c.bad = g_bad_faces;
+          failed = true;
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    for (int32_t i = 0; i < n_geom; ++i)
+      if (cs[i]->rc != EB_OK) {
+        set_error(cs[i]->err);
+        g_bad_faces = cs[i]->bad;
+        return cs[i]->rc;
+      }
+    return failed ? EB_ERR_CUDA : EB_OK;
+  };
+  cudaError_t e = fork();
+  if (e != cudaSuccess) return cleanup(cuda_status(e, "batch fork"));
+  r = phase(false);
+  if (r != EB_OK) return cleanup(r);
+  if ((e = join()) != cudaSuccess) return cleanup(cuda_status(e, "batch join"));
+  r = build_ls(cs.data(), n_geom, s);
+  if (r != EB_OK) return cleanup(r);
+  if ((e = fork()) != cudaSuccess) return cleanup(cuda_status(e, "batch fork"));
+  r = phase(true);
+  if (r != EB_OK) return cleanup(r);
+  if ((e = join()) != cudaSuccess) return cleanup(cuda_status(e, "batch join"));
+  return cleanup(EB_OK);
 }
 
 // apply order of the footprint for the quad layout (eb_apply_quad.cuh): groups of four wide segments,
@@ -890,7 +1014,8 @@ static eb_status build_pre(BuildCtx& c) {
   EB_CUDA(cudaMemsetAsync(counts + n_slots, 0, 8, s));
   EB_TRY(scan<int64_t>(counts, n_slots + 1, st->row_ptr, &nnz, s, tmp));
   int32_t h_too = 0;
-  EB_CUDA(cudaMemcpy(&h_too, too_many, 4, cudaMemcpyDeviceToHost));
+  EB_CUDA(cudaMemcpyAsync(&h_too, too_many, 4, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
   if (h_too) { set_error("a face has more LS rows than the kernel supports"); return EB_ERR_CAPACITY; }
   EB_TRY(dalloc(st, &st->row_desc, nnz));
   EB_TRY(dalloc(st, &st->row_val, nnz));
@@ -1306,7 +1431,8 @@ static eb_status build_post(BuildCtx& c) {
     int64_t n_open = 0, n_cls = 0;
     for (int d = 0; d < D; ++d) {
       std::vector<int32_t> hs(dm.nface[d]);
-      EB_CUDA(cudaMemcpy(hs.data(), st->face_slot[d], dm.nface[d] * 4, cudaMemcpyDeviceToHost));
+      EB_CUDA(cudaMemcpyAsync(hs.data(), st->face_slot[d], dm.nface[d] * 4, cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
       for (int32_t v : hs) {
         if (v >= 0) ++n_open;
         if (v >= n_unique) ++n_cls;
@@ -1318,7 +1444,8 @@ static eb_status build_post(BuildCtx& c) {
   info->n_classes = st->n_classes;
   {
     std::vector<int64_t> rp(n_slots + 1);
-    EB_CUDA(cudaMemcpy(rp.data(), st->row_ptr, (n_slots + 1) * 8, cudaMemcpyDeviceToHost));
+    EB_CUDA(cudaMemcpyAsync(rp.data(), st->row_ptr, (n_slots + 1) * 8, cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
     int32_t mx = 0;
     double fl = 0.0;
     int K = T.K;

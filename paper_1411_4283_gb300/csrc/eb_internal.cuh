@@ -62,6 +62,15 @@ struct DevBuf {
 
 }  // namespace eb
 
+namespace eb {
+// Bump allocation state over chunks of pooled device memory (see arena_alloc in eb_api.cu).
+struct Arena {
+  char* cur = nullptr;
+  size_t left = 0;
+  size_t next = (size_t)1 << 20;  // size of the next chunk
+};
+}  // namespace eb
+
 struct eb_stencils {
   eb::Dims dm;
   // geometry copies
@@ -118,8 +127,9 @@ struct eb_stencils {
   // scratch for solves
   void* work = nullptr;
   size_t work_bytes = 0;
-  std::vector<void*> allocs;       // device arrays owned by the stencils (stream-ordered pool)
+  std::vector<void*> allocs;       // device memory owned by the stencils (chunks and large arrays from the pool)
   cudaStream_t build_stream = nullptr;  // stream the arrays are allocated in
+  eb::Arena arena;                 // the stencils' small arrays share chunks
 };
 
 namespace eb {
