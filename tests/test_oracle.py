@@ -50,6 +50,53 @@ def test_minimum_weighted_norm_conditions(Q):
         assert np.linalg.norm(t - Qm @ (Qm.T @ t)) <= 1e-10 * np.linalg.norm(t), f
 
 
+def test_min_norm_against_high_precision_normal_equations():
+    """The oracle's FP64 least-squares route (SVD-based lstsq of (WA)^T t = F, s = W t) against the
+    same minimum-||W^-1 s|| solution computed by another route at 50 significant digits: the
+    normal equations s = W B (B^T B)^-1 F with B = W A (Sec. 2.2.1), in mpmath, on 100 faces
+    (grid faces and EB faces) of the Q = 4 circle problem."""
+    mpmath = pytest.importorskip("mpmath")
+    g = E.circle_config(32)
+    o = Oracle(g, Params(order=4))
+    faces = o.flux_faces()
+    ncut = len(g.cut_cells)
+    rng = np.random.default_rng(5)
+    sample = list(rng.choice(faces[:-ncut], 60, replace=False)) + list(faces[-ncut:][:40])
+    mp = mpmath.mp
+    mp.dps = 50
+    for f in sample:
+        A, F, w, _ = o.face_system(int(f))
+        _, s = o.stencil(int(f))
+        B = mpmath.matrix((w[:, None] * A).tolist())
+        G = B.T * B
+        y = mpmath.lu_solve(G, mpmath.matrix(F.tolist()))
+        t = B * y
+        ref = np.array([float(w[i] * t[i]) for i in range(len(w))])
+        assert np.abs(s - ref).max() <= 1e-11 * np.abs(ref).max(), f
+
+
+def test_stencil_is_row_permutation_equivariant():
+    """Reordering the rows of a face's system (volumes, wall faces, EB faces) reorders its stencil
+    the same way: the minimum-norm solution does not depend on the row order (Sec. 2.2.1).
+    Checked through the oracle's own solve on permuted systems."""
+    g = E.circle_config(24)
+    o = Oracle(g, Params(order=4))
+    faces = o.flux_faces()
+    rng = np.random.default_rng(6)
+    orig = o.face_system
+    for f in list(rng.choice(faces, 25, replace=False)):
+        A, F, w, cols = orig(int(f))
+        perm = rng.permutation(len(w))
+        o.face_system = lambda fid, A=A, F=F, w=w, cols=cols, perm=perm: (A[perm], F, w[perm], cols[perm])
+        try:
+            cp, sp_ = o.stencil(int(f))
+        finally:
+            o.face_system = orig
+        _, s = o.stencil(int(f))
+        assert np.array_equal(cp, cols[perm])
+        assert np.abs(sp_ - s[perm]).max() <= 1e-13 * np.abs(s).max(), f
+
+
 def _face_body(g, d, loc):
     pos = np.searchsorted(g.cut_faces[d], loc)
     if pos < len(g.cut_faces[d]) and g.cut_faces[d][pos] == loc:
