@@ -35,7 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cut-face LS stencils/s; EB Laplacian apply GB/s (% HBM); solve s at fixed error"
-LSQ_DRAM_BYTES_PER_SYSTEM = 911.65e6 / 90123
+# DRAM bytes (read + write) of one k_lsq launch per LS system solved, from the ncu capture of the
+# 48^3 build (profiles/k_lsq_sphere48.md): 823.3 MB read + 7363.4 MB written for 90,123 systems.  The
+# writes are the per-warp row scratch (each system's rows, kept for the corrected semi-normal step)
+# leaving L2.
+LSQ_DRAM_BYTES_PER_SYSTEM = (823.290368e6 + 7363.410e6) / 90123
 
 
 def parse():
