@@ -153,11 +153,13 @@ def dist_setup(args):
 
 
 def barrier_max(ws, val):
+    """The largest of the ranks' values (the slowest rank's time): every rank gets it."""
     if ws <= 1:
         return val
     import torch
     import torch.distributed as dist
-    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([val], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -1,0 +1,49 @@
+"""The replica path of bench.py on two gloo ranks (CPU): each rank times its own replica and the
+reported time is the slowest rank's, so the whole-job value counts all ranks' units over it."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        ms = 100.0 + 50.0 * rank  # rank 1 is the slower replica
+        q.put((rank, bench.barrier_max(ws, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_barrier_max_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in ps)
+    got = dict(q.get(timeout=5) for _ in range(2))
+    assert got == {0: 150.0, 1: 150.0}
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.barrier_max(1, 12.5) == 12.5
