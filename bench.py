@@ -27,6 +27,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -270,8 +271,7 @@ def main():
         del st
     torch.cuda.synchronize()
     # timed region
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clocks = Clocks(os.path.join(os.environ.get("EB_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_rank{rank}.csv"))
     clocks.start()
     if ws > 1:
         torch.distributed.barrier()

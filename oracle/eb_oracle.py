@@ -34,11 +34,16 @@ Everything is computed face by face from the paper's definitions:
 All moments are used in h-scaled coordinates xi = (x - x0)/h: since A^T s = F
 is homogeneous in h, s = h^{D-2} s_hat with s_hat from the scaled system.
 
-Readings of passages that are silent, ambiguous or garbled (each listed in
-the design doc): neighbourhood = face-connected path distance <= R_n through
-faces with area fraction > 0; x_i and x0 are Cartesian centres (not
+Readings of passages that are silent, ambiguous or garbled: neighbourhood =
+the volumes of the max-norm box of radius R_n around each adjacent volume,
+reached through faces with area fraction > 0 (the face-connected path reading
+is the ``metric="path"`` option); x_i and x0 are Cartesian centres (not
 centroids); interior faces use the same weighted LS stencil as cut faces;
-rank-deficient systems raise instead of falling back.
+rank-deficient systems raise instead of falling back.  Neumann EB faces: the
+least squares is the paper's, in physical units.  In the h-scaled system a
+Neumann row is a derivative in xi, so its datum enters as h <g> and its weight
+is W_ii / h (the physical minimum-norm problem, rescaled); the flux through a
+Neumann EB face is the datum, |A_f| <g>_f.
 """
 from __future__ import annotations
 
@@ -91,6 +96,8 @@ class Params:
                               # distance <= R_n
     w_threshold: float = 0.5
     w_power: float = 5.0
+    neumann_weight: str = "physical"  # "physical" (default): Neumann rows weighted W_ii / h in the
+                              # scaled system (the physical minimum-norm problem); "scaled": W_ii
 
     def radius(self) -> int:
         if self.path_radius is not None:
@@ -445,7 +452,10 @@ class Oracle:
             cols.append(-(1 + wf))
         for e in ebs:
             rows.append(self._boundary_row(e, "eb", x0))
-            w.append(self._weight(self.cell_center(int(self.g.cut_cells[e])), x0))
+            we = self._weight(self.cell_center(int(self.g.cut_cells[e])), x0)
+            # Neumann row: its coefficient is h^(D-1) s_hat, not h^(D-2) s_hat, so the physical
+            # minimum-norm problem weighs it with W_ii / h in the scaled system
+            w.append(we / self.h if self.bc_eb[e] == 1 and self.p.neumann_weight == "physical" else we)
             cols.append(-(1 + self.eb_id(e)))
         return np.array(rows), self.flux_vector(fid, x0), np.array(w), np.array(cols, dtype=np.int64)
 
@@ -537,7 +547,10 @@ class Oracle:
                 Lr.append(np.full(int(vm.sum()), c)); Lc.append(cols[vm]); Lv.append(scale * sv[vm])
                 bm = ~vm
                 if bm.any():
-                    Br.append(np.full(int(bm.sum()), c)); Bc.append(bpos[-cols[bm] - 1]); Bv.append(scale * sv[bm])
+                    bc = -cols[bm] - 1
+                    # a Neumann row is a derivative in xi = (x - x0)/h: its datum enters as h <g>
+                    hn = np.array([self.h if self._is_neumann(int(b)) else 1.0 for b in bc])
+                    Br.append(np.full(int(bm.sum()), c)); Bc.append(bpos[bc]); Bv.append(scale * sv[bm] * hn)
         n = g.ncell
         cat = lambda a: np.concatenate(a) if a else np.zeros(0)
         L = sp.csr_matrix((cat(Lv), (cat(Lr).astype(np.int64), cat(Lc).astype(np.int64))), shape=(n, n))

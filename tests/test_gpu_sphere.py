@@ -2,7 +2,8 @@
 solution errors at N = 32 and 64 against the paper's table, and the observed order.
 
 At N = 32 the FP64 oracle gives L_inf 1.016e-4, L1 1.539e-5, L2 2.423e-5 (a uniform 1.11x the
-printed values); the GPU must reproduce the oracle's numbers, sit within 15% of the
+printed values: a difference in the 3-D problem set-up rather than in a norm or neighbourhood
+reading, which would move the three norms differently); the GPU must reproduce the oracle's numbers, sit within 15% of the
 paper's, and converge at fourth order between N = 32 and 64.
 """
 import json
