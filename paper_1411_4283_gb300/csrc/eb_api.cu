@@ -1141,12 +1141,12 @@ static eb_status build_post(BuildCtx& c) {
     std::vector<int64_t> hf(n_slots);
     EB_CUDA(cudaMemcpyAsync(hf.data(), st->slot_face, n_slots * 8, cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
-    int unsupported = 0;
+    int unbuilt = 0;
     for (int64_t i = 0; i < n_slots; ++i) {
       if (hs[i] == 1) g_bad_faces.push_back(hf[i]);
-      if (hs[i] == 2) unsupported = 1;
+      if (hs[i] == 2) unbuilt = 1;  // a row flagged by the row builder
     }
-    if (unsupported) { set_error("Neumann EB rows are not supported by the GPU build"); return EB_ERR_INVALID; }
+    if (unbuilt) { set_error("an LS row could not be built"); return EB_ERR_INVALID; }
     if (!g_bad_faces.empty()) {
       set_error("rank-deficient LS systems: " + std::to_string(g_bad_faces.size()) + " faces");
       return EB_ERR_RANK_DEFICIENT;
@@ -1256,6 +1256,8 @@ static eb_status build_post(BuildCtx& c) {
     aa.rows64 = st->rows64;
     aa.rows32 = st->rows32;
     aa.inv_h2 = 1.0 / (dm.h * dm.h);
+    aa.eb_bc = st->eb_bc;
+    aa.eb_mom = st->eb_mom;
     int32_t* aerr;
     EB_TRY(tmp.get(&aerr, 1));
     EB_CUDA(cudaMemsetAsync(aerr, 0, 4, s));

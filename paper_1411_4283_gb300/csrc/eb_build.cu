@@ -507,10 +507,26 @@ __device__ double row_prepare(const LsArgs& a, const Tables& T, uint32_t desc, c
       for (int i = 0; i < K; ++i) row[i] = fr[i];
       return w;
     }
-    if (kind == 1) {
-      if (a.eb_bc && a.eb_bc[cut] != 0) *bad = 1;  // Neumann EB rows are not supported on the GPU path
-      src = a.eb_mom + (int64_t)cut * dm.KS;
-    } else src = cut >= 0 ? a.vol_mom + (int64_t)cut * dm.KS : T.full_vol;
+    if (kind == 1 && a.eb_bc && a.eb_bc[cut] != 0) {
+      // Neumann row (Sec. 2.2.1): (1/m^0) sum_d p_d m^{p - e_d}_d, from the EB moments weighted by
+      // the normal components, shifted to x0.  It is a derivative in xi = (x - x0)/h, so its
+      // coefficient is h^(D-1) s_hat and the physical minimum-norm problem weighs it with W_ii / h.
+      const double wn = w / dm.h;
+      double sh[MAXK];
+      for (int i = 0; i < K; ++i) row[i] = 0.0;
+      for (int d = 0; d < dm.dim; ++d) {
+        shift_moments(T, a.eb_nmom + ((int64_t)cut * dm.dim + d) * dm.KS, delta, sh);
+        for (int i = 0; i < K; ++i) {
+          const int lo = T.lower[d][i];
+          if (lo >= 0) row[i] = fma((double)T.mon[i][d], sh[lo], row[i]);
+        }
+      }
+      const double sc = wn / a.eb_mom[(int64_t)cut * dm.KS];
+      for (int i = 0; i < K; ++i) row[i] *= sc;
+      return wn;
+    }
+    if (kind == 1) src = a.eb_mom + (int64_t)cut * dm.KS;
+    else src = cut >= 0 ? a.vol_mom + (int64_t)cut * dm.KS : T.full_vol;
   }
   row[0] = __longlong_as_double((long long)(uintptr_t)src);
   row[1] = delta[0];
@@ -1027,6 +1043,11 @@ __device__ int cell_faces(const AsmArgs& a, const int* x, int64_t c, int32_t* sl
   return nf;
 }
 
+// the cell is cut and its EB face carries Neumann data (the EB face is the last of cell_faces)
+__device__ __forceinline__ bool neumann_eb(const AsmArgs& a, int64_t c) {
+  return a.flag[c] == 2 && a.eb_bc[a.cut_of_cell[c]] != 0;
+}
+
 __device__ __forceinline__ int foot_index(const AsmArgs& a, int dx, int dy, int dz) {
   int L = a.dm.R + 1, S = 2 * L + 1;
   if (dx < -L || dx > L || dy < -L || dy > L || dz < -L || dz > L) return -1;
@@ -1050,6 +1071,8 @@ __global__ void k_assemble_rows(AsmArgs a, const int32_t* __restrict__ rep_cell,
   double sig[8];
   int bases[8][3];
   int nf = cell_faces(a, x, c, slots, sig, bases);
+  // the flux through a Neumann EB face is its datum (a column of B), not a stencil
+  if (neumann_eb(a, c)) --nf;
   for (int q = 0; q < nf; ++q) {
     int64_t p0 = a.row_ptr[slots[q]], p1 = a.row_ptr[slots[q] + 1];
     for (int64_t p = p0 + lane; p < p1; p += 32) {
@@ -1086,6 +1109,16 @@ __global__ void k_assemble_b(AsmArgs a, const int32_t* __restrict__ cells, int64
   int nf = cell_faces(a, x, c, slots, sig, bases);
   int64_t k = bptr ? bptr[t] : 0;
   int64_t n = 0;
+  if (neumann_eb(a, c)) {
+    // Neumann EB face: the flux is the datum, |A_f| <g>_f (sigma = +1, kappa-weighted scale 1/h^2)
+    --nf;
+    if (bptr) {
+      const int32_t cut = a.cut_of_cell[c];
+      bcol[k + n] = dm.n_grid_faces + cut;
+      bval[k + n] = a.eb_mom[(int64_t)cut * dm.KS] * dm.h * a.inv_h2;
+    }
+    ++n;
+  }
   for (int q = 0; q < nf; ++q) {
     int64_t p0 = a.row_ptr[slots[q]], p1 = a.row_ptr[slots[q] + 1];
     for (int64_t p = p0; p < p1; ++p) {
@@ -1096,14 +1129,18 @@ __global__ void k_assemble_b(AsmArgs a, const int32_t* __restrict__ cells, int64
         int y[3];
         for (int d = 0; d < 3; ++d) y[d] = bases[q][d] + (d < dm.dim ? rd_off(ds, d) : 0);
         int64_t col;
-        if (kind == 1) col = dm.n_grid_faces + a.cut_of_cell[cell_id(dm, y)];
-        else {
+        double sc = 1.0;
+        if (kind == 1) {
+          const int32_t cut = a.cut_of_cell[cell_id(dm, y)];
+          col = dm.n_grid_faces + cut;
+          if (a.eb_bc[cut] != 0) sc = dm.h;  // a Neumann row's datum enters as h <g> (derivative in xi)
+        } else {
           int wd = rd_wdir(ds);
           if (rd_wside(ds)) y[wd] += 1;
           col = dm.face_base[wd] + face_local(dm, wd, y);
         }
         bcol[k + n] = col;
-        bval[k + n] = sig[q] * a.row_val[p] * a.inv_h2;
+        bval[k + n] = sig[q] * a.row_val[p] * a.inv_h2 * sc;
       }
       ++n;
     }

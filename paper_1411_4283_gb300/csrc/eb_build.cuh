@@ -102,6 +102,8 @@ struct AsmArgs {
   double* rows64;
   float* rows32;
   double inv_h2;
+  const uint8_t* eb_bc;   // [n_cut] 0 Dirichlet, 1 Neumann
+  const double* eb_mom;   // [n_cut][KS] (the EB area fraction is entry 0)
 };
 
 __global__ void k_mark(Dims dm, const uint8_t* flag, uint8_t* mark);

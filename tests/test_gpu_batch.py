@@ -69,19 +69,16 @@ def test_batch_rejects_mixed_dimensions():
 
 
 def test_batch_failure_in_a_worker_reaches_the_caller():
-    """A geometry that the GPU build rejects (a Neumann EB face) fails the whole batch with its own
-    status and message, although its phases ran on a worker thread; the other geometries' stencils
-    are released and a later batch works."""
+    """A geometry that the build rejects (moment tables shallower than the order) fails the whole
+    batch with its own status and message, although its phases ran on a worker thread; the other
+    geometries' stencils are released and a later batch works."""
     import paper_1411_4283_gb300 as P
     gs = [E.circle_config(16 + 4 * i) for i in range(6)]
-    bad = gs[3]
-    eb_bc = np.zeros(len(bad.cut_cells), dtype=np.uint8)
-    eb_bc[0] = 1
     dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
-    dgs[3] = P.DeviceGeometry.from_geometry(bad, eb_bc=eb_bc)
+    dgs[3].moment_degree = 2
     with pytest.raises(P.EbError) as ei:
         P.eb_build_stencils_batch(dgs, order=4)
-    assert ei.value.code == 1 and "Neumann" in str(ei.value)
-    dgs[3] = P.DeviceGeometry.from_geometry(bad)
+    assert ei.value.code == 1 and "shallower" in str(ei.value)
+    dgs[3] = P.DeviceGeometry.from_geometry(gs[3])
     batch = P.eb_build_stencils_batch(dgs, order=4)
     assert len(batch) == len(gs)
