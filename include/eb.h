@@ -78,7 +78,10 @@ typedef struct eb_geom {
   const double* vol_mom;     /* [n_cut][K_D] volume moments */
   const double* eb_mom;      /* [n_cut][K_D] EB-patch moments */
   const double* eb_nmom;     /* [n_cut][dim][K_D] EB moments weighted by the normal component */
-  const uint8_t* eb_bc;      /* [n_cut] EB_DIRICHLET/EB_NEUMANN, or NULL = all Dirichlet */
+  const uint8_t* eb_bc;      /* [n_cut] EB_DIRICHLET/EB_NEUMANN, or NULL = all Dirichlet.  Neumann
+                              * rows are the Sec. 2.2.1 b_{f_b p}, weighed as in the physical
+                              * minimum-norm problem; the flux through a Neumann EB face is its
+                              * datum |A_f| <grad phi . n>_f (a column of B) */
   const uint8_t* face_flag[3];  /* per direction [nface_d]: 0 covered, 1 full, 2 cut */
   int32_t n_cutface[3];
   const int32_t* cutface[3];    /* [n_cutface[d]] ascending face indices */
