@@ -311,7 +311,7 @@ def main():
     lsq_share = lsq_ms / ms_step
     if lsq_share >= apply_share:
         # DRAM traffic of k_lsq: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 48^3
-        # sphere workload (911.6 MB for 90,123 systems), scaled by the systems of this launch
+        # sphere workload (8.19 GB for 90,123 systems), scaled by the systems of this launch
         traffic = LSQ_DRAM_BYTES_PER_SYSTEM * (bi["n_unique_faces"] + bi["n_classes"]) if args.order == 4 else None
         roof = {"kernel": "k_lsq (FP64 weighted least squares)", "bound": "alu", "achieved": lsq_tflops,
                 "peak": fp64_pk, "unit": "TFLOP/s", "frac": lsq_tflops / fp64_pk, "traffic": traffic,
@@ -334,6 +334,7 @@ def main():
                    "geometry_seconds_host": round(t_geom, 1)},
         "components": {"build_ms": build_ms, "lsq_ms": lsq_ms, "ls_build_stencils_per_s": n_ls / (build_ms / 1e3),
                        "n_cut_face_systems": n_ls, "n_systems_solved": bi["n_unique_faces"] + bi["n_classes"],
+                       "n_eb_face_systems": int(len(g.cut_cells)),
                        "lsq_tflops": lsq_tflops, "lsq_frac_fp64_peak": lsq_tflops / fp64_pk,
                        "apply_fp32_ms": apply_ms, "apply_gbs": apply_gbs, "apply_frac_hbm": apply_gbs / hbm_peak,
                        "apply_alg_bytes": alg_bytes, "solve_ms": ms_step - build_ms,
