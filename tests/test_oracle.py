@@ -296,6 +296,23 @@ def test_spectrum_lambda_max_64():
     assert abs(lam.real - (-104)) < 3.0 and abs(lam.imag) < 1e-6
 
 
+@pytest.mark.slow
+def test_sphere_spectrum_stable_and_first_eigenvalue():
+    """The 3-D example of Sec. 3.6 (inside the sphere of radius 0.45, Dirichlet) at N = 12: every
+    eigenvalue of the (not kappa-weighted) operator lies in the left half-plane (the paper's claim
+    for its examples), and the one with the largest real part is the first Dirichlet eigenvalue of
+    the ball, -(pi / R)^2 = -48.738 (its eigenfunction sin(pi r / R) / r), to 0.1 %."""
+    g = E.sphere_inside_config(12)
+    o = Oracle(g, Params(order=4))
+    L, _ = o.operator()
+    idx = np.nonzero(g.flag > 0)[0]
+    ev = np.linalg.eigvals(L[idx][:, idx].toarray())
+    lam = ev[np.argmax(ev.real)]
+    exact = -(math.pi / 0.45) ** 2
+    assert ev.real.max() < 0
+    assert abs(lam.real - exact) <= 1e-3 * abs(exact) and abs(lam.imag) < 1e-6
+
+
 def test_unweighted_control_is_unstable():
     """Without weights (W = I) the operator has eigenvalues with positive real part (Sec. 2.2.1 and
     Sec. 3.4); with weights every eigenvalue has negative real part."""
