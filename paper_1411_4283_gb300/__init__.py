@@ -86,7 +86,7 @@ def load():
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB
+    path = os.environ.get("EB_LIB_PATH") or _build.LIB  # EB_LIB_PATH: a tuning variant of the library
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_1411_4283_gb300.build.build() "
                           "(there is no CPU fallback)")

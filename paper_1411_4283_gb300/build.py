@@ -7,6 +7,7 @@ benchmark load the library built here.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import json
 import os
 import shutil
 import subprocess
@@ -28,25 +29,44 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _stale(objs, deps) -> bool:
-    if not os.path.exists(LIB):
+TUNED = os.path.join(HERE, "tuned_gb300.json")  # kernel shapes picked by tune.py on a GB300
+
+
+def tuned_flags(path: str = TUNED) -> list:
+    """-D flags of the tuned kernel shapes (empty when no tuning record exists)."""
+    if not os.path.exists(path):
+        return []
+    with open(path) as f:
+        best = json.load(f).get("best", {})
+    return [f"-D{k}={int(v)}" for k, v in sorted(best.items())]
+
+
+def _stale(lib, deps) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(os.path.join(OUT_DIR, "obj"), exist_ok=True)
+def build(force: bool = False, verbose: bool = False, out_dir: str = OUT_DIR, flags=None) -> str:
+    """Compile into out_dir/libeb_gb300.so.  flags: extra nvcc flags (default: EB_NVCC_FLAGS from the
+    environment, else the tuned kernel shapes)."""
+    lib = os.path.join(out_dir, "libeb_gb300.so")
+    os.makedirs(os.path.join(out_dir, "obj"), exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "eb.h")]
-    if not force and not _stale([], deps):
-        return LIB
+    if os.path.exists(TUNED):
+        deps.append(TUNED)
+    if not force and flags is None and not _stale(lib, deps):
+        return lib
+    if flags is None:
+        env = os.environ.get("EB_NVCC_FLAGS")
+        flags = env.split() if env is not None else tuned_flags()
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, "obj", src.replace(".cu", ".o"))
-        extra = os.environ.get("EB_NVCC_FLAGS", "").split()  # e.g. kernel-shape overrides for tuning
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, "obj", src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -56,13 +76,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

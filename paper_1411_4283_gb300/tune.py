@@ -1,0 +1,104 @@
+"""Autotuner of the compile-time kernel shapes, run on the target GPU.
+
+The least-squares kernel's shape is fixed at compile time: how many systems one CTA keeps in
+flight (EB_LS_SYS; their shared-memory blocks must fit in 227 KB) and how many rows each lane holds
+per chunk (EB_LS_RPL; larger chunks amortise the per-step Householder scalars and column sums over
+more rows but leave fewer warps per SM to hide the serial parts).  Each candidate is compiled into
+its own copy of the library (a candidate whose blocks do not fit fails its compile-time check and
+is skipped), timed in a fresh process that builds the stencils of the 3-D sphere workload and reads
+the least-squares launch's device time, and the fastest is written to tuned_gb300.json, from which
+build.py takes the default flags.
+
+    python -m paper_1411_4283_gb300.tune --n 128 --reps 2
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CANDIDATES = [(4, 4), (3, 5), (3, 6), (2, 8), (4, 3), (2, 6)]
+
+
+def flags_of(shape) -> list:
+    return [f"-DEB_LS_SYS={shape[0]}", f"-DEB_LS_RPL={shape[1]}"]
+
+
+def build_variant(shape) -> str | None:
+    """Library path of the candidate, or None when it does not compile (shared memory)."""
+    out = os.path.join(HERE, "_lib", "tune", f"sys{shape[0]}_rpl{shape[1]}")
+    try:
+        return _build.build(force=True, out_dir=out, flags=flags_of(shape))
+    except RuntimeError:
+        return None
+
+
+_MEASURE = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import torch
+import eb_inputs as E
+import paper_1411_4283_gb300 as P
+g = E.sphere_box_config({n}, seed=2)
+dg = P.DeviceGeometry.from_geometry(g)
+ms = []
+for _ in range({reps} + 1):
+    st = P.eb_build_stencils(dg, order=4)
+    torch.cuda.synchronize()
+    ms.append(st.info["ms_lsq"])
+    del st
+print(json.dumps({{"ms_lsq": min(ms[1:])}}))
+"""
+
+
+def measure(lib: str, n: int, reps: int) -> float:
+    """Least-squares launch time (ms, best of reps after one warm-up build) with library lib."""
+    env = dict(os.environ, EB_LIB_PATH=lib)
+    r = subprocess.run([sys.executable, "-c", _MEASURE.format(root=ROOT, n=n, reps=reps)], capture_output=True,
+                       text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return float(json.loads(r.stdout.strip().splitlines()[-1])["ms_lsq"])
+
+
+def tune(n: int = 128, reps: int = 2, candidates=CANDIDATES, build_fn=build_variant, measure_fn=measure,
+         out: str = _build.TUNED) -> dict:
+    """Time every candidate that compiles; write and return the record with the fastest as `best`."""
+    results = []
+    for shape in candidates:
+        lib = build_fn(shape)
+        if lib is None:
+            results.append({"EB_LS_SYS": shape[0], "EB_LS_RPL": shape[1], "ms_lsq": None,
+                            "note": "does not fit in shared memory"})
+            continue
+        results.append({"EB_LS_SYS": shape[0], "EB_LS_RPL": shape[1], "ms_lsq": measure_fn(lib, n, reps)})
+    timed = [r for r in results if r["ms_lsq"] is not None]
+    if not timed:
+        raise RuntimeError("no candidate compiled")
+    best = min(timed, key=lambda r: r["ms_lsq"])
+    rec = {"workload": f"3-D unit cube minus sphere r=0.35 (seed 2), {n}^3, Q=4: least-squares launch (ms)",
+           "date": time.strftime("%Y-%m-%d"), "results": results,
+           "best": {"EB_LS_SYS": best["EB_LS_SYS"], "EB_LS_RPL": best["EB_LS_RPL"]}}
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--n", type=int, default=128)
+    p.add_argument("--reps", type=int, default=2)
+    a = p.parse_args()
+    print(json.dumps(tune(a.n, a.reps), indent=1))
+
+
+if __name__ == "__main__":
+    main()
