@@ -644,3 +644,22 @@ def run_problem(geom, man, params: Params | None = None, bc_eb=None, solve: bool
         out["phi"] = phi
         out["sol"] = error_norms(phi - Phi, volw, vol)
     return out
+
+
+# --------------------------------------------------------------------- adjoint of one stencil solve
+
+def stencil_adjoint(A: np.ndarray, F: np.ndarray, w: np.ndarray, sbar: np.ndarray):
+    """Reverse-mode derivative of the stencil s = W (A^T W)^+ F of Sec. 2.2.1 (full column rank):
+    given sbar = dJ/ds, returns (Abar, Fbar) = (dJ/dA, dJ/dF) for J = J(s(A, F)).
+
+    Written from s = W B (B^T B)^-1 F with B = W A (the minimum-||W^-1 s|| solution of A^T s = F):
+    with y = (B^T B)^-1 F, t = B y (s = W t), tbar = W sbar and z = (B^T B)^-1 B^T tbar,
+        Fbar = z,   Abar = W [tbar y^T - B (z y^T + y z^T)].
+    The weights are held fixed (they depend on cell and face centres only)."""
+    B = w[:, None] * A
+    G = B.T @ B
+    y = np.linalg.solve(G, F)
+    tbar = w * sbar
+    z = np.linalg.solve(G, B.T @ tbar)
+    Bbar = np.outer(tbar, y) - B @ (np.outer(z, y) + np.outer(y, z))
+    return w[:, None] * Bbar, z

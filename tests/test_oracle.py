@@ -343,3 +343,39 @@ def test_template_face_symmetry():
     for (dx, dy), v in m.items():
         assert abs(v + m[(-1 - dx, dy)]) < 1e-13  # swap the two cells of the face (x -> -1 - x)
         assert abs(v - m[(dx, -dy)]) < 1e-13
+
+
+def test_stencil_adjoint_against_central_differences():
+    """The reverse-mode derivative of one stencil solve (the LS-build adjoint's building block)
+    against central finite differences of the oracle's own forward solve (SVD-based lstsq), for
+    J = c^T s with random c, on random weighted systems and on real face systems of the circle."""
+    from oracle.eb_oracle import stencil_adjoint
+
+    def forward(A, F, w):
+        t = np.linalg.lstsq((w[:, None] * A).T, F, rcond=None)[0]
+        return w * t
+
+    rng = np.random.default_rng(9)
+    g = E.circle_config(24)
+    o = Oracle(g, Params(order=4))
+    systems = [(rng.normal(size=(20, 6)), rng.normal(size=6), rng.uniform(0.1, 1.0, 20))]
+    for f in (o.eb_id(0), o.face_id(0, o.face_local(0, [12, 4]))):
+        A, F, w, _ = o.face_system(f)
+        systems.append((A, F, w))
+    for A, F, w in systems:
+        c = rng.normal(size=len(w))
+        Abar, Fbar = stencil_adjoint(A, F, w, c)
+        eps = 1e-6
+        for _ in range(6):
+            i, j = rng.integers(A.shape[0]), rng.integers(A.shape[1])
+            Ap, Am = A.copy(), A.copy()
+            Ap[i, j] += eps
+            Am[i, j] -= eps
+            fd = (c @ forward(Ap, F, w) - c @ forward(Am, F, w)) / (2 * eps)
+            assert abs(fd - Abar[i, j]) <= 1e-6 * max(1.0, abs(fd)), (i, j, fd, Abar[i, j])
+        for k in range(A.shape[1]):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[k] += eps
+            Fm[k] -= eps
+            fd = (c @ forward(A, Fp, w) - c @ forward(A, Fm, w)) / (2 * eps)
+            assert abs(fd - Fbar[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, Fbar[k])
