@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 # written by tests/golden/make_sphere_golden.py (calls only the oracle)
 ORACLE_32 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sphere_n32.json")))["sol"]
-PAPER = {32: {"linf": 9.16e-05, "l1": 1.38e-05, "l2": 2.17e-05}, 64: {"linf": 6.27e-06, "l1": 9.81e-07, "l2": 1.54e-06}}
+PRINTED = {32: {"linf": 9.16e-05, "l1": 1.38e-05, "l2": 2.17e-05}, 64: {"linf": 6.27e-06, "l1": 9.81e-07, "l2": 1.54e-06}}
 
 
 def _solve(N):
@@ -38,9 +38,9 @@ def test_sphere_errors_and_order():
     e32 = _solve(32)
     for k in ("linf", "l1", "l2"):
         assert e32[k] == pytest.approx(ORACLE_32[k], rel=1e-6), (k, e32[k])
-        assert abs(e32[k] / PAPER[32][k] - 1) < 0.15
+        assert abs(e32[k] / PRINTED[32][k] - 1) < 0.15
     e64 = _solve(64)
     for k in ("linf", "l1", "l2"):
-        assert abs(e64[k] / PAPER[64][k] - 1) < 0.2, (k, e64[k])
+        assert abs(e64[k] / PRINTED[64][k] - 1) < 0.2, (k, e64[k])
         order = np.log2(e32[k] / e64[k])
         assert 3.5 < order < 4.6, (k, order)
