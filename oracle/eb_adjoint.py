@@ -1,0 +1,207 @@
+"""Plain FP64 oracle of the adjoint of the cut-cell Poisson discretisation with respect to a
+geometry parameter (Devendran, Graves, Johansen, arXiv:1411.4283): 2-D, the unit square minus
+circles, derivative with respect to one circle's radius.
+
+TEST INFRASTRUCTURE, like eb_oracle.py: only tests/ may import it; the GPU library never does.
+
+Objective and problem: phi solves the kappa-weighted system kappa L phi = kappa rho with rho = 1
+and homogeneous Dirichlet data on the walls and the circles (Sec. 2.3); J = 1/2 sum_v |V_v| phi_v^2.
+Its derivative with respect to the radius r of one circle, by the adjoint method:
+
+    R(phi, r) = kappa L phi - kappa = 0,   (kappa L)^T lam = |V| phi,
+    dJ/dr = sum_v (h^D phi_v^2 / 2 + lam_v) dkappa_v/dr - lam^T (d(kappa L)/dr) phi,
+
+where kappa L = (1/h^2) sum_f sigma s_hat_f (Sec. 2.3) changes through the stencils of the faces
+whose LS systems hold moments of cut cells, cut faces or EB faces.  Each stencil's change is taken
+through the reverse-mode derivative of its solve (stencil_adjoint) and the derivatives of its
+rows and right-hand side with respect to the moment tables; those come from the moment tables'
+shape derivatives (below), pushed through the oracle's own row construction by the complex step
+(Squire and Trapp 1998: f(m + i e dm) = f(m) + i e f'(m) dm + O(e^2), no cancellation), the rows
+being analytic functions of the moments.
+
+Shape derivatives of the moment tables (fluid outside the circle, boundary moving out with unit
+normal speed as r grows; xi = (x - x_c)/h about the cell or face centre):
+  volume moments   d/dr int_V xi^p dV / h^2 = - int_{EB patch} xi^p ds / h^2 = - eb_mom / h;
+  EB moments       the patch is the arc {c + r e(t)}, t in [ta, tb]:
+                   d/dr int f r dt = int (r grad f . e + f) dt + f(tb) r tb' - f(ta) r ta',
+                   with the endpoint angles moving along the cell edges they lie on;
+  face moments     the covered chord |t - c_t| < s, s = (r^2 - (x_n - c_n)^2)^(1/2), grows at both
+                   ends with speed r / s.
+The cut-cell and cut-face sets are held fixed (the derivative of a fixed topology).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from .eb_oracle import Oracle, Params, stencil_adjoint
+
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(24)
+
+
+def _arcs(cx, cy, r, x0, x1, y0, y1):
+    """Arcs of the circle inside the box [x0,x1]x[y0,y1]: list of ((ta, dta), (tb, dtb)) with the
+    endpoint angles and their derivatives with respect to r (ta < tb)."""
+    pts = []  # (angle, dtheta/dr)
+    for xe in (x0, x1):
+        q = r * r - (xe - cx) ** 2
+        if q > 0:
+            for sg in (-1.0, 1.0):
+                y = cy + sg * math.sqrt(q)
+                if y0 < y < y1:
+                    t = math.atan2(y - cy, xe - cx) % (2 * math.pi)
+                    pts.append((t, math.cos(t) / (r * math.sin(t))))
+    for ye in (y0, y1):
+        q = r * r - (ye - cy) ** 2
+        if q > 0:
+            for sg in (-1.0, 1.0):
+                x = cx + sg * math.sqrt(q)
+                if x0 < x < x1:
+                    t = math.atan2(ye - cy, x - cx) % (2 * math.pi)
+                    pts.append((t, -math.sin(t) / (r * math.cos(t))))
+    pts.sort()
+    arcs = []
+    for i in range(len(pts)):
+        a = pts[i]
+        b = pts[(i + 1) % len(pts)]
+        ta, tb = a[0], b[0] if i + 1 < len(pts) else b[0] + 2 * math.pi
+        tm = 0.5 * (ta + tb)
+        xm, ym = cx + r * math.cos(tm), cy + r * math.sin(tm)
+        if x0 < xm < x1 and y0 < ym < y1:
+            arcs.append(((ta, a[1]), (tb, b[1])))
+    return arcs
+
+
+def circle_moment_derivatives(o: Oracle, body: int):
+    """d/dr of the moment tables of o.g (2-D, fluid outside the circles) for the radius of circle
+    `body`: (dvol [n_cut, K], deb [n_cut, K], debn [n_cut, 2, K], dface [per d: n_cutface, K_F])."""
+    g = o.g
+    assert g.dim == 2 and not g.inside
+    h = g.h
+    cx, cy = g.centers[body, 0], g.centers[body, 1]
+    r = g.radii[body]
+    mons = o.store_mons
+    K = len(mons)
+    n_cut = len(g.cut_cells)
+    deb = np.zeros((n_cut, K))
+    debn = np.zeros((n_cut, 2, K))
+    for k, c in enumerate(g.cut_cells):
+        if g.cut_body[k] != body:
+            continue
+        i, j = int(c) % g.N, int(c) // g.N
+        xc, yc = (i + 0.5) * h, (j + 0.5) * h
+        for (ta, dta), (tb, dtb) in _arcs(cx, cy, r, i * h, (i + 1) * h, j * h, (j + 1) * h):
+            t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+            wq = 0.5 * (tb - ta) * _GL_W
+            e = np.stack([np.cos(t), np.sin(t)])
+            xi = np.stack([(cx + r * e[0] - xc) / h, (cy + r * e[1] - yc) / h])
+            ends = []
+            for tt, dt, sgn in ((ta, dta, -1.0), (tb, dtb, 1.0)):
+                ee = np.array([math.cos(tt), math.sin(tt)])
+                ends.append((np.array([(cx + r * ee[0] - xc) / h, (cy + r * ee[1] - yc) / h]), ee, dt, sgn))
+            for m, p in enumerate(mons):
+                f = xi[0] ** p[0] * xi[1] ** p[1]
+                grad_e = np.zeros_like(t)  # grad_x(xi^p) . e
+                if p[0] > 0:
+                    grad_e += p[0] * xi[0] ** (p[0] - 1) * xi[1] ** p[1] * e[0] / h
+                if p[1] > 0:
+                    grad_e += p[1] * xi[0] ** p[0] * xi[1] ** (p[1] - 1) * e[1] / h
+                for comp in (None, 0, 1):
+                    nd = 1.0 if comp is None else -e[comp]  # normal out of the fluid: -e
+                    val = np.sum(wq * (r * grad_e + f) * nd)
+                    for xe, ee, dt, sgn in ends:
+                        fe = xe[0] ** p[0] * xe[1] ** p[1] * (1.0 if comp is None else -ee[comp])
+                        val += sgn * fe * r * dt
+                    if comp is None:
+                        deb[k, m] += val / h
+                    else:
+                        debn[k, comp, m] += val / h
+    dvol = np.zeros((n_cut, K))
+    mine = g.cut_body == body
+    dvol[mine] = -g.eb_mom[mine] / h  # transport theorem: the fluid loses the patch
+    dface = []
+    for d in range(2):
+        cf = g.cut_faces[d]
+        qn = g.face_mom[d].shape[1]
+        out = np.zeros((len(cf), qn))
+        for k, f in enumerate(cf):
+            if g.cut_face_body[d][k] != body:
+                continue
+            ijk = o.face_coords(d, int(f))
+            xn = ijk[d] * h                       # normal coordinate of the face
+            tdim = 1 - d
+            t0, t1 = ijk[tdim] * h, (ijk[tdim] + 1) * h
+            tcen = 0.5 * (t0 + t1)
+            cn, ct = (cx, cy) if d == 0 else (cy, cx)
+            q = r * r - (xn - cn) ** 2
+            if q <= 0:
+                continue
+            s = math.sqrt(q)
+            for end in (ct - s, ct + s):
+                if t0 < end < t1:
+                    eta = (end - tcen) / h
+                    for m in range(qn):
+                        out[k, m] -= eta ** m * (r / s) / h
+        dface.append(out)
+    return dvol, deb, debn, dface
+
+
+def _perturbed(o: Oracle, dm, eps):
+    """The oracle's geometry arrays moved to m + i eps dm (complex step)."""
+    g = o.g
+    dvol, deb, debn, dface = dm
+    g.vol_mom = g.vol_mom + 1j * eps * dvol
+    g.eb_mom = g.eb_mom + 1j * eps * deb
+    g.eb_nmom = g.eb_nmom + 1j * eps * debn
+    g.face_mom = [fm + 1j * eps * df for fm, df in zip(g.face_mom, dface)]
+
+
+def _restore(o: Oracle, saved):
+    g = o.g
+    g.vol_mom, g.eb_mom, g.eb_nmom, g.face_mom = saved
+
+
+def objective_and_radius_gradient(g, body: int = 0, params: Params | None = None):
+    """(J, dJ/dr) for the radius of circle `body` (see the module docstring)."""
+    o = Oracle(g, params or Params(order=4))
+    h, D = g.h, g.dim
+    st = o.all_stencils()
+    L, _ = o.operator(st, kappa_weighted=True)
+    vol = g.flag > 0
+    idx = np.nonzero(vol)[0]
+    A = L[idx][:, idx].tocsc()
+    kap = g.kappa
+    phi = np.zeros(g.ncell)
+    phi[idx] = spla.spsolve(A, kap[idx])
+    w = kap * h ** D
+    J = 0.5 * float(np.sum(w * phi * phi))
+    lam = np.zeros(g.ncell)
+    lam[idx] = spla.spsolve(A.T.tocsc(), (w * phi)[idx])
+    dm = circle_moment_derivatives(o, body)
+    dkap = np.zeros(g.ncell)
+    dkap[g.cut_cells] = dm[0][:, 0]
+    dJ = float(np.sum((0.5 * h ** D * phi * phi + lam) * dkap))
+    # stencil terms: -lam^T (d(kappa L)/dr) phi = sum_f <c_f, d s_hat_f>, c_f[i] = -(1/h^2) sum_v sigma lam_v phi_col_i
+    eps = 1e-20
+    saved = (g.vol_mom, g.eb_mom, g.eb_nmom, g.face_mom)
+    for fid in o.flux_faces():
+        A0, F0, wf, cols = o.face_system(fid)
+        _perturbed(o, dm, eps)
+        o._full_rows.clear()
+        try:
+            Ac, Fc, _, _ = o.face_system(fid)
+        finally:
+            _restore(o, saved)
+            o._full_rows.clear()
+        dA, dF = np.imag(Ac) / eps, np.imag(Fc) / eps
+        if not (np.any(dA) or np.any(dF)):
+            continue
+        cvec = np.zeros(len(cols))
+        vm = cols >= 0
+        for c, sg in o.face_cells(fid):
+            cvec[vm] -= sg * lam[c] * phi[cols[vm]] / h ** 2
+        Abar, Fbar = stencil_adjoint(np.real(A0), np.real(F0), wf, cvec)
+        dJ += float(np.sum(Abar * dA) + np.sum(Fbar * dF))
+    return J, dJ

@@ -148,6 +148,11 @@ class Oracle:
         self._full_rows: dict = {}
 
     # ----------------------------------------------------------- indexing
+    def _dtype(self):
+        """float64, or complex128 when the moment tables carry a complex-step perturbation."""
+        g = self.g
+        return np.result_type(g.vol_mom, g.eb_mom, g.eb_nmom, *g.face_mom, np.float64)
+
     def cell_coords(self, c: int) -> list[int]:
         out = []
         for d in range(self.D):
@@ -355,7 +360,7 @@ class Oracle:
         delta = fc - x0
         tm = self.grid_face_tangential_moments(d, f)
         tdims = [k for k in range(self.D) if k != d]
-        out = np.zeros(len(mons))
+        out = np.zeros(len(mons), dtype=self._dtype())
         for i, p in enumerate(mons):
             pt = tuple(p[k] for k in tdims)
             acc = 0.0
@@ -398,7 +403,7 @@ class Oracle:
             return np.array([M[self.store_index[m]] for m in self.mons]) / M[self.store_index[(0,) * self.D]]
         # Neumann row: (1/m^0) sum_d p_d m^{p - e_d}_{d}
         m0 = self.eb_moments(cut, x0)[self.store_index[(0,) * self.D]]
-        row = np.zeros(self.K)
+        row = np.zeros(self.K, dtype=self._dtype())
         for d in range(self.D):
             N = self.eb_moments(cut, x0, normal=d)
             for i, p in enumerate(self.mons):
@@ -412,7 +417,7 @@ class Oracle:
         """F_hat_p = integral over f of grad (xi)^p . n (xi about x0; grid faces: n = +e_d;
         EB faces: n out of the fluid), / h^(D-1)."""
         kind = self.decode_face(fid)
-        F = np.zeros(self.K)
+        F = np.zeros(self.K, dtype=self._dtype())
         if kind[0] == "grid":
             d, f = kind[1], kind[2]
             lower = []

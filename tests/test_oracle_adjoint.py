@@ -1,0 +1,43 @@
+"""Pins of the adjoint oracle (oracle/eb_adjoint.py) against central finite differences of what it
+differentiates: the geometry generator's moment tables, and the whole forward problem (moments ->
+stencils -> operator -> solve -> J), for the radius of a circle in the unit square."""
+import numpy as np
+import pytest
+
+import eb_inputs as E
+from oracle.eb_adjoint import circle_moment_derivatives, objective_and_radius_gradient
+from oracle.eb_oracle import Oracle, Params
+
+EPS = 1e-6
+
+
+def _pair(N, center, r, **kw):
+    g = E.circle_config(N, center=center, r=r, **kw)
+    gp = E.circle_config(N, center=center, r=r + EPS, **kw)
+    gm = E.circle_config(N, center=center, r=r - EPS, **kw)
+    assert np.array_equal(gp.cut_cells, g.cut_cells) and np.array_equal(gm.cut_cells, g.cut_cells)
+    for d in range(2):
+        assert np.array_equal(gp.cut_faces[d], g.cut_faces[d]) and np.array_equal(gm.cut_faces[d], g.cut_faces[d])
+    return g, gp, gm
+
+
+def test_moment_shape_derivatives():
+    """Transport-theorem volume derivatives, arc derivatives of the EB moments (with the endpoints
+    sliding along the cell edges) and chord-end derivatives of the face moments, against central
+    differences of the generator's moments (relative to each table's largest derivative)."""
+    g, gp, gm = _pair(16, (0.51, 0.49), 0.3)
+    dvol, deb, debn, dface = circle_moment_derivatives(Oracle(g, Params(order=4)), 0)
+    pairs = [(dvol, gp.vol_mom, gm.vol_mom), (deb, gp.eb_mom, gm.eb_mom), (debn, gp.eb_nmom, gm.eb_nmom)]
+    pairs += [(dface[d], gp.face_mom[d], gm.face_mom[d]) for d in range(2)]
+    for an, a, b in pairs:
+        fd = (a - b) / (2 * EPS)
+        assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
+def test_radius_gradient_adjoint_against_central_differences():
+    """dJ/dr through the solve adjoint and the LS-build adjoint against central differences of J."""
+    g, gp, gm = _pair(16, (0.51, 0.49), 0.3)
+    J, dJ = objective_and_radius_gradient(g)
+    fd = (objective_and_radius_gradient(gp)[0] - objective_and_radius_gradient(gm)[0]) / (2 * EPS)
+    assert J > 0
+    assert abs(dJ - fd) <= 1e-6 * abs(fd)
