@@ -1,6 +1,6 @@
 """Plain FP64 oracle of the adjoint of the cut-cell Poisson discretisation with respect to a
-geometry parameter (Devendran, Graves, Johansen, arXiv:1411.4283): 2-D, the unit square minus
-circles, derivative with respect to one circle's radius.
+geometry parameter (Devendran, Graves, Johansen, arXiv:1411.4283): the unit square minus circles
+(2-D) or the unit cube minus spheres (3-D), derivative with respect to one body's radius.
 
 TEST INFRASTRUCTURE, like eb_oracle.py: only tests/ may import it; the GPU library never does.
 
@@ -148,6 +148,139 @@ def circle_moment_derivatives(o: Oracle, body: int):
     return dvol, deb, debn, dface
 
 
+def _mono_index(D, deg):
+    from eb_inputs.geometry import monomials
+    ms = monomials(D, deg)
+    return ms, {m: i for i, m in enumerate(ms)}
+
+
+def sphere_moment_derivatives(o: Oracle, body: int):
+    """d/dr of the moment tables of o.g (3-D, fluid outside the spheres) for the radius of sphere
+    `body`.  On the sphere, with e = (x - c)/r (n = -e out of the fluid, mean curvature 2/r):
+        d/dr int_{patch} f dA = int_{patch} (d f/d rho + (2/r) f) dA + oint_{edge} f V dl,
+    where the patch's edge lies on the cell's faces and moves, inside the sphere, with the outward
+    conormal speed V = -(e . n_p) / (1 - (e . n_p)^2)^(1/2) (n_p the face's normal out of the cell);
+    the surface integrals come from the generator's patch quadrature of higher-degree monomials,
+    the edge integrals from Gauss-Legendre on the edge arcs.  Face moments: the covered disk of radius
+    rho = (r^2 - (x_n - c_n)^2)^(1/2) grows with speed r / rho along its rim."""
+    g = o.g
+    assert g.dim == 3 and not g.inside
+    h, N = g.h, g.N
+    c = g.centers[body]
+    r = g.radii[body]
+    mons = o.store_mons
+    K = len(mons)
+    deg = max(sum(m) for m in mons)
+    big, bidx = _mono_index(3, deg + 2)
+    mine = np.nonzero(g.cut_body == body)[0]
+    cells = g.cut_cells[mine].astype(np.int64)
+    terms = g._terms_mono(3, deg + 2)
+    M = g.eb_integrals(cells, g.cut_body[mine], g._basis_pow(deg + 2), terms, ncomp=-1)  # int xi^t dA / h^2
+    n_cut = len(g.cut_cells)
+    deb = np.zeros((n_cut, K))
+    debn = np.zeros((n_cut, 3, K))
+    for row, k in enumerate(mine):
+        cc = int(g.cut_cells[k])
+        ijk = [cc % N, (cc // N) % N, cc // (N * N)]
+        xc = (np.array(ijk) + 0.5) * h
+        a = xc - c  # x - c = h xi + a
+        Mk = M[row]
+
+        def mom(t):
+            return Mk[bidx[tuple(t)]]
+
+        def ee_mom(q, kk, d):  # int xi^q e_kk e_d dA / h^2, e = (h xi + a) / r
+            t = list(q)
+            out = a[kk] * a[d] * mom(t)
+            t1 = list(q); t1[kk] += 1
+            out += h * a[d] * mom(t1)
+            t2 = list(q); t2[d] += 1
+            out += h * a[kk] * mom(t2)
+            t3 = list(q); t3[kk] += 1; t3[d] += 1
+            out += h * h * mom(t3)
+            return out / (r * r)
+
+        def e_mom(q, kk):  # int xi^q e_kk dA / h^2
+            t1 = list(q); t1[kk] += 1
+            return (a[kk] * mom(q) + h * mom(t1)) / r
+
+        for m, p in enumerate(mons):
+            # d(xi^p)/d rho = sum_kk (p_kk / h) xi^(p - e_kk) e_kk
+            v = 2.0 / r * mom(p)
+            for kk in range(3):
+                if p[kk] > 0:
+                    q = list(p); q[kk] -= 1
+                    v += p[kk] / h * e_mom(q, kk)
+            deb[k, m] += v
+            for d in range(3):  # f = xi^p n_d = -xi^p e_d
+                t1 = list(p); t1[d] += 1
+                v = -2.0 / r * e_mom(p, d)
+                for kk in range(3):
+                    if p[kk] > 0:
+                        q = list(p); q[kk] -= 1
+                        v -= p[kk] / h * ee_mom(q, kk, d)
+                debn[k, d, m] += v
+        # edges: the sphere's circles on the six faces of the cell, inside each face
+        lo, hi = np.array(ijk) * h, (np.array(ijk) + 1) * h
+        for ax in range(3):
+            oth = [b for b in range(3) if b != ax]
+            for side, pa in ((-1.0, lo[ax]), (1.0, hi[ax])):
+                q2 = r * r - (pa - c[ax]) ** 2
+                if q2 <= 0:
+                    continue
+                rho = math.sqrt(q2)
+                for (ta, _), (tb, _) in _arcs(c[oth[0]], c[oth[1]], rho, lo[oth[0]], hi[oth[0]], lo[oth[1]], hi[oth[1]]):
+                    t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+                    wq = 0.5 * (tb - ta) * _GL_W * rho  # dl
+                    x = np.zeros((3, len(t)))
+                    x[ax] = pa
+                    x[oth[0]] = c[oth[0]] + rho * np.cos(t)
+                    x[oth[1]] = c[oth[1]] + rho * np.sin(t)
+                    e = (x - c[:, None]) / r
+                    en = side * e[ax]  # e . n_p
+                    V = -en / np.sqrt(1.0 - en * en)
+                    xi = (x - xc[:, None]) / h
+                    for m, p in enumerate(mons):
+                        f = xi[0] ** p[0] * xi[1] ** p[1] * xi[2] ** p[2]
+                        deb[k, m] += np.sum(wq * f * V) / h ** 2
+                        for d in range(3):
+                            debn[k, d, m] += np.sum(wq * f * (-e[d]) * V) / h ** 2
+    dvol = np.zeros((n_cut, K))
+    dvol[mine] = -g.eb_mom[mine] / h
+    dface = []
+    from eb_inputs.geometry import monomials
+    for d in range(3):
+        cf = g.cut_faces[d]
+        tm = monomials(2, deg)[:g.face_mom[d].shape[1]]  # the face tables' tangential monomials
+        oth = [b for b in range(3) if b != d]
+        out = np.zeros((len(cf), len(tm)))
+        for k, f in enumerate(cf):
+            if g.cut_face_body[d][k] != body:
+                continue
+            ijk = o.face_coords(d, int(f))
+            pa = ijk[d] * h
+            q2 = r * r - (pa - c[d]) ** 2
+            if q2 <= 0:
+                continue
+            rho = math.sqrt(q2)
+            lo = [ijk[b] * h for b in oth]
+            hi = [(ijk[b] + 1) * h for b in oth]
+            fc = [(ijk[b] + 0.5) * h for b in oth]
+            for (ta, _), (tb, _) in _arcs(c[oth[0]], c[oth[1]], rho, lo[0], hi[0], lo[1], hi[1]):
+                t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+                wq = 0.5 * (tb - ta) * _GL_W * rho
+                u = (c[oth[0]] + rho * np.cos(t) - fc[0]) / h
+                v = (c[oth[1]] + rho * np.sin(t) - fc[1]) / h
+                for m, (pu, pv) in enumerate(tm):
+                    out[k, m] -= np.sum(wq * u ** pu * v ** pv) * (r / rho) / h ** 2
+        dface.append(out)
+    return dvol, deb, debn, dface
+
+
+def moment_derivatives(o: Oracle, body: int):
+    return circle_moment_derivatives(o, body) if o.g.dim == 2 else sphere_moment_derivatives(o, body)
+
+
 def _perturbed(o: Oracle, dm, eps):
     """The oracle's geometry arrays moved to m + i eps dm (complex step)."""
     g = o.g
@@ -179,7 +312,7 @@ def objective_and_radius_gradient(g, body: int = 0, params: Params | None = None
     J = 0.5 * float(np.sum(w * phi * phi))
     lam = np.zeros(g.ncell)
     lam[idx] = spla.spsolve(A.T.tocsc(), (w * phi)[idx])
-    dm = circle_moment_derivatives(o, body)
+    dm = moment_derivatives(o, body)
     dkap = np.zeros(g.ncell)
     dkap[g.cut_cells] = dm[0][:, 0]
     dJ = float(np.sum((0.5 * h ** D * phi * phi + lam) * dkap))

@@ -41,3 +41,22 @@ def test_radius_gradient_adjoint_against_central_differences():
     fd = (objective_and_radius_gradient(gp)[0] - objective_and_radius_gradient(gm)[0]) / (2 * EPS)
     assert J > 0
     assert abs(dJ - fd) <= 1e-6 * abs(fd)
+
+
+def test_sphere_moment_shape_derivatives():
+    """3-D: the sphere patch's derivative (mean curvature 2/r, the normal derivative from the
+    generator's higher-degree patch moments, and the patch edges sliding on the cell faces with the
+    conormal speed), the transport-theorem volume derivatives and the face disks' rims, against
+    central differences of the generator's moments."""
+    from oracle.eb_adjoint import sphere_moment_derivatives
+    mk = lambda r: E.Geometry(3, 8, np.array([[0.503, 0.497, 0.501]]), np.array([r]), False, 4)
+    g, gp, gm = mk(0.3), mk(0.3 + EPS), mk(0.3 - EPS)
+    assert np.array_equal(gp.cut_cells, g.cut_cells) and np.array_equal(gm.cut_cells, g.cut_cells)
+    dvol, deb, debn, dface = sphere_moment_derivatives(Oracle(g, Params(order=4)), 0)
+    pairs = [(dvol, gp.vol_mom, gm.vol_mom), (deb, gp.eb_mom, gm.eb_mom), (debn, gp.eb_nmom, gm.eb_nmom)]
+    for d in range(3):
+        assert np.array_equal(gp.cut_faces[d], g.cut_faces[d]) and np.array_equal(gm.cut_faces[d], g.cut_faces[d])
+        pairs.append((dface[d], gp.face_mom[d], gm.face_mom[d]))
+    for an, a, b in pairs:
+        fd = (a - b) / (2 * EPS)
+        assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
