@@ -60,3 +60,16 @@ def test_sphere_moment_shape_derivatives():
     for an, a, b in pairs:
         fd = (a - b) / (2 * EPS)
         assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
+def test_radius_gradient_two_circles():
+    """Two circles: the derivative with respect to the second circle's radius moves only the cells and
+    faces that circle cuts (the first circle's tables are held), against central differences."""
+    from oracle.eb_adjoint import objective_and_radius_gradient as grad
+    cen = np.array([[0.31, 0.29, 0.0], [0.69, 0.66, 0.0]])
+    mk = lambda r2: E.Geometry(2, 20, cen, np.array([0.13, r2]), False, 4)
+    g, gp, gm = mk(0.17), mk(0.17 + EPS), mk(0.17 - EPS)
+    assert np.array_equal(gp.cut_cells, g.cut_cells) and np.array_equal(gm.cut_cells, g.cut_cells)
+    J, dJ = grad(g, body=1)
+    fd = (grad(gp, body=1)[0] - grad(gm, body=1)[0]) / (2 * EPS)
+    assert abs(dJ - fd) <= 1e-6 * abs(fd)
