@@ -669,8 +669,16 @@ eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb
       }
     };
     std::vector<std::thread> th;
-    for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
+    std::vector<int> inline_t;  // workers whose thread could not be started run on this thread
+    for (int t = 1; t < nthr; ++t) {
+      try {
+        th.emplace_back(work, t);
+      } catch (...) {
+        inline_t.push_back(t);
+      }
+    }
     work(0);
+    for (int t : inline_t) work(t);
     for (auto& x : th) x.join();
     for (int32_t i = 0; i < n_geom; ++i)
       if (cs[i]->rc != EB_OK) {
@@ -678,7 +686,11 @@ eb_status eb_build_stencils_batch(const eb_geom* geoms, int32_t n_geom, const eb
         g_bad_faces = cs[i]->bad;
         return cs[i]->rc;
       }
-    return failed ? EB_ERR_CUDA : EB_OK;
+    if (failed) {
+      set_error("a batch worker thread could not select the device");
+      return EB_ERR_CUDA;
+    }
+    return EB_OK;
   };
   cudaError_t e = fork();
   if (e != cudaSuccess) return cleanup(cuda_status(e, "batch fork"));
