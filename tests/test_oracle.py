@@ -39,7 +39,8 @@ def test_minimum_weighted_norm_conditions(Q):
     o = Oracle(g, Params(order=Q))
     faces = o.flux_faces()
     rng = np.random.default_rng(0)
-    sample = list(rng.choice(faces[:-len(g.cut_cells)], 40, replace=False)) + faces[-len(g.cut_cells):][:40]
+    ncut = len(g.cut_cells)
+    sample = list(rng.choice(faces[:-ncut], 1000 - ncut, replace=False)) + faces[-ncut:]  # 1000 faces
     for f in sample:
         A, F, w, cols = o.face_system(int(f))
         _, s = o.stencil(int(f))
