@@ -79,6 +79,11 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 FMA issue: 128 FFMA per clock per SM, 2 flops each."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
@@ -305,6 +310,10 @@ def main():
     nfoot = 637 if args.order == 4 else 275
     alg_bytes = 2 * g.ncell * 4 + (bi["n_irregular_rows"] + bi["n_row_classes"]) * nfoot * 4
     apply_gbs = alg_bytes / (apply_ms / 1e3) / 1e9
+    # algorithmic FP32 flops of one apply: one FMA per footprint entry per volume (no folding counted)
+    apply_flops = 2.0 * nfoot * int((g.flag > 0).sum())
+    apply_tflops = apply_flops / (apply_ms / 1e3) / 1e12
+    fp32_pk = fp32_peak_tflops(sm_max)
     fp64_pk = fp64_peak_tflops(sm_max)
     lsq_tflops = bi["lsq_flops"] / (lsq_ms / 1e3) / 1e12
     apply_share = np.mean([i[1]["apply_ms"] for i in infos]) / ms_step
@@ -337,7 +346,9 @@ def main():
                        "n_eb_face_systems": int(len(g.cut_cells)),
                        "lsq_tflops": lsq_tflops, "lsq_frac_fp64_peak": lsq_tflops / fp64_pk,
                        "apply_fp32_ms": apply_ms, "apply_gbs": apply_gbs, "apply_frac_hbm": apply_gbs / hbm_peak,
-                       "apply_alg_bytes": alg_bytes, "solve_ms": ms_step - build_ms,
+                       "apply_alg_bytes": alg_bytes, "apply_fp32_tflops": apply_tflops,
+                       "apply_frac_fp32_peak": apply_tflops / fp32_pk,
+                       "apply_fp32_flops_per_volume": 2 * nfoot, "solve_ms": ms_step - build_ms,
                        "solve_iterations": sinfo["iterations"], "solve_sweeps": sinfo["sweeps"],
                        "rel_residual": sinfo["rel_residual"], "error_linf": infos[-1][2]["linf"],
                        "e_star_linf": e_star, "solve_tol": tol, "solve_s_at_fixed_error": (ms_step - build_ms) / 1e3,
