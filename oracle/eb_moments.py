@@ -126,3 +126,137 @@ def circle_moments(N, centers, radii, qmax=4):
                 idx = (a + (N + 1) * bidx) if d == 0 else (bidx + N * a)
                 faces[d][idx] = mom
     return cells, faces
+
+
+# --------------------------------------------------------------------- 3-D: the cube minus spheres
+
+_S_X, _S_W = np.polynomial.legendre.leggauss(48)
+
+
+def _sin2_panels(breaks):
+    """Nodes and weights on the panels [b_i, b_(i+1)] with t = a + (b - a) sin^2(pi s / 2), s in [0, 1]
+    (48-point Gauss-Legendre in s): the substitution flattens the square-root behaviour of chord and
+    arc ends at tangencies, which the panel breaks put at panel ends."""
+    xs, ws = [], []
+    s = 0.5 * _S_X + 0.5
+    wg = 0.5 * _S_W
+    sn, cs = np.sin(0.5 * math.pi * s), np.cos(0.5 * math.pi * s)
+    for a, b in zip(breaks[:-1], breaks[1:]):
+        if b <= a:
+            continue
+        xs.append(a + (b - a) * sn * sn)
+        ws.append(wg * (b - a) * math.pi * sn * cs)
+    if not xs:
+        return np.zeros(0), np.zeros(0)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def _mons3(q):
+    from eb_inputs.geometry import monomials
+    return monomials(3, q)
+
+
+def _disk_rect_moments(cu, cv, rho, u0, u1, v0, v1, uc, vc, h, qmax):
+    """int over [u0,u1]x[v0,v1] minus the open disk of radius rho about (cu, cv) of eta^a zeta^b
+    d eta d zeta, eta = (u - uc)/h, zeta = (v - vc)/h, for the graded exponents (a, b), a + b <= qmax."""
+    mons = _mons2(qmax)
+    su = _segment_moments((u0 - uc) / h, (u1 - uc) / h, qmax)
+    sv = _segment_moments((v0 - vc) / h, (v1 - vc) / h, qmax)
+    rect = np.array([su[a] * sv[b] for a, b in mons])
+    lo, hi = max(u0, cu - rho), min(u1, cu + rho)
+    if rho <= 0 or hi <= lo:
+        return rect
+    br = [lo, hi]  # chord ends crossing v0 or v1 put kinks in the u integrand
+    for ve in (v0, v1):
+        dv = ve - cv
+        if abs(dv) < rho:
+            w = math.sqrt(rho * rho - dv * dv)
+            for uu in (cu - w, cu + w):
+                if lo < uu < hi:
+                    br.append(uu)
+    u, wu = _sin2_panels(sorted(br))
+    half = np.sqrt(np.maximum(rho * rho - (u - cu) ** 2, 0.0))
+    za = (np.clip(cv - half, v0, v1) - vc) / h
+    zb = (np.clip(cv + half, v0, v1) - vc) / h
+    eta = (u - uc) / h
+    disk = np.array([np.sum(wu * eta ** a * (zb ** (b + 1) - za ** (b + 1)) / (b + 1)) / h for a, b in mons])
+    return rect - disk
+
+
+def sphere_moments(N, centers, radii, cells, qmax=4):
+    """Volume and EB moment tables of the unit cube minus spheres for the listed cut cells (each cut
+    by one sphere): dict cell -> {'vol' [K], 'eb' [K], 'ebn' [3, K]}, scaled like the input tables.
+
+    EB patch: the sphere's area element in (z, phi) is r dz dphi (Archimedes), and at each z the
+    patch is the arcs of the circle of radius (r^2 - (z - c_z)^2)^(1/2) inside the cell's x-y
+    rectangle (the whole circle when it lies inside); the z integral is split where the arcs change
+    (tangencies with the rectangle's edge lines and corners) and mapped by the sin^2 substitution.
+    Volume moments by the divergence theorem: int_V xi^p dV = h/(p_x+1) oint xi^(p+e_x) n_x dA over
+    the cell's two x faces (their fluid parts: square minus disk) and the patch (n_x = -e_x)."""
+    h = 1.0 / N
+    mons = _mons3(qmax)
+    K = len(mons)
+    fidx = {mm: n for n, mm in enumerate(_mons2(qmax + 1))}
+    out = {}
+    for cell in cells:
+        cell = int(cell)
+        ijk = np.array([cell % N, (cell // N) % N, cell // (N * N)], float)
+        lo, hi = ijk * h, (ijk + 1) * h
+        xc = lo + 0.5 * h
+        b = None
+        for bb, (cc, rr) in enumerate(zip(centers, radii)):
+            cc = np.asarray(cc, float)
+            near = np.linalg.norm(np.clip(cc, lo, hi) - cc)
+            far = max(np.linalg.norm(np.array([x, y, z]) - cc) for x in (lo[0], hi[0]) for y in (lo[1], hi[1])
+                      for z in (lo[2], hi[2]))
+            if near < rr < far:
+                b = bb
+        if b is None:
+            continue
+        c, r = np.asarray(centers[b], float), float(radii[b])
+        z_lo, z_hi = max(lo[2], c[2] - r), min(hi[2], c[2] + r)
+        br = [z_lo, z_hi]
+        d2 = [(lo[0] - c[0]) ** 2, (hi[0] - c[0]) ** 2, (lo[1] - c[1]) ** 2, (hi[1] - c[1]) ** 2]
+        d2 += [(x - c[0]) ** 2 + (y - c[1]) ** 2 for x in (lo[0], hi[0]) for y in (lo[1], hi[1])]
+        for dd in d2:
+            q = r * r - dd
+            if q > 0:
+                for zz in (c[2] - math.sqrt(q), c[2] + math.sqrt(q)):
+                    if z_lo < zz < z_hi:
+                        br.append(zz)
+        zs, wz = _sin2_panels(sorted(br))
+        eb = np.zeros(K)
+        ebn = np.zeros((3, K))
+        vol = np.zeros(K)
+        for z, wzz in zip(zs, wz):
+            rho2 = r * r - (z - c[2]) ** 2
+            if rho2 <= 0:
+                continue
+            rho = math.sqrt(rho2)
+            arcs = [(ta, tb) for (ta, _), (tb, _) in _arcs(c[0], c[1], rho, lo[0], hi[0], lo[1], hi[1])]
+            if not arcs and lo[0] < c[0] - rho and c[0] + rho < hi[0] and lo[1] < c[1] - rho and c[1] + rho < hi[1]:
+                arcs = [(0.0, 2 * math.pi)]
+            for ta, tb in arcs:
+                t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+                wt = wzz * r * 0.5 * (tb - ta) * _GL_W  # dA = r dz dphi
+                x, y = c[0] + rho * np.cos(t), c[1] + rho * np.sin(t)
+                ex, ey, ez = (x - c[0]) / r, (y - c[1]) / r, (z - c[2]) / r
+                xi, et, ze = (x - xc[0]) / h, (y - xc[1]) / h, (z - xc[2]) / h
+                for m, p in enumerate(mons):
+                    f = xi ** p[0] * et ** p[1] * ze ** p[2]
+                    eb[m] += np.sum(wt * f)
+                    ebn[0, m] -= np.sum(wt * f * ex)
+                    ebn[1, m] -= np.sum(wt * f * ey)
+                    ebn[2, m] -= np.sum(wt * f * ez)
+                    vol[m] -= np.sum(wt * xi ** (p[0] + 1) * et ** p[1] * ze ** p[2] * ex) / (p[0] + 1)
+        eb /= h * h
+        ebn /= h * h
+        vol /= h * h  # vol_mom = int_V xi^p dV / h^3 = (1 / (h^2 (p_x+1))) oint xi^(p+e_x) n_x dA
+        for xe, sgn in ((lo[0], -1.0), (hi[0], 1.0)):
+            q2 = r * r - (xe - c[0]) ** 2
+            rho = math.sqrt(q2) if q2 > 0 else 0.0
+            fm = _disk_rect_moments(c[1], c[2], rho, lo[1], hi[1], lo[2], hi[2], xc[1], xc[2], h, qmax + 1)
+            for m, p in enumerate(mons):  # dA = h^2 d eta d zeta on the face
+                vol[m] += sgn * (sgn * 0.5) ** (p[0] + 1) * fm[fidx[(p[1], p[2])]] / (p[0] + 1)
+        out[cell] = {"vol": vol, "eb": eb, "ebn": ebn}
+    return out

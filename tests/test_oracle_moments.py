@@ -34,3 +34,25 @@ def test_circle_moments_two_routes(N, cen, rad):
     assert abs(area - (1 - sum(math.pi * r * r for r in rad))) <= 1e-13
     length = sum(m["eb"][0] for m in cells.values()) * h
     assert abs(length - sum(2 * math.pi * r for r in rad)) <= 1e-13
+
+
+def test_sphere_moments_two_routes():
+    """3-D, the cube minus a sphere at N = 8: the (z, phi) patch quadrature and the divergence-theorem
+    volume moments against the generator (1e-10; the pole cells are the hardest), and the closed-form
+    fluid volume and sphere area."""
+    from oracle.eb_moments import sphere_moments
+    N, cen, r = 8, (0.503, 0.497, 0.501), 0.3
+    g = E.Geometry(3, N, np.array([cen]), np.array([r]), False, 4)
+    mm = sphere_moments(N, [np.array(cen)], [r], g.cut_cells, 4)
+    assert sorted(mm) == sorted(int(c) for c in g.cut_cells)
+    for k, c in enumerate(g.cut_cells):
+        m = mm[int(c)]
+        assert np.abs(m["vol"] - g.vol_mom[k]).max() <= 1e-10
+        assert np.abs(m["eb"] - g.eb_mom[k]).max() <= 1e-10
+        assert np.abs(m["ebn"] - g.eb_nmom[k]).max() <= 1e-10
+    h = 1.0 / N
+    n_full = int((g.flag == 1).sum())
+    vol = n_full * h ** 3 + sum(m["vol"][0] for m in mm.values()) * h ** 3
+    assert abs(vol - (1 - 4.0 / 3.0 * math.pi * r ** 3)) <= 1e-12
+    area = sum(m["eb"][0] for m in mm.values()) * h * h
+    assert abs(area - 4 * math.pi * r * r) <= 1e-10
