@@ -260,3 +260,29 @@ def sphere_moments(N, centers, radii, cells, qmax=4):
                 vol[m] += sgn * (sgn * 0.5) ** (p[0] + 1) * fm[fidx[(p[1], p[2])]] / (p[0] + 1)
         out[cell] = {"vol": vol, "eb": eb, "ebn": ebn}
     return out
+
+
+def sphere_face_moments(N, centers, radii, d, faces, qmax=4):
+    """Tangential moments of the fluid parts of the listed faces normal to d (3-D, the cube minus
+    spheres): the face square minus the disks the spheres cut from its plane, about the face centre,
+    in the graded order of the two tangential coordinates (ascending dimensions)."""
+    h = 1.0 / N
+    oth = [b for b in range(3) if b != d]
+    shape = [N + (k == d) for k in range(3)]
+    out = {}
+    for f in faces:
+        f = int(f)
+        ijk = [f % shape[0], (f // shape[0]) % shape[1], f // (shape[0] * shape[1])]
+        pa = ijk[d] * h
+        lo = [ijk[b] * h for b in oth]
+        hi = [(ijk[b] + 1) * h for b in oth]
+        fc = [(ijk[b] + 0.5) * h for b in oth]
+        mom = None
+        for c, r in zip(centers, radii):
+            q2 = r * r - (pa - c[d]) ** 2
+            rho = math.sqrt(q2) if q2 > 0 else 0.0
+            m = _disk_rect_moments(c[oth[0]], c[oth[1]], rho, lo[0], hi[0], lo[1], hi[1], fc[0], fc[1], h, qmax)
+            full = _disk_rect_moments(0.0, 0.0, 0.0, lo[0], hi[0], lo[1], hi[1], fc[0], fc[1], h, qmax)
+            mom = m if mom is None else mom - (full - m)  # disks of different spheres do not overlap
+        out[f] = mom
+    return out

@@ -56,3 +56,13 @@ def test_sphere_moments_two_routes():
     assert abs(vol - (1 - 4.0 / 3.0 * math.pi * r ** 3)) <= 1e-12
     area = sum(m["eb"][0] for m in mm.values()) * h * h
     assert abs(area - 4 * math.pi * r * r) <= 1e-10
+
+
+def test_sphere_face_moments_two_routes():
+    from oracle.eb_moments import sphere_face_moments
+    N, cen, r = 8, (0.503, 0.497, 0.501), 0.3
+    g = E.Geometry(3, N, np.array([cen]), np.array([r]), False, 4)
+    for d in range(3):
+        fm = sphere_face_moments(N, [np.array(cen)], [r], d, g.cut_faces[d], 4)
+        for k, f in enumerate(g.cut_faces[d]):
+            assert np.abs(fm[int(f)] - g.face_mom[d][k]).max() <= 1e-11, (d, f)
