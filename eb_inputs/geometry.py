@@ -379,6 +379,30 @@ def multi_circle_config(N: int, seed: int = 1, qmax: int = 4) -> Geometry:
     return Geometry(2, N, c, np.array(radii), False, qmax, name=f"multi-circle-{N}", seed=seed)
 
 
+def multi_sphere_config(N: int, n: int = 8, seed: int = 4, rmin: float = 0.08, rmax: float = 0.2,
+                        qmax: int = 4) -> Geometry:
+    """The unit cube minus n seeded non-overlapping spheres: each draws (r, cx, cy, cz) from
+    SplitMix64(seed), r ~ U[rmin, rmax), and is accepted when its surface keeps a clearance of at
+    least 2h from every accepted sphere and from the box (no cell is cut by two spheres)."""
+    h = 1.0 / N
+    gap = 2.0 * h
+    centers, radii = [], []
+    stream = uniform(seed, 4 * 200000)
+    k = 0
+    while len(radii) < n:
+        if k + 4 > len(stream):
+            raise RuntimeError("could not place the spheres with the requested clearance")
+        r = rmin + (rmax - rmin) * stream[k]
+        c = stream[k + 1:k + 4]
+        k += 4
+        if np.any(c - r < gap) or np.any(c + r > 1.0 - gap):
+            continue
+        if all(np.linalg.norm(c - cc) - r - rr >= gap for cc, rr in zip(centers, radii)):
+            centers.append(np.array(c))
+            radii.append(r)
+    return Geometry(3, N, np.array(centers), np.array(radii), False, qmax, name=f"multi-sphere-{N}", seed=seed)
+
+
 def sphere_box_config(N: int, seed: int = 2, r: float = 0.35, qmax: int = 4) -> Geometry:
     """Unit cube minus a sphere of radius r centred at 0.5 + delta, delta_i ~ U[-h/2, h/2) from seed."""
     h = 1.0 / N

@@ -140,3 +140,20 @@ def test_manufactured_full_cell_average():
     ex = (-(math.cos(2 * math.pi * x1) - math.cos(2 * math.pi * x0)) / (2 * math.pi * h)) * \
          ((math.sin(3 * math.pi * x1) - math.sin(3 * math.pi * x0)) / (3 * math.pi * h))
     assert abs(avg[c] - ex) < 1e-15
+
+
+def test_multi_sphere_clearance_and_volume():
+    """Eight seeded spheres, radii in [0.08, 0.2): pairwise and wall clearance >= 2h, no cell cut by two
+    spheres (the generator would refuse), and the fluid volume 1 - sum 4/3 pi r^3 to 1e-12."""
+    import math
+    N = 24
+    g = E.multi_sphere_config(N)
+    h = 1.0 / N
+    c, r = g.centers, g.radii
+    assert len(r) == 8 and np.all((r >= 0.08) & (r < 0.2))
+    assert np.all(c - r[:, None] >= 2 * h - 1e-15) and np.all(c + r[:, None] <= 1 - 2 * h + 1e-15)
+    for i in range(8):
+        for j in range(i):
+            assert np.linalg.norm(c[i] - c[j]) - r[i] - r[j] >= 2 * h - 1e-15
+    vol = (g.flag == 1).sum() * h ** 3 + g.vol_mom[:, 0].sum() * h ** 3
+    assert abs(vol - (1 - sum(4 / 3 * math.pi * x ** 3 for x in r))) <= 1e-12
