@@ -73,3 +73,30 @@ def test_radius_gradient_two_circles():
     J, dJ = grad(g, body=1)
     fd = (grad(gp, body=1)[0] - grad(gm, body=1)[0]) / (2 * EPS)
     assert abs(dJ - fd) <= 1e-6 * abs(fd)
+
+
+def test_sphere_moment_derivatives_eight_spheres():
+    """The eight-sphere geometry: the derivative with respect to one sphere's radius moves only the
+    cells and faces that sphere cuts, against central differences of the generator."""
+    from oracle.eb_adjoint import sphere_moment_derivatives
+    g = E.multi_sphere_config(24)
+    for b in range(len(g.radii)):  # the first sphere whose cut cells and faces survive +-EPS
+        rp, rm = g.radii.copy(), g.radii.copy()
+        rp[b] += EPS
+        rm[b] -= EPS
+        gp = E.Geometry(3, 24, g.centers, rp, False, 4)
+        gm = E.Geometry(3, 24, g.centers, rm, False, 4)
+        if all(np.array_equal(x.cut_cells, g.cut_cells) for x in (gp, gm)) and all(
+                np.array_equal(x.cut_faces[d], g.cut_faces[d]) for x in (gp, gm) for d in range(3)):
+            break
+    else:
+        pytest.fail("every sphere changes the cut sets under +-EPS")
+    dvol, deb, debn, dface = sphere_moment_derivatives(Oracle(g, Params(order=4)), b)
+    pairs = [(dvol, gp.vol_mom, gm.vol_mom), (deb, gp.eb_mom, gm.eb_mom), (debn, gp.eb_nmom, gm.eb_nmom)]
+    for d in range(3):
+        assert np.array_equal(gp.cut_faces[d], g.cut_faces[d]) and np.array_equal(gm.cut_faces[d], g.cut_faces[d])
+        pairs.append((dface[d], gp.face_mom[d], gm.face_mom[d]))
+    for an, a, bb in pairs:
+        fd = (a - bb) / (2 * EPS)
+        assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+    assert np.all(deb[g.cut_body != b] == 0) and np.any(deb[g.cut_body == b] != 0)
