@@ -21,6 +21,10 @@
  *     stream).  eb_build_stencils and eb_solve synchronise that stream to
  *     read back small scalars (counts, status, residual norms); eb_apply and
  *     eb_bc_rhs do not synchronise.
+ *   - Device memory of builds and solves comes from a library-owned,
+ *     stream-ordered memory pool per device that keeps freed memory cached
+ *     (small arrays share chunks of it); eb_stencils_destroy synchronises the
+ *     device before returning the stencils' memory to the pool.
  *   - Errors are returned as eb_status; nothing is thrown across the ABI.
  *     eb_last_error_message() gives a human-readable reason for the last
  *     failure on the calling thread.
