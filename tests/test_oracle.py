@@ -273,6 +273,26 @@ def test_paper_circle_table_n64(Q):
     _check_table(r, GOLD["circle_r025"][f"q{Q}"], 1, ["trunc_linf", "trunc_l1", "sol_linf", "sol_l1"])
 
 
+def _four_circles(N):
+    g = E.four_circles_config(N)
+    man = E.Manufactured(g, E.sin_product("paper2d"))
+    return run_problem(g, man, Params(order=4))
+
+
+def test_paper_four_circles_table_n64():
+    """Sec. 3.5.2 table (outside four circles of radius 0.215 centred at (0.25|0.75, 0.25|0.75),
+    Dirichlet, fourth order), N = 64: truncation and solution errors to the printed digits."""
+    tab = GOLD["four_circles"]
+    r = _four_circles(64)
+    _check_table(r, tab, 0, ["trunc_linf", "trunc_l1", "sol_linf", "sol_l1"])
+
+
+@pytest.mark.slow
+def test_paper_four_circles_table_n128():
+    r = _four_circles(128)
+    _check_table(r, GOLD["four_circles"], 1, ["trunc_linf", "trunc_l1", "sol_linf", "sol_l1"])
+
+
 def _neumann_circle(N, weight="physical"):
     g = E.circle_config(N)
     man = E.Manufactured(g, E.sin_product("paper2d"))
