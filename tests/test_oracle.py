@@ -293,6 +293,19 @@ def test_paper_four_circles_table_n128():
     _check_table(r, GOLD["four_circles"], 1, ["trunc_linf", "trunc_l1", "sol_linf", "sol_l1"])
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_paper_perturbation_tables_n32(bc):
+    """Sec. 3.5.1 tables (three perturbed circles; Dirichlet or Neumann on the circle, Dirichlet on
+    the square), N = 32: truncation and solution errors to the printed digits."""
+    tab = GOLD["perturbations_n32"]
+    for k, geo in enumerate(tab["geometries"]):
+        g = E.circle_config(32, center=tuple(geo["center"]), r=geo["r"])
+        man = E.Manufactured(g, E.sin_product("paper2d"))
+        bc_eb = np.ones(len(g.cut_cells), np.int8) if bc == "neumann" else None
+        r = run_problem(g, man, Params(order=4), bc_eb=bc_eb)
+        _check_table(r, tab[bc], k, ["trunc_linf", "trunc_l1", "sol_linf", "sol_l1"])
+
+
 def _neumann_circle(N, weight="physical"):
     g = E.circle_config(N)
     man = E.Manufactured(g, E.sin_product("paper2d"))
