@@ -374,6 +374,28 @@ def test_sphere_spectrum_stable_and_first_eigenvalue():
     assert abs(lam.real - exact) <= 1e-3 * abs(exact) and abs(lam.imag) < 1e-6
 
 
+@pytest.mark.slow
+def test_spectra_table_lambda_max():
+    """Spectra summary table of Sec. 3.5 at 64^2: the eigenvalue with the largest real part of the
+    (not kappa-weighted) operator, to the printed digits, for a perturbed circle (Dirichlet), the
+    circle with Neumann data on the EB and the four circles."""
+    pr = GOLD["spectrum_64"]["lambda_max_printed"]
+
+    def lam(g, bc=None):
+        o = Oracle(g, Params(order=4), bc_eb=bc)
+        L, _ = o.operator()
+        idx = np.nonzero(g.flag > 0)[0]
+        vals = spla.eigs(L[idx][:, idx].tocsc(), k=3, sigma=0.0, return_eigenvectors=False)
+        v = vals[np.argmax(vals.real)]
+        assert abs(v.imag) < 1e-6
+        return v.real
+
+    assert round(lam(E.circle_config(64, r=0.255))) == pr["circle_r0255_dirichlet"]
+    g = E.circle_config(64)
+    assert round(lam(g, np.ones(len(g.cut_cells), np.int8))) == pr["circle_r025_neumann"]
+    assert round(lam(E.four_circles_config(64)), -1) == pr["four_circles_dirichlet"]
+
+
 def test_unweighted_control_is_unstable():
     """Without weights (W = I) the operator has eigenvalues with positive real part (Sec. 2.2.1 and
     Sec. 3.4); with weights every eigenvalue has negative real part."""
