@@ -462,3 +462,17 @@ def test_stencil_adjoint_against_central_differences():
             Fm[k] -= eps
             fd = (c @ forward(A, Fp, w) - c @ forward(A, Fm, w)) / (2 * eps)
             assert abs(fd - Fbar[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, Fbar[k])
+
+
+def test_rank_deficient_systems_are_reported():
+    """Degenerate case: with path neighbourhoods of radius 1 a fourth-order face sees fewer volumes
+    than the 15 monomials, so every system is rank-deficient and the oracle refuses it instead of
+    returning a least-squares answer (no fallback, Sec. 2.4 uses one R_n everywhere)."""
+    from oracle.eb_oracle import RankDeficient
+    g = E.circle_config(16, center=(0.51, 0.49), r=0.3)
+    o = Oracle(g, Params(order=4, path_radius=1, metric="path"))
+    for f in o.flux_faces()[::9]:
+        A, F, w, cols = o.face_system(f)
+        assert np.linalg.matrix_rank(w[:, None] * A) < A.shape[1]
+        with pytest.raises(RankDeficient):
+            o.stencil(f)
