@@ -148,6 +148,102 @@ def circle_moment_derivatives(o: Oracle, body: int):
     return dvol, deb, debn, dface
 
 
+def circle_velocity_derivatives(o: Oracle, body: int, V, gradV):
+    """Moment-table derivatives of o.g (2-D, fluid outside the circles) when circle `body`'s boundary
+    moves with the normal speed V(x) along N = (x - c)/r (out of the body), gradV(x) its gradient:
+    the general form of circle_moment_derivatives (V = 1) -- a centre translation t is V = N . t, a
+    level-set perturbation psi + a f(x) of the distance function is V = -f.  On the boundary
+        d/dt int_patch F ds = int (grad F . N V + kappa F V) ds + sum_ends F s_end,   kappa = 1/r,
+        d/dt N = -grad_G V (the surface gradient), so d/dt n = +grad_G V for n = -N,
+    an arc end on an edge line moves along the line with normal component V (its arc-length speed
+    is V times the radius-change speed r dt/dr), a chord end on a face with speed V r / s, and the
+    volume loses int_patch xi^p V ds.  V and gradV take arrays x[2, m] and return [m] and [2, m]."""
+    g = o.g
+    assert g.dim == 2 and not g.inside
+    h = g.h
+    c = g.centers[body, :2]
+    r = g.radii[body]
+    mons = o.store_mons
+    K = len(mons)
+    n_cut = len(g.cut_cells)
+    dvol = np.zeros((n_cut, K))
+    deb = np.zeros((n_cut, K))
+    debn = np.zeros((n_cut, 2, K))
+    for k, cc in enumerate(g.cut_cells):
+        if g.cut_body[k] != body:
+            continue
+        i, j = int(cc) % g.N, int(cc) // g.N
+        xcell = np.array([(i + 0.5) * h, (j + 0.5) * h])
+        for (ta, dta), (tb, dtb) in _arcs(c[0], c[1], r, i * h, (i + 1) * h, j * h, (j + 1) * h):
+            t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+            ds = 0.5 * (tb - ta) * _GL_W * r
+            N = np.stack([np.cos(t), np.sin(t)])
+            x = c[:, None] + r * N
+            xi = (x - xcell[:, None]) / h
+            v = V(x)
+            gv = gradV(x)
+            gG = gv - np.sum(gv * N, axis=0) * N  # surface gradient
+            ends = []
+            for tt, dt, sgn in ((ta, dta, -1.0), (tb, dtb, 1.0)):
+                Ne = np.array([math.cos(tt), math.sin(tt)])
+                xe = c + r * Ne
+                ends.append(((xe - xcell) / h, Ne, sgn * float(V(xe[:, None])[0]) * r * dt))
+            for m, p in enumerate(mons):
+                f = xi[0] ** p[0] * xi[1] ** p[1]
+                gN = np.zeros_like(t)  # grad_x(xi^p) . N
+                if p[0] > 0:
+                    gN += p[0] * xi[0] ** (p[0] - 1) * xi[1] ** p[1] * N[0] / h
+                if p[1] > 0:
+                    gN += p[1] * xi[0] ** p[0] * xi[1] ** (p[1] - 1) * N[1] / h
+                dvol[k, m] -= np.sum(ds * f * v) / h ** 2
+                deb[k, m] += (np.sum(ds * (gN * v + f * v / r)) + sum(
+                    xe[0] ** p[0] * xe[1] ** p[1] * se for xe, _, se in ends)) / h
+                for d in range(2):
+                    val = np.sum(ds * (gN * v * -N[d] + f * gG[d] + f * -N[d] * v / r))
+                    val += sum(xe[0] ** p[0] * xe[1] ** p[1] * -Ne[d] * se for xe, Ne, se in ends)
+                    debn[k, d, m] += val / h
+    dface = []
+    for d in range(2):
+        cf = g.cut_faces[d]
+        qn = g.face_mom[d].shape[1]
+        out = np.zeros((len(cf), qn))
+        for k, f in enumerate(cf):
+            if g.cut_face_body[d][k] != body:
+                continue
+            ijk = o.face_coords(d, int(f))
+            xn = ijk[d] * h
+            tdim = 1 - d
+            t0, t1 = ijk[tdim] * h, (ijk[tdim] + 1) * h
+            tcen = 0.5 * (t0 + t1)
+            q = r * r - (xn - c[d]) ** 2
+            if q <= 0:
+                continue
+            s_ = math.sqrt(q)
+            for end in (c[tdim] - s_, c[tdim] + s_):
+                if t0 < end < t1:
+                    xe = np.zeros(2)
+                    xe[d], xe[tdim] = xn, end
+                    speed = float(V(xe[:, None])[0]) * r / s_
+                    eta = (end - tcen) / h
+                    for m in range(qn):
+                        out[k, m] -= eta ** m * speed / h
+        dface.append(out)
+    return dvol, deb, debn, dface
+
+
+def fourier_mode_velocity(k, theta):
+    """Normal speed of the boundary of the distance-function level set psi + a f = 0 per unit a at
+    a = 0, for the mode f(x) = sin(2 pi k . x + theta) (|grad psi| = 1): V = -f, grad V = -grad f."""
+    k = np.asarray(k, float)
+
+    def V(x):
+        return -np.sin(2 * math.pi * (k[:, None] * x).sum(0) + theta)
+
+    def gradV(x):
+        return -2 * math.pi * k[:, None] * np.cos(2 * math.pi * (k[:, None] * x).sum(0) + theta)
+    return V, gradV
+
+
 def _mono_index(D, deg):
     from eb_inputs.geometry import monomials
     ms = monomials(D, deg)
@@ -296,8 +392,9 @@ def _restore(o: Oracle, saved):
     g.vol_mom, g.eb_mom, g.eb_nmom, g.face_mom = saved
 
 
-def objective_and_radius_gradient(g, body: int = 0, params: Params | None = None):
-    """(J, dJ/dr) for the radius of circle `body` (see the module docstring)."""
+def objective_and_radius_gradient(g, body: int = 0, params: Params | None = None, derivs=None):
+    """(J, dJ/dr) for the radius of circle `body` (see the module docstring); derivs(o) -> the moment
+    tables' derivatives for another geometry parameter (default: that radius)."""
     o = Oracle(g, params or Params(order=4))
     h, D = g.h, g.dim
     st = o.all_stencils()
@@ -312,7 +409,7 @@ def objective_and_radius_gradient(g, body: int = 0, params: Params | None = None
     J = 0.5 * float(np.sum(w * phi * phi))
     lam = np.zeros(g.ncell)
     lam[idx] = spla.spsolve(A.T.tocsc(), (w * phi)[idx])
-    dm = moment_derivatives(o, body)
+    dm = moment_derivatives(o, body) if derivs is None else derivs(o)
     dkap = np.zeros(g.ncell)
     dkap[g.cut_cells] = dm[0][:, 0]
     dJ = float(np.sum((0.5 * h ** D * phi * phi + lam) * dkap))

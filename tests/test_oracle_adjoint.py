@@ -100,3 +100,53 @@ def test_sphere_moment_derivatives_eight_spheres():
         fd = (a - bb) / (2 * EPS)
         assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
     assert np.all(deb[g.cut_body != b] == 0) and np.any(deb[g.cut_body == b] != 0)
+
+
+def _translation_velocity(c, r, t):
+    """Normal speed and gradient of a translation t of the body centred at c (radius r): V = N . t."""
+    def V(x):
+        return (((x - c[:, None]) / r) * t[:, None]).sum(0)
+
+    def gradV(x):
+        N = (x - c[:, None]) / r
+        return (t[:, None] - (N * t[:, None]).sum(0) * N) / r
+    return V, gradV
+
+
+def test_velocity_derivatives_2d():
+    """The general normal-velocity form of the moment derivatives: a uniform speed reproduces the
+    radius derivatives, and a centre translation (a non-uniform speed, which also turns the normals)
+    matches central differences of the generator's moments with the centre moved."""
+    from oracle.eb_adjoint import circle_moment_derivatives, circle_velocity_derivatives
+    N, c, r = 16, np.array([0.51, 0.49]), 0.3
+    g = E.circle_config(N, center=tuple(c), r=r)
+    o = Oracle(g, Params(order=4))
+    a = circle_velocity_derivatives(o, 0, lambda x: np.ones(x.shape[1]), lambda x: np.zeros_like(x))
+    b = circle_moment_derivatives(o, 0)
+    for x, y in list(zip(a[:3], b[:3])) + list(zip(a[3], b[3])):
+        assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(y).max())
+    t = np.array([1.0, 0.0])
+    V, gradV = _translation_velocity(c, r, t)
+    dm = circle_velocity_derivatives(o, 0, V, gradV)
+    gp = E.circle_config(N, center=tuple(c + EPS * t), r=r)
+    gm = E.circle_config(N, center=tuple(c - EPS * t), r=r)
+    assert np.array_equal(gp.cut_cells, g.cut_cells) and np.array_equal(gm.cut_cells, g.cut_cells)
+    pairs = [(dm[0], gp.vol_mom, gm.vol_mom), (dm[1], gp.eb_mom, gm.eb_mom), (dm[2], gp.eb_nmom, gm.eb_nmom)]
+    pairs += [(dm[3][d], gp.face_mom[d], gm.face_mom[d]) for d in range(2)]
+    for an, x, y in pairs:
+        fd = (x - y) / (2 * EPS)
+        assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
+def test_centre_gradient_adjoint_against_central_differences():
+    """dJ/dc_x through the solve and LS-build adjoints with the translation's moment derivatives,
+    against central differences of J with the circle moved."""
+    from oracle.eb_adjoint import circle_velocity_derivatives
+    N, c, r = 16, np.array([0.51, 0.49]), 0.3
+    t = np.array([1.0, 0.0])
+    V, gradV = _translation_velocity(c, r, t)
+    g = E.circle_config(N, center=tuple(c), r=r)
+    J, dJ = objective_and_radius_gradient(g, derivs=lambda o: circle_velocity_derivatives(o, 0, V, gradV))
+    Jp = objective_and_radius_gradient(E.circle_config(N, center=tuple(c + EPS * t), r=r))[0]
+    Jm = objective_and_radius_gradient(E.circle_config(N, center=tuple(c - EPS * t), r=r))[0]
+    assert abs(dJ - (Jp - Jm) / (2 * EPS)) <= 1e-6 * abs(dJ)
