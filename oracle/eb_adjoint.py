@@ -231,6 +231,96 @@ def circle_velocity_derivatives(o: Oracle, body: int, V, gradV):
     return dvol, deb, debn, dface
 
 
+def sphere_velocity_derivatives(o: Oracle, body: int, V, gradV):
+    """Moment-table derivatives of o.g (3-D, fluid outside the spheres) when sphere `body`'s surface
+    moves with the normal speed V(x) along N = (x - c)/r: the 3-D counterpart of
+    circle_velocity_derivatives, with the patch and its edges from the moment oracle's quadrature.
+        d/dt int_patch F dA = int (grad F . N V + (2/r) F V) dA + oint_edges F V_e dl,
+        V_e = -V (N . n_p) / (1 - (N . n_p)^2)^(1/2)    (n_p the cell face's normal out of the cell),
+        d/dt n = +grad_G V for n = -N,  the volume loses int_patch xi^p V dA,
+    and a face's covered disk grows along its rim with speed V r / rho."""
+    from .eb_moments import sphere_patch_edges, sphere_patch_nodes
+    from eb_inputs.geometry import monomials
+    g = o.g
+    assert g.dim == 3 and not g.inside
+    h, N = g.h, g.N
+    c = g.centers[body]
+    r = g.radii[body]
+    mons = o.store_mons
+    K = len(mons)
+    n_cut = len(g.cut_cells)
+    dvol = np.zeros((n_cut, K))
+    deb = np.zeros((n_cut, K))
+    debn = np.zeros((n_cut, 3, K))
+    for k in np.nonzero(g.cut_body == body)[0]:
+        cc = int(g.cut_cells[k])
+        ijk = np.array([cc % N, (cc // N) % N, cc // (N * N)], float)
+        lo, hi = ijk * h, (ijk + 1) * h
+        xcell = lo + 0.5 * h
+        x, w = sphere_patch_nodes(c, r, lo, hi)
+        Nn = (x - c[:, None]) / r
+        xi = (x - xcell[:, None]) / h
+        v = V(x)
+        gv = gradV(x)
+        gG = gv - (gv * Nn).sum(0) * Nn
+        edges = []
+        for xe, we, n_p in sphere_patch_edges(c, r, lo, hi):
+            Ne = (xe - c[:, None]) / r
+            en = (Ne * n_p[:, None]).sum(0)
+            edges.append(((xe - xcell[:, None]) / h, Ne, we * V(xe) * -en / np.sqrt(1.0 - en * en)))
+        for m, p in enumerate(mons):
+            f = xi[0] ** p[0] * xi[1] ** p[1] * xi[2] ** p[2]
+            gN = np.zeros_like(f)
+            for d in range(3):
+                if p[d] > 0:
+                    q = list(p)
+                    q[d] -= 1
+                    gN += p[d] * xi[0] ** q[0] * xi[1] ** q[1] * xi[2] ** q[2] * Nn[d] / h
+            dvol[k, m] = -np.sum(w * f * v) / h ** 3
+            val = np.sum(w * (gN * v + 2.0 / r * f * v))
+            for xe, Ne, se in edges:
+                val += np.sum(se * xe[0] ** p[0] * xe[1] ** p[1] * xe[2] ** p[2])
+            deb[k, m] = val / h ** 2
+            for d in range(3):
+                val = np.sum(w * (gN * v * -Nn[d] + f * gG[d] + 2.0 / r * f * -Nn[d] * v))
+                for xe, Ne, se in edges:
+                    val += np.sum(se * xe[0] ** p[0] * xe[1] ** p[1] * xe[2] ** p[2] * -Ne[d])
+                debn[k, d, m] = val / h ** 2
+    deg = max(sum(m) for m in mons)
+    dface = []
+    for d in range(3):
+        cf = g.cut_faces[d]
+        tm = monomials(2, deg)[:g.face_mom[d].shape[1]]
+        oth = [b for b in range(3) if b != d]
+        out = np.zeros((len(cf), len(tm)))
+        for k, f in enumerate(cf):
+            if g.cut_face_body[d][k] != body:
+                continue
+            ijk = o.face_coords(d, int(f))
+            pa = ijk[d] * h
+            q2 = r * r - (pa - c[d]) ** 2
+            if q2 <= 0:
+                continue
+            rho = math.sqrt(q2)
+            lo = [ijk[b] * h for b in oth]
+            hi = [(ijk[b] + 1) * h for b in oth]
+            fc = [(ijk[b] + 0.5) * h for b in oth]
+            for (ta, _), (tb, _) in _arcs(c[oth[0]], c[oth[1]], rho, lo[0], hi[0], lo[1], hi[1]):
+                t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+                wq = 0.5 * (tb - ta) * _GL_W * rho
+                xr = np.zeros((3, len(t)))
+                xr[d] = pa
+                xr[oth[0]] = c[oth[0]] + rho * np.cos(t)
+                xr[oth[1]] = c[oth[1]] + rho * np.sin(t)
+                speed = V(xr) * r / rho
+                u = (xr[oth[0]] - fc[0]) / h
+                vv = (xr[oth[1]] - fc[1]) / h
+                for m, (pu, pv) in enumerate(tm):
+                    out[k, m] -= np.sum(wq * speed * u ** pu * vv ** pv) / h ** 2
+        dface.append(out)
+    return dvol, deb, debn, dface
+
+
 def fourier_mode_velocity(k, theta):
     """Normal speed of the boundary of the distance-function level set psi + a f = 0 per unit a at
     a = 0, for the mode f(x) = sin(2 pi k . x + theta) (|grad psi| = 1): V = -f, grad V = -grad f."""

@@ -183,15 +183,71 @@ def _disk_rect_moments(cu, cv, rho, u0, u1, v0, v1, uc, vc, h, qmax):
     return rect - disk
 
 
+def sphere_patch_nodes(c, r, lo, hi):
+    """Quadrature of the part of the sphere (centre c, radius r) inside the box [lo, hi]:
+    (x [3, m], w [m]) with w the area weights.  The area element in (z, phi) is r dz dphi
+    (Archimedes); at each z the patch is the arcs of the circle of radius (r^2 - (z - c_z)^2)^(1/2)
+    inside the box's x-y rectangle (the whole circle when it lies inside); the z integral is split
+    where the arcs change (tangencies with the rectangle's edge lines and corners) and mapped by
+    the sin^2 substitution."""
+    z_lo, z_hi = max(lo[2], c[2] - r), min(hi[2], c[2] + r)
+    br = [z_lo, z_hi]
+    d2 = [(lo[0] - c[0]) ** 2, (hi[0] - c[0]) ** 2, (lo[1] - c[1]) ** 2, (hi[1] - c[1]) ** 2]
+    d2 += [(x - c[0]) ** 2 + (y - c[1]) ** 2 for x in (lo[0], hi[0]) for y in (lo[1], hi[1])]
+    for dd in d2:
+        q = r * r - dd
+        if q > 0:
+            for zz in (c[2] - math.sqrt(q), c[2] + math.sqrt(q)):
+                if z_lo < zz < z_hi:
+                    br.append(zz)
+    zs, wz = _sin2_panels(sorted(br))
+    xs, ws = [], []
+    for z, wzz in zip(zs, wz):
+        rho2 = r * r - (z - c[2]) ** 2
+        if rho2 <= 0:
+            continue
+        rho = math.sqrt(rho2)
+        arcs = [(ta, tb) for (ta, _), (tb, _) in _arcs(c[0], c[1], rho, lo[0], hi[0], lo[1], hi[1])]
+        if not arcs and lo[0] < c[0] - rho and c[0] + rho < hi[0] and lo[1] < c[1] - rho and c[1] + rho < hi[1]:
+            arcs = [(0.0, 2 * math.pi)]
+        for ta, tb in arcs:
+            t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+            xs.append(np.stack([c[0] + rho * np.cos(t), c[1] + rho * np.sin(t), np.full_like(t, z)]))
+            ws.append(wzz * r * 0.5 * (tb - ta) * _GL_W)
+    if not xs:
+        return np.zeros((3, 0)), np.zeros(0)
+    return np.concatenate(xs, axis=1), np.concatenate(ws)
+
+
+def sphere_patch_edges(c, r, lo, hi):
+    """The edges of the sphere patch inside the box: on each face plane of the box the arcs of the
+    circle the sphere cuts from it, inside the face.  List of (x [3, m], w [m] length weights,
+    n_p [3] the face's normal out of the box)."""
+    out = []
+    for ax in range(3):
+        oth = [b for b in range(3) if b != ax]
+        for side, pa in ((-1.0, lo[ax]), (1.0, hi[ax])):
+            q2 = r * r - (pa - c[ax]) ** 2
+            if q2 <= 0:
+                continue
+            rho = math.sqrt(q2)
+            n_p = np.zeros(3)
+            n_p[ax] = side
+            for (ta, _), (tb, _) in _arcs(c[oth[0]], c[oth[1]], rho, lo[oth[0]], hi[oth[0]], lo[oth[1]], hi[oth[1]]):
+                t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
+                x = np.zeros((3, len(t)))
+                x[ax] = pa
+                x[oth[0]] = c[oth[0]] + rho * np.cos(t)
+                x[oth[1]] = c[oth[1]] + rho * np.sin(t)
+                out.append((x, 0.5 * (tb - ta) * _GL_W * rho, n_p))
+    return out
+
+
 def sphere_moments(N, centers, radii, cells, qmax=4):
     """Volume and EB moment tables of the unit cube minus spheres for the listed cut cells (each cut
     by one sphere): dict cell -> {'vol' [K], 'eb' [K], 'ebn' [3, K]}, scaled like the input tables.
 
-    EB patch: the sphere's area element in (z, phi) is r dz dphi (Archimedes), and at each z the
-    patch is the arcs of the circle of radius (r^2 - (z - c_z)^2)^(1/2) inside the cell's x-y
-    rectangle (the whole circle when it lies inside); the z integral is split where the arcs change
-    (tangencies with the rectangle's edge lines and corners) and mapped by the sin^2 substitution.
-    Volume moments by the divergence theorem: int_V xi^p dV = h/(p_x+1) oint xi^(p+e_x) n_x dA over
+    EB patch: the quadrature of sphere_patch_nodes.  Volume moments by the divergence theorem: int_V xi^p dV = h/(p_x+1) oint xi^(p+e_x) n_x dA over
     the cell's two x faces (their fluid parts: square minus disk) and the patch (n_x = -e_x)."""
     h = 1.0 / N
     mons = _mons3(qmax)
@@ -214,41 +270,18 @@ def sphere_moments(N, centers, radii, cells, qmax=4):
         if b is None:
             continue
         c, r = np.asarray(centers[b], float), float(radii[b])
-        z_lo, z_hi = max(lo[2], c[2] - r), min(hi[2], c[2] + r)
-        br = [z_lo, z_hi]
-        d2 = [(lo[0] - c[0]) ** 2, (hi[0] - c[0]) ** 2, (lo[1] - c[1]) ** 2, (hi[1] - c[1]) ** 2]
-        d2 += [(x - c[0]) ** 2 + (y - c[1]) ** 2 for x in (lo[0], hi[0]) for y in (lo[1], hi[1])]
-        for dd in d2:
-            q = r * r - dd
-            if q > 0:
-                for zz in (c[2] - math.sqrt(q), c[2] + math.sqrt(q)):
-                    if z_lo < zz < z_hi:
-                        br.append(zz)
-        zs, wz = _sin2_panels(sorted(br))
+        x, wt = sphere_patch_nodes(c, r, lo, hi)
+        e = (x - c[:, None]) / r
+        xi = (x - xc[:, None]) / h
         eb = np.zeros(K)
         ebn = np.zeros((3, K))
         vol = np.zeros(K)
-        for z, wzz in zip(zs, wz):
-            rho2 = r * r - (z - c[2]) ** 2
-            if rho2 <= 0:
-                continue
-            rho = math.sqrt(rho2)
-            arcs = [(ta, tb) for (ta, _), (tb, _) in _arcs(c[0], c[1], rho, lo[0], hi[0], lo[1], hi[1])]
-            if not arcs and lo[0] < c[0] - rho and c[0] + rho < hi[0] and lo[1] < c[1] - rho and c[1] + rho < hi[1]:
-                arcs = [(0.0, 2 * math.pi)]
-            for ta, tb in arcs:
-                t = 0.5 * (tb - ta) * _GL_X + 0.5 * (tb + ta)
-                wt = wzz * r * 0.5 * (tb - ta) * _GL_W  # dA = r dz dphi
-                x, y = c[0] + rho * np.cos(t), c[1] + rho * np.sin(t)
-                ex, ey, ez = (x - c[0]) / r, (y - c[1]) / r, (z - c[2]) / r
-                xi, et, ze = (x - xc[0]) / h, (y - xc[1]) / h, (z - xc[2]) / h
-                for m, p in enumerate(mons):
-                    f = xi ** p[0] * et ** p[1] * ze ** p[2]
-                    eb[m] += np.sum(wt * f)
-                    ebn[0, m] -= np.sum(wt * f * ex)
-                    ebn[1, m] -= np.sum(wt * f * ey)
-                    ebn[2, m] -= np.sum(wt * f * ez)
-                    vol[m] -= np.sum(wt * xi ** (p[0] + 1) * et ** p[1] * ze ** p[2] * ex) / (p[0] + 1)
+        for m, p in enumerate(mons):
+            f = xi[0] ** p[0] * xi[1] ** p[1] * xi[2] ** p[2]
+            eb[m] = np.sum(wt * f)
+            for d in range(3):
+                ebn[d, m] = -np.sum(wt * f * e[d])
+            vol[m] = -np.sum(wt * xi[0] ** (p[0] + 1) * xi[1] ** p[1] * xi[2] ** p[2] * e[0]) / (p[0] + 1)
         eb /= h * h
         ebn /= h * h
         vol /= h * h  # vol_mom = int_V xi^p dV / h^3 = (1 / (h^2 (p_x+1))) oint xi^(p+e_x) n_x dA
