@@ -334,6 +334,20 @@ def fourier_mode_velocity(k, theta):
     return V, gradV
 
 
+def fourier_mode_derivatives(o: Oracle, k, theta):
+    """Moment-table derivatives with respect to the amplitude a of the mode sin(2 pi k . x + theta)
+    added to the distance-function level set of all the bodies, at a = 0: every body's boundary
+    moves with V = -sin(...)."""
+    V, gradV = fourier_mode_velocity(k, theta)
+    fn = circle_velocity_derivatives if o.g.dim == 2 else sphere_velocity_derivatives
+    parts = [fn(o, b, V, gradV) for b in range(len(o.g.radii))]
+    dvol = sum(p_[0] for p_ in parts)
+    deb = sum(p_[1] for p_ in parts)
+    debn = sum(p_[2] for p_ in parts)
+    dface = [sum(p_[3][d] for p_ in parts) for d in range(o.g.dim)]
+    return dvol, deb, debn, dface
+
+
 def _mono_index(D, deg):
     from eb_inputs.geometry import monomials
     ms = monomials(D, deg)

@@ -1,6 +1,8 @@
 """Pins of the adjoint oracle (oracle/eb_adjoint.py) against central finite differences of what it
 differentiates: the geometry generator's moment tables, and the whole forward problem (moments ->
 stencils -> operator -> solve -> J), for the radius of a circle in the unit square."""
+import math
+
 import numpy as np
 import pytest
 
@@ -176,3 +178,20 @@ def test_velocity_derivatives_3d():
     for an, x, y in pairs:
         fd = (x - y) / (2 * EPS)
         assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
+def test_fourier_mode_derivatives_sum_over_bodies():
+    """A mode with k = 0 is a constant shift of the level set: its derivative is -sin(theta) times the
+    sum over the bodies of the radius derivatives."""
+    from oracle.eb_adjoint import circle_moment_derivatives, fourier_mode_derivatives
+    g = E.Geometry(2, 16, np.array([[0.31, 0.29, 0.0], [0.69, 0.66, 0.0]]), np.array([0.13, 0.17]), False, 4)
+    o = Oracle(g, Params(order=4))
+    th = 0.7
+    a = fourier_mode_derivatives(o, (0, 0), th)
+    parts = [circle_moment_derivatives(o, b) for b in range(2)]
+    for i in range(3):
+        ref = -math.sin(th) * (parts[0][i] + parts[1][i])
+        assert np.abs(a[i] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    for d in range(2):
+        ref = -math.sin(th) * (parts[0][3][d] + parts[1][3][d])
+        assert np.abs(a[3][d] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
