@@ -319,3 +319,124 @@ def sphere_face_moments(N, centers, radii, d, faces, qmax=4):
             mom = m if mom is None else mom - (full - m)  # disks of different spheres do not overlap
         out[f] = mom
     return out
+
+
+# --------------------------------------------------------------------- 2-D: a perturbed level set
+
+def level_set_moments_2d(g, modes):
+    """Moment tables of the level set psi(x) = min_i(|x - c_i| - r_i) + sum_m a_m sin(2 pi k_m . x +
+    theta_m) (fluid where psi > 0), on the cut cells and cut faces of the circle geometry g (the
+    perturbation is taken small enough to keep them): (vol [n_cut, K], eb, ebn [n_cut, 2, K],
+    face [per d]).  modes: list of (a, (k_x, k_y), theta).
+
+    Each cut cell is integrated as a height function: along the direction where the circle's normal
+    at the cell centre is largest the boundary is a graph, its height found by bracketed root
+    finding in each column; the columns' fluid parts are integrated in closed form, the boundary with
+    ds = |grad psi| / |d psi / d height| d(other), its normal out of the fluid -grad psi / |grad psi|;
+    the other coordinate is split where the boundary crosses the cell's edges (Gauss-Legendre on
+    sin^2-mapped panels).  Faces: the fluid parts of each edge between the roots of psi on it."""
+    from scipy.optimize import brentq
+    h, N = g.h, g.N
+    cen = g.centers[:, :2]
+    rad = g.radii
+
+    def psi_b(x, y, b):
+        v = np.hypot(x - cen[b, 0], y - cen[b, 1]) - rad[b]
+        for a, k, th in modes:
+            v = v + a * np.sin(2 * math.pi * (k[0] * x + k[1] * y) + th)
+        return v
+
+    def grad_b(x, y, b):
+        rr = np.hypot(x - cen[b, 0], y - cen[b, 1])
+        gx, gy = (x - cen[b, 0]) / rr, (y - cen[b, 1]) / rr
+        for a, k, th in modes:
+            cs = a * 2 * math.pi * np.cos(2 * math.pi * (k[0] * x + k[1] * y) + th)
+            gx, gy = gx + cs * k[0], gy + cs * k[1]
+        return gx, gy
+
+    mons = _mons2(g.qmax)
+    K = len(mons)
+    n_cut = len(g.cut_cells)
+    vol = np.zeros((n_cut, K))
+    eb = np.zeros((n_cut, K))
+    ebn = np.zeros((n_cut, 2, K))
+    for kc, cc in enumerate(g.cut_cells):
+        b = int(g.cut_body[kc])
+        i, j = int(cc) % N, int(cc) // N
+        lo, hi = np.array([i * h, j * h]), np.array([(i + 1) * h, (j + 1) * h])
+        xc = lo + 0.5 * h
+        nrm = xc - cen[b]
+        hd = int(np.argmax(np.abs(nrm)))  # height direction
+        od = 1 - hd
+
+        def P(u, v):  # psi with (u, v) = (other, height) coordinates
+            return psi_b(u, v, b) if od == 0 else psi_b(v, u, b)
+
+        def G(u, v):
+            gx, gy = grad_b(u, v, b) if od == 0 else grad_b(v, u, b)
+            return (gx, gy) if od == 0 else (gy, gx)  # (d/du, d/dv)
+
+        # breaks in u: where the boundary meets the edges v = lo[hd], hi[hd]
+        br = [lo[od], hi[od]]
+        for ve in (lo[hd], hi[hd]):
+            us = np.linspace(lo[od], hi[od], 65)
+            vals = P(us, np.full_like(us, ve))
+            for a_, b_, fa, fb in zip(us[:-1], us[1:], vals[:-1], vals[1:]):
+                if fa == 0.0 or fa * fb < 0:
+                    br.append(brentq(lambda u: P(u, ve), a_, b_, xtol=1e-15, rtol=1e-15) if fa != 0.0 else a_)
+        us, wu = _sin2_panels(sorted(br))
+        for u, w in zip(us, wu):
+            f0, f1 = P(u, lo[hd]), P(u, hi[hd])
+            if f0 * f1 < 0:
+                v = brentq(lambda t: P(u, t), lo[hd], hi[hd], xtol=1e-15, rtol=1e-15)
+                fluid = (v, hi[hd]) if f1 > 0 else (lo[hd], v)
+                gu, gv = G(u, v)
+                gn = math.hypot(gu, gv)
+                ds = gn / abs(gv)
+                nvec = np.array([-gu / gn, -gv / gn])  # out of the fluid, in (u, v) order
+                xy = np.zeros(2)
+                xy[od], xy[hd] = u, v
+                xi = (xy - xc) / h
+                nd = np.zeros(2)
+                nd[od], nd[hd] = nvec[0], nvec[1]
+                for m, p in enumerate(mons):
+                    f = xi[0] ** p[0] * xi[1] ** p[1]
+                    eb[kc, m] += w * ds * f / h
+                    ebn[kc, 0, m] += w * ds * f * nd[0] / h
+                    ebn[kc, 1, m] += w * ds * f * nd[1] / h
+            elif f0 > 0 and f1 > 0:
+                fluid = (lo[hd], hi[hd])
+            else:
+                continue
+            a_, b_ = (fluid[0] - xc[hd]) / h, (fluid[1] - xc[hd]) / h
+            su = (u - xc[od]) / h
+            for m, p in enumerate(mons):
+                ph, po = p[hd], p[od]
+                vol[kc, m] += w / h * su ** po * (b_ ** (ph + 1) - a_ ** (ph + 1)) / (ph + 1)
+    faces = []
+    for d in range(2):
+        cf = g.cut_faces[d]
+        out = np.zeros((len(cf), g.face_mom[d].shape[1]))
+        for kf, f in enumerate(cf):
+            b = int(g.cut_face_body[d][kf])
+            shape = [N + (k == d) for k in range(2)]
+            ij = [int(f) % shape[0], int(f) // shape[0]]
+            xn = ij[d] * h
+            td = 1 - d
+            t0, t1 = ij[td] * h, (ij[td] + 1) * h
+            tc = 0.5 * (t0 + t1)
+
+            def Pt(t):
+                return psi_b(xn, t, b) if d == 0 else psi_b(t, xn, b)
+            ts = np.linspace(t0, t1, 129)
+            vals = Pt(ts)
+            pts = [t0]
+            for a_, b_, fa, fb in zip(ts[:-1], ts[1:], vals[:-1], vals[1:]):
+                if fa * fb < 0:
+                    pts.append(brentq(Pt, a_, b_, xtol=1e-15, rtol=1e-15))
+            pts.append(t1)
+            for a_, b_ in zip(pts[:-1], pts[1:]):
+                if Pt(0.5 * (a_ + b_)) > 0:
+                    out[kf] += _segment_moments((a_ - tc) / h, (b_ - tc) / h, out.shape[1] - 1)
+        faces.append(out)
+    return vol, eb, ebn, faces

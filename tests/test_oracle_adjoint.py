@@ -195,3 +195,50 @@ def test_fourier_mode_derivatives_sum_over_bodies():
     for d in range(2):
         ref = -math.sin(th) * (parts[0][3][d] + parts[1][3][d])
         assert np.abs(a[3][d] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def _two_circles():
+    return E.Geometry(2, 16, np.array([[0.31, 0.29, 0.0], [0.69, 0.66, 0.0]]), np.array([0.13, 0.17]), False, 4)
+
+
+def _with_moments(g, mo):
+    import copy
+    gg = copy.copy(g)
+    gg.vol_mom, gg.eb_mom, gg.eb_nmom, gg.face_mom = mo[0], mo[1], mo[2], list(mo[3])
+    gg.kappa = g.kappa.copy()
+    gg.kappa[g.cut_cells] = mo[0][:, 0]
+    return gg
+
+
+def test_level_set_moments_reduce_to_circles():
+    """The level-set moment oracle (height functions with root finding) with no Fourier term equals the
+    generator's circle moments."""
+    from oracle.eb_moments import level_set_moments_2d
+    g = _two_circles()
+    vol, eb, ebn, faces = level_set_moments_2d(g, [])
+    assert np.abs(vol - g.vol_mom).max() <= 1e-13
+    assert np.abs(eb - g.eb_mom).max() <= 1e-13
+    assert np.abs(ebn - g.eb_nmom).max() <= 1e-13
+    for d in range(2):
+        assert np.abs(faces[d] - g.face_mom[d]).max() <= 1e-13
+
+
+def test_fourier_mode_derivatives_against_level_set():
+    """dJ/da for a Fourier mode of the level set at a = 0: the moment derivatives (every boundary
+    moving with V = -sin(2 pi k . x + theta)) against central differences of the level-set moments,
+    and dJ/da through the solve and LS-build adjoints against central differences of J."""
+    from oracle.eb_adjoint import fourier_mode_derivatives
+    from oracle.eb_moments import level_set_moments_2d
+    g = _two_circles()
+    k, th = (1, 2), 0.3
+    mp = level_set_moments_2d(g, [(EPS, k, th)])
+    mm = level_set_moments_2d(g, [(-EPS, k, th)])
+    dm = fourier_mode_derivatives(Oracle(g, Params(order=4)), k, th)
+    pairs = [(dm[i], mp[i], mm[i]) for i in range(3)] + [(dm[3][d], mp[3][d], mm[3][d]) for d in range(2)]
+    for an, a, b in pairs:
+        fd = (a - b) / (2 * EPS)
+        assert np.abs(an - fd).max() <= 1e-7 * np.abs(fd).max()
+    J, dJ = objective_and_radius_gradient(g, derivs=lambda o: fourier_mode_derivatives(o, k, th))
+    fdJ = (objective_and_radius_gradient(_with_moments(g, mp))[0]
+           - objective_and_radius_gradient(_with_moments(g, mm))[0]) / (2 * EPS)
+    assert abs(dJ - fdJ) <= 1e-6 * abs(fdJ)
