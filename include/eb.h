@@ -148,7 +148,10 @@ eb_status eb_apply(const eb_stencils* st, const void* phi, void* y, int32_t dtyp
                    eb_stream_t stream);
 
 /* Bg = B g, the boundary-data part of the Laplacian (FP64; kappa-weighted
- * when kappa_weighted = 1).  g_eb: [n_cut] face averages on the EB faces
+ * when kappa_weighted = 1): the boundary-face columns of the flux stencils
+ * (Sec. 2.2.1, boundary rows b_{f_b p}) summed into each volume's flux
+ * divergence (Sec. 2.3).  Bg: [ncell], written on every cell (0 where no
+ * boundary face reaches).  g_eb: [n_cut] face averages on the EB faces
  * (Dirichlet: <phi>_f; Neumann: <grad phi . n>_f); g_wall: values on the
  * open wall faces in ascending global face id (eb_wall_faces lists them). */
 eb_status eb_bc_rhs(const eb_stencils* st, const double* g_eb, const double* g_wall, double* Bg,
@@ -174,11 +177,17 @@ typedef struct eb_solve_info {
   int32_t n_history;
   int32_t n_applies;      /* Krylov operator applies timed (check_every < 0) */
   double apply_ms;        /* their summed device time */
+  int32_t precond_blocks; /* exact local block solves in the preconditioner (0 for Jacobi) */
 } eb_solve_info;
 
-/* Solve L phi = rho - B g to a relative residual tol (kappa-weighted system
- * kappa L phi = kappa (rho - B g)).  rho: [ncell] cell averages of the
- * source; phi: [ncell] initial guess on entry, solution on exit (FP64). */
+/* Solve the discrete Poisson problem L phi = rho - B g of Sec. 2.3 (the
+ * paper solves it with preconditioned GMRES, Sec. 3.2; here BiCGStab with
+ * FP64 iterative refinement) to a relative residual tol of the
+ * kappa-weighted system kappa L phi = kappa (rho - B g).  rho: [ncell] cell
+ * averages of the source; phi: [ncell] initial guess on entry, solution on
+ * exit (FP64); g_eb, g_wall as for eb_bc_rhs.  Returns
+ * EB_ERR_NOT_CONVERGED (phi holds the last iterate) when the iteration caps
+ * are reached first.  Synchronises the stream to read residual norms. */
 eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
                    const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream);
 
@@ -186,7 +195,8 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
  * L2 = (sum e^2 |V| / sum |V|)^(1/2).  err: [ncell] FP64 device; out_host[3]. */
 eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, eb_stream_t stream);
 
-/* Debug / parity: the flux stencil of a face (global face id).  Columns:
+/* Debug / parity: the flux stencil s_f of Sec. 2.2.1 (the minimum-||W^-1 s||
+ * solution of A^T s = F) of a face (global face id).  Columns:
  * volume -> cell index; boundary face -> -(1 + global face id).  Values are
  * the h-scaled stencil s_hat (s = h^(D-2) s_hat), rows in canonical order
  * (volumes ascending, wall faces ascending, EB faces ascending).  With
@@ -197,7 +207,11 @@ eb_status eb_stencil_query(const eb_stencils* st, int64_t face, int32_t* n, int6
 /* Open wall faces in ascending global face id (the g_wall order). */
 eb_status eb_wall_faces(const eb_stencils* st, int64_t* ids_host, int64_t cap, int64_t* n);
 
-/* Faces whose LS system was rank deficient in the last failed build. */
+/* Faces whose LS system was rank deficient in the last failed build on the
+ * calling thread (Sec. 2.4 uses one R_n everywhere, so no fallback is
+ * applied): every such face in ascending global face id, including each face
+ * of a translation class whose shared system failed.  With ids_host == NULL
+ * only *n is written; at most cap ids are copied. */
 eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n);
 
 /* Batched weighted minimum-norm least squares that allocates nothing (the
@@ -208,8 +222,8 @@ eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n);
  * For each system q (rows row_ptr[q] .. row_ptr[q+1]-1, at most 256 rows and
  * K <= 35 unknowns): B holds the weighted rows W A ([nnz][K], row-major), w
  * the weights W_ii, F the right-hand side ([n_sys][K]); s receives the
- * stencil s = W t with t the least-||t|| solution of B^T t = F (Sec. 2.2.1
- * applied to rows the caller formed); status[q] = 0 ok, 1 rank deficient or
+ * stencil s = W t with t the least-||t|| solution of B^T t = F (the
+ * weighted minimum-norm problem, for rows the caller formed); status[q] = 0 ok, 1 rank deficient or
  * fewer rows than K, 3 more than 256 rows.  All pointers are device pointers
  * owned by the caller.  max_rows is the caller's bound on the rows of any
  * system; above 256 the call returns EB_ERR_CAPACITY without launching.
@@ -218,10 +232,41 @@ eb_status eb_last_error_faces(int64_t* ids_host, int32_t cap, int32_t* n);
  * The first call on each device looks up that array's device address (with
  * the device current) and should come before any stream capture.  Every call
  * shares the array, so calls that overlap on the GPU (other streams, other
- * host threads) race: serialise them.  Never synchronises. */
+ * host threads) race: serialise them.  The array's address is cached per
+ * device for the life of the process; after a cudaDeviceReset the process
+ * must not call this entry point on that device again.  Never synchronises. */
 eb_status eb_lsq_batch_noalloc(const double* B, const double* w, const double* F, const int64_t* row_ptr,
                                int32_t n_sys, int32_t K, int32_t max_rows, double* s, int32_t* status,
                                eb_stream_t stream);
+
+/* Moment tables computed on the device (Sec. 2.1: volume moments m^p_v,
+ * face moments m^p_f and the EB-patch moments, plain and weighted by each
+ * normal component; exact to rounding, which meets the O(h^{6+D}) of Sec.
+ * 3.1), for the unit square [0,1]^2 on an N x N grid minus n_body circles
+ * (inside = 0: fluid outside every circle) or inside one circle (inside = 1,
+ * n_body = 1).  centers_host: [n_body][2], radii_host: [n_body] (host
+ * arrays); moment_degree 0..6 (>= the order of the stencils built on it).
+ * On success *out owns the device tables and *desc points into them, in the
+ * layout eb_geom documents (cut cells and cut faces ascending; cells with
+ * volume fraction <= 1e-14 count as covered, >= 1 - 1e-14 as full, faces
+ * likewise, and a face next to a covered cell is closed); desc can be passed
+ * to eb_build_stencils as it is.  A cell or face that two circles reach into
+ * gives EB_ERR_MULTIVALUED.  Synchronises the stream.  Free with
+ * eb_geometry_destroy (which synchronises the device) after the last use of
+ * desc. */
+typedef struct eb_geometry eb_geometry; /* opaque, library-owned */
+eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double* centers_host, const double* radii_host,
+                              int32_t inside, int32_t moment_degree, eb_geometry** out, eb_geom* desc,
+                              eb_stream_t stream);
+void eb_geometry_destroy(eb_geometry* g);
+
+/* Copy one table of a device geometry to host memory (dir: face direction
+ * for the face tables).  *bytes receives the table's size; with dst_host ==
+ * NULL nothing is copied.  Synchronous. */
+enum { EB_TABLE_CELL_FLAG = 0, EB_TABLE_CUT_CELL = 1, EB_TABLE_VOL_MOM = 2, EB_TABLE_EB_MOM = 3,
+       EB_TABLE_EB_NMOM = 4, EB_TABLE_FACE_FLAG = 5, EB_TABLE_CUTFACE = 6, EB_TABLE_FACE_MOM = 7 };
+eb_status eb_geometry_table(const eb_geometry* g, int32_t which, int32_t dir, void* dst_host, int64_t cap_bytes,
+                            int64_t* bytes);
 
 void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);

@@ -63,12 +63,12 @@ class EbSolveOpts(ctypes.Structure):
 class EbSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("history", ctypes.c_double * 64), ("n_history", ctypes.c_int32), ("n_applies", ctypes.c_int32),
-                ("apply_ms", ctypes.c_double)]
+                ("apply_ms", ctypes.c_double), ("precond_blocks", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "sweeps": self.sweeps, "rel_residual": self.rel_residual,
                 "history": [self.history[i] for i in range(self.n_history)], "n_applies": self.n_applies,
-                "apply_ms": self.apply_ms}
+                "apply_ms": self.apply_ms, "precond_blocks": self.precond_blocks}
 
 
 class EbError(RuntimeError):
@@ -109,6 +109,9 @@ def load():
         "eb_abi_version": (i32, []),
         "eb_kernel_launches": (i64, []),
         "eb_lsq_batch_noalloc": (i32, [_vp, _vp, _vp, _vp, i32, i32, i32, _vp, _vp, _vp]),
+        "eb_geometry_circles": (i32, [i32, i32, P(dbl), P(dbl), i32, i32, P(_vp), P(EbGeom), _vp]),
+        "eb_geometry_destroy": (None, [_vp]),
+        "eb_geometry_table": (i32, [_vp, i32, i32, _vp, i64, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,6 +190,71 @@ class DeviceGeometry:
             s.cutface[d] = _ptr(self.cut_faces[d])
             s.face_mom[d] = _ptr(self.face_mom[d])
         return s
+
+
+class GpuGeometry:
+    """Moment tables computed on the device by the library (eb_geometry_circles); owns the handle.
+    Usable wherever a DeviceGeometry is (eb_build_stencils takes either)."""
+
+    TABLES = {"flag": 0, "cut_cells": 1, "vol_mom": 2, "eb_mom": 3, "eb_nmom": 4, "face_flag": 5, "cut_faces": 6,
+              "face_mom": 7}
+
+    def __init__(self, handle, desc: EbGeom, eb_bc=None):
+        self.handle = handle
+        self.desc = desc
+        self.dim = desc.dim
+        self.n = tuple(desc.n[d] for d in range(3))
+        self.h = desc.h
+        self.moment_degree = desc.moment_degree
+        self.n_cut = desc.n_cut
+        self.eb_bc = None
+        if eb_bc is not None:
+            self.set_eb_bc(eb_bc)
+
+    def set_eb_bc(self, eb_bc):
+        import torch
+        self.eb_bc = _dev(eb_bc, torch.uint8)
+        self.desc.eb_bc = _ptr(self.eb_bc)
+
+    def struct(self) -> EbGeom:
+        return self.desc
+
+    def table(self, name: str, d: int = 0) -> np.ndarray:
+        """A table copied to the host, shaped like the eb_inputs.Geometry attribute of that name."""
+        lib = load()
+        w = self.TABLES[name]
+        nb = ctypes.c_int64()
+        _check(lib.eb_geometry_table(self.handle, w, d, None, 0, ctypes.byref(nb)))
+        dt = {0: np.uint8, 1: np.int32, 5: np.uint8, 6: np.int32}.get(w, np.float64)
+        out = np.zeros(max(nb.value // np.dtype(dt).itemsize, 1), dtype=dt)
+        _check(lib.eb_geometry_table(self.handle, w, d, out.ctypes.data_as(ctypes.c_void_p), out.nbytes,
+                                     ctypes.byref(nb)))
+        out = out[:nb.value // np.dtype(dt).itemsize]
+        if name in ("vol_mom", "eb_mom"):
+            out = out.reshape(self.n_cut, -1)
+        elif name == "eb_nmom":
+            out = out.reshape(self.n_cut, self.dim, -1)
+        elif name == "face_mom":
+            out = out.reshape(self.desc.n_cutface[d], -1)
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.eb_geometry_destroy(self.handle)
+            self.handle = None
+
+
+def eb_geometry_circles(N, centers, radii, inside=False, moment_degree=4, stream=None) -> GpuGeometry:
+    """Moment tables of the unit square minus circles (or inside one circle), computed on the device."""
+    lib = load()
+    c = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 2))
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+    h = ctypes.c_void_p()
+    desc = EbGeom()
+    _check(lib.eb_geometry_circles(int(N), len(r), c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(bool(inside)),
+                                   int(moment_degree), ctypes.byref(h), ctypes.byref(desc), _stream(stream)))
+    return GpuGeometry(h, desc)
 
 
 class Stencils:
@@ -307,7 +375,14 @@ def eb_lsq_batch_noalloc(B, w, F, row_ptr, K, max_rows, s, status, stream=None):
     real-time hosts, allocation-free plugin callbacks): all tensors are the caller's, and the
     library's working storage is one fixed array.  Calls that overlap on the GPU race.
     """
+    import torch
     n_sys = int(row_ptr.numel()) - 1
+    for t, dt in ((B, torch.float64), (w, torch.float64), (F, torch.float64), (s, torch.float64),
+                  (row_ptr, torch.int64), (status, torch.int32)):
+        assert t.dtype == dt and t.is_cuda and t.is_contiguous(), "eb_lsq_batch_noalloc: argument type"
+    nnz = w.numel()  # the caller's row count (row_ptr[-1]), taken from w to avoid a device read
+    assert n_sys >= 0 and B.numel() == nnz * int(K) and s.numel() == nnz, "eb_lsq_batch_noalloc: row arrays"
+    assert F.numel() == n_sys * int(K) and status.numel() == n_sys, "eb_lsq_batch_noalloc: system arrays"
     _check(load().eb_lsq_batch_noalloc(_ptr(B), _ptr(w), _ptr(F), _ptr(row_ptr), n_sys, int(K), int(max_rows),
                                        _ptr(s), _ptr(status), _stream(stream)))
     return s
@@ -317,5 +392,5 @@ def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "GpuGeometry", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libeb_gb300.so")
-SOURCES = ["eb_api.cu", "eb_build.cu", "eb_apply.cu", "eb_solve.cu", "eb_noalloc.cu", "eb_mg.cu"]
+SOURCES = ["eb_api.cu", "eb_build.cu", "eb_apply.cu", "eb_solve.cu", "eb_noalloc.cu", "eb_mg.cu", "eb_geom.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

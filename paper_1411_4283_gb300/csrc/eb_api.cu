@@ -17,6 +17,7 @@
 
 #include "eb_apply.cuh"
 #include "eb_apply_quad.cuh"
+#include "eb_apply_brick.cuh"
 #include "eb_internal.cuh"
 #include "eb_scan.cuh"
 #include "eb_solve.cuh"
@@ -418,6 +419,73 @@ __global__ void k_run_split(int64_t nC, const int32_t* cellC, const int32_t* cla
   }
 }
 
+// class cells outside the runs: those in the x slabs (x < BR_W or x >= nx - BR_W) go to the slab map of the
+// brick pass, the others stay in the per-cell list (keep = 1)
+__global__ void k_slab_scatter(int64_t nL, const int32_t* cellL, const int32_t* classL, int nx, int ny, int nz,
+                               int32_t* slab, int32_t* keep) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nL) return;
+  const int32_t c = cellL[t];
+  const int x = c % nx, y = (c / nx) % ny, z = c / nx / ny;
+  int side, xl;
+  if (x < BR_W) { side = 0; xl = x; }
+  else if (x >= nx - BR_W) { side = 1; xl = x - (nx - BR_W); }
+  else { keep[t] = 1; return; }
+  keep[t] = 0;
+  slab[((int64_t)(side * BR_W + xl) * nz + z) * ny + y] = classL[t];
+}
+
+// the unit of a slab cell (side, x layer, z block, y block), or -1 outside the units
+__device__ __forceinline__ int64_t brick_unit(int side, int xl, int y, int z, int nyb, int nzb, int y_org, int z_org,
+                                              int y_hi, int z_hi) {
+  if (y < y_org || y >= y_hi || z < z_org || z >= z_hi) return -1;
+  return (((int64_t)side * BR_W + xl) * nzb + (z - z_org) / BR_BZ) * nyb + (y - y_org) / 32;
+}
+
+}  // namespace eb
+
+__global__ void eb::k_brick_units(const int32_t* __restrict__ slab, int ny, int nz, int nyb, int nzb, int y_org,
+                                  int z_org, int y_hi, int z_hi, int32_t* __restrict__ unit_class) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= (int64_t)2 * BR_W * nzb * nyb) return;
+  const int yblk = (int)(u % nyb), zblk = (int)((u / nyb) % nzb), sx = (int)(u / ((int64_t)nyb * nzb));
+  const int y0 = y_org + 32 * yblk, z0 = z_org + BR_BZ * zblk;
+  const int y1 = min(y0 + 32, y_hi), z1 = min(z0 + BR_BZ, z_hi);
+  int cls = -2;
+  for (int z = z0; z < z1 && cls != -1; ++z)
+    for (int y = y0; y < y1; ++y) {
+      const int v = slab[((int64_t)sx * nz + z) * ny + y];
+      if (v < 0 || (cls != -2 && v != cls)) { cls = -1; break; }
+      cls = v;
+    }
+  unit_class[u] = cls < 0 ? -1 : cls;
+}
+
+namespace eb {
+
+// class cells of the slab list that a uniform brick unit covers leave the per-cell list (keep = 0)
+__global__ void k_brick_keep(int64_t nL, const int32_t* cellL, int nx, int ny, int nz, int nyb, int nzb, int y_org,
+                             int z_org, int y_hi, int z_hi, const int32_t* unit_class, int32_t* keep) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nL) return;
+  const int32_t c = cellL[t];
+  const int x = c % nx, y = (c / nx) % ny, z = c / nx / ny;
+  int side, xl;
+  if (x < BR_W) { side = 0; xl = x; }
+  else if (x >= nx - BR_W) { side = 1; xl = x - (nx - BR_W); }
+  else { keep[t] = 1; return; }
+  const int64_t u = brick_unit(side, xl, y, z, nyb, nzb, y_org, z_org, y_hi, z_hi);
+  keep[t] = (u < 0 || unit_class[u] < 0) ? 1 : 0;
+}
+
+__global__ void k_compact_pair(int64_t n, const int32_t* keep, const int64_t* pos, const int32_t* a,
+                               const int32_t* b, int32_t* a2, int32_t* b2) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n || !keep[t]) return;
+  a2[pos[t]] = a[t];
+  b2[pos[t]] = b[t];
+}
+
 // class rows, class-major: out[k * nfoot + i] = rows[i][k]
 template <typename T>
 __global__ void k_class_major(const T* __restrict__ rows, int64_t n_rows, int64_t n_class, int nfoot,
@@ -482,7 +550,7 @@ const char* eb_status_string(eb_status s) {
 }
 
 const char* eb_last_error_message(void) { return g_err.c_str(); }
-int32_t eb_abi_version(void) { return 1; }
+int32_t eb_abi_version(void) { return 2; }
 int64_t eb_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 void eb_stencils_destroy(eb_stencils* st) {
@@ -793,6 +861,43 @@ static eb_status build_quad_plan(eb_stencils* st, ApplyPlan* pl, int R, cudaStre
     EB_TRY(dalloc(st, &pl->classL, std::max<int64_t>(nL, 1)));
     k_run_split<<<nblk(nC, 256), 256, 0, s>>>(nC, pl->cellC, pl->classC, gs, rest, gpos, lpos, pl->cellG, pl->classG,
                                               pl->cellL, pl->classL); eb::count_launch();
+    if (nL > 0 && pl->nx >= 2 * BR_W && pl->dim == 3) {
+      const int64_t ns = (int64_t)2 * BR_W * pl->nz * pl->ny;
+      EB_TRY(dalloc(st, &pl->slab_class, ns));
+      EB_CUDA(cudaMemsetAsync(pl->slab_class, 0xFF, ns * 4, s));
+      int32_t* keep;
+      int64_t* kpos;
+      int64_t nK = 0;
+      EB_TRY(tmp.get(&keep, nL));
+      EB_TRY(tmp.get(&kpos, nL));
+      k_slab_scatter<<<nblk(nL, 256), 256, 0, s>>>(nL, pl->cellL, pl->classL, pl->nx, pl->ny, pl->nz, pl->slab_class,
+                                                   keep); eb::count_launch();
+      // uniform units: 32 y by BR_BZ z cells of one x layer, away from the y and z wall layers
+      const int org = R + 2;
+      pl->y_org = pl->z_org = org;
+      pl->y_hi = std::max(org, pl->ny - org);
+      pl->z_hi = std::max(org, pl->nz - org);
+      pl->nyb = std::max(1, (pl->y_hi - org + 31) / 32);
+      pl->nzb = std::max(1, (pl->z_hi - org + BR_BZ - 1) / BR_BZ);
+      const int64_t nu = (int64_t)2 * BR_W * pl->nzb * pl->nyb;
+      EB_TRY(dalloc(st, &pl->unit_class, nu));
+      k_brick_units<<<nblk(nu, 128), 128, 0, s>>>(pl->slab_class, pl->ny, pl->nz, pl->nyb, pl->nzb, pl->y_org,
+                                                  pl->z_org, pl->y_hi, pl->z_hi, pl->unit_class);
+      eb::count_launch();
+      k_brick_keep<<<nblk(nL, 256), 256, 0, s>>>(nL, pl->cellL, pl->nx, pl->ny, pl->nz, pl->nyb, pl->nzb, pl->y_org,
+                                                 pl->z_org, pl->y_hi, pl->z_hi, pl->unit_class, keep);
+      eb::count_launch();
+      EB_TRY(scan<int32_t>(keep, nL, kpos, &nK, s, tmp));
+      int32_t *cellK, *classK;
+      EB_TRY(dalloc(st, &cellK, std::max<int64_t>(nK, 1)));
+      EB_TRY(dalloc(st, &classK, std::max<int64_t>(nK, 1)));
+      k_compact_pair<<<nblk(nL, 256), 256, 0, s>>>(nL, keep, kpos, pl->cellL, pl->classL, cellK, classK);
+      eb::count_launch();
+      pl->cellL = cellK;
+      pl->classL = classK;
+      pl->nL = nK;
+      pl->brick = 1;
+    }
     const int64_t nk = n_class * (int64_t)st->nfoot;
     EB_TRY(dalloc(st, &pl->rowsK32, nk));
     EB_TRY(dalloc(st, &pl->rowsK64, nk));
@@ -1150,15 +1255,31 @@ static eb_status build_post(BuildCtx& c) {
   {
     std::vector<int32_t> hs(n_slots);
     EB_CUDA(cudaMemcpyAsync(hs.data(), status, n_slots * 4, cudaMemcpyDeviceToHost, s));
-    std::vector<int64_t> hf(n_slots);
-    EB_CUDA(cudaMemcpyAsync(hf.data(), st->slot_face, n_slots * 8, cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
-    int unbuilt = 0;
+    int unbuilt = 0, nbad = 0;
     for (int64_t i = 0; i < n_slots; ++i) {
-      if (hs[i] == 1) g_bad_faces.push_back(hf[i]);
+      if (hs[i] == 1) ++nbad;
       if (hs[i] == 2) unbuilt = 1;  // a row flagged by the row builder
     }
     if (unbuilt) { set_error("an LS row could not be built"); return EB_ERR_INVALID; }
+    if (nbad) {
+      // every face whose system failed: a class slot stands for all the faces of its class, so the
+      // faces are listed from the face -> slot maps (ascending global face id)
+      for (int d = 0; d < D; ++d) {
+        std::vector<int32_t> fs(dm.nface[d]);
+        EB_CUDA(cudaMemcpyAsync(fs.data(), st->face_slot[d], dm.nface[d] * 4, cudaMemcpyDeviceToHost, s));
+        EB_CUDA(cudaStreamSynchronize(s));
+        for (int64_t f = 0; f < dm.nface[d]; ++f)
+          if (fs[f] >= 0 && hs[fs[f]] == 1) g_bad_faces.push_back(dm.face_base[d] + f);
+      }
+      if (nc > 0) {
+        std::vector<int32_t> es(nc);
+        EB_CUDA(cudaMemcpyAsync(es.data(), st->eb_slot, nc * 4, cudaMemcpyDeviceToHost, s));
+        EB_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < nc; ++i)
+          if (es[i] >= 0 && hs[es[i]] == 1) g_bad_faces.push_back(dm.n_grid_faces + i);
+      }
+    }
     if (!g_bad_faces.empty()) {
       set_error("rank-deficient LS systems: " + std::to_string(g_bad_faces.size()) + " faces");
       return EB_ERR_RANK_DEFICIENT;
@@ -1425,6 +1546,30 @@ static eb_status build_post(BuildCtx& c) {
           }
       pl->zsym = dmax <= 64.0 * 2.220446049250313e-16 * mx;
       pl->zcube32.assign(pl->zcube64.begin(), pl->zcube64.end());
+      // reflection symmetry in x, y and z: T(a, b, c) = mean of c(+-a, +-b, +-c) over the sign images
+      const int F = L + 1;
+      pl->fold64.assign(F * F * F, 0.0);
+      double fmax = 0.0;
+      for (int c = 0; c <= L; ++c)
+        for (int b = 0; b <= L; ++b)
+          for (int a = 0; a <= L; ++a) {
+            double sum = 0.0;
+            int cnt = 0;
+            for (int sz = -1; sz <= 1; sz += 2)
+              for (int sy = -1; sy <= 1; sy += 2)
+                for (int sx = -1; sx <= 1; sx += 2) {
+                  sum += pl->cube64[(sx * a + L) + S * ((sy * b + L) + S * (sz * c + L))];
+                  ++cnt;
+                }
+            const double t = sum / cnt;
+            pl->fold64[a + F * (b + F * c)] = t;
+            for (int sz = -1; sz <= 1; sz += 2)
+              for (int sy = -1; sy <= 1; sy += 2)
+                for (int sx = -1; sx <= 1; sx += 2)
+                  fmax = std::max(fmax, fabs(pl->cube64[(sx * a + L) + S * ((sy * b + L) + S * (sz * c + L))] - t));
+          }
+      pl->fsym = fmax <= 64.0 * 2.220446049250313e-16 * mx;
+      pl->fold32.assign(pl->fold64.begin(), pl->fold64.end());
     }
     bool ok = dm.nbr_box && st->n_row_classes > 0;
     pl->tma32 = ok && (dm.n[0] % 4 == 0);
@@ -1655,6 +1800,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
       const_cast<eb_stencils*>(st)->mg = m;
     }
     mg = st->mg;
+    inf->precond_blocks = mg->nblk;
   }
   void* timer = o.check_every < 0 ? new_apply_timer() : nullptr;  // check_every < 0: time every Krylov apply
   set_apply_timer(timer);

@@ -6,6 +6,7 @@
 //       stored footprint-major so that consecutive rows load coalesced.
 // Covered cells get y = 0.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "eb_apply.cuh"
@@ -13,6 +14,8 @@
 #include "eb_apply_tma.cuh"
 #include "eb_apply_quad.cuh"
 #include "eb_apply_wall.cuh"
+#include "eb_apply_brick.cuh"
+#include "eb_apply_fold.cuh"
 
 #include <cuda.h>
 
@@ -163,26 +166,83 @@ static cudaError_t launch_runs(const ApplyArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
+static cudaError_t launch_brick(const ApplyArgs<T>& a, cudaStream_t st) {
+  const ApplyPlan* pl = a.plan;
+  BrickArgs<T> b;
+  b.nx = pl->nx;
+  b.ny = pl->ny;
+  b.nz = pl->nz;
+  b.nyb = pl->nyb;
+  b.nzb = pl->nzb;
+  b.y_org = pl->y_org;
+  b.z_org = pl->z_org;
+  b.y_hi = pl->y_hi;
+  b.z_hi = pl->z_hi;
+  b.unit_class = pl->unit_class;
+  if constexpr (sizeof(T) == 4) b.rowsK = pl->rowsK32;
+  else b.rowsK = pl->rowsK64;
+  b.nfoot = a.nfoot;
+  b.phi = a.phi;
+  b.y = a.y;
+  b.inv_kappa = a.inv_kappa;
+  b.kappa_weighted = a.kappa_weighted;
+  const unsigned grid = (unsigned)(2 * b.nyb * b.nzb);
+  cudaError_t e;
+  if (pl->R == 3) {
+    constexpr size_t sm = brick_smem<T, 3>();
+    if ((e = cudaFuncSetAttribute(k_wall_brick<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    k_wall_brick<T, 3><<<grid, BR_W * 32, sm, st>>>(b);
+  } else {
+    constexpr size_t sm = brick_smem<T, 2>();
+    if ((e = cudaFuncSetAttribute(k_wall_brick<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    k_wall_brick<T, 2><<<grid, BR_W * 32, sm, st>>>(b);
+  }
+  eb::count_launch();
+  return cudaGetLastError();
+}
+
+#ifndef EB_QUAD_PER_SM
+#define EB_QUAD_PER_SM 8  // CTAs per SM of the unique-row stream (0: one CTA per 128 rows)
+#endif
+
+// class cells outside the runs and the slab bricks: per-cell segment walk over the canonical rows
+template <typename T>
+static cudaError_t launch_seg_rest(const ApplyArgs<T>& a, cudaStream_t st) {
+  const ApplyPlan* pl = a.plan;
+  ApplyArgs<T> c = a;
+  c.n_irr = pl->nL;
+  c.irr_cell = pl->cellL;
+  c.irr_row = pl->classL;
+  const unsigned bc = (unsigned)((pl->nL + 255) / 256);
+  if (pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
+  else k_apply_irregular_seg<T, 2, 3><<<bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
+  eb::count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
   const ApplyPlan* pl = a.plan;
+  cudaError_t e;
   int64_t nb = (a.n_irr + 255) / 256;
   if (pl && pl->quad) {
-    // unique rows (HBM stream) in the quad layout, then the class rows (L2-resident, shared by the
-    // wall-layer cells) by the segment walk over the canonical rows
+    // unique rows (HBM stream) in the quad layout; without the x-runs (phi not 16-byte aligned) the class
+    // rows (L2-resident, shared by the wall-layer cells) follow by the segment walk over the canonical rows
     const QuadArgs<T> q = quad_args<T>(*pl);
-    const int64_t bu = (pl->nU + 127) / 128;
+    int64_t bu = (pl->nU + 127) / 128;
+    if (EB_QUAD_PER_SM > 0) bu = std::min<int64_t>(bu, (int64_t)pl->nsm * EB_QUAD_PER_SM);
     if (bu > 0) {
       if (pl->R == 3) k_irr_quad<T, 3, ApplyEpi><<<(unsigned)bu, 128, 0, st>>>(a, q, ApplyEpi());
       else k_irr_quad<T, 2, ApplyEpi><<<(unsigned)bu, 128, 0, st>>>(a, q, ApplyEpi());
       eb::count_launch();
     }
-    const bool runs = use_runs(a);  // the x-runs go on the template pass's stream
-    const int64_t nrest = runs ? pl->nL : pl->nC;
+    if (use_runs(a)) return cudaGetLastError();  // the class cells go on the template pass's stream
+    const int64_t nrest = pl->nC;
     if (nrest > 0) {
       ApplyArgs<T> c = a;
       c.n_irr = nrest;
-      c.irr_cell = runs ? pl->cellL : pl->cellC;
-      c.irr_row = runs ? pl->classL : pl->classC;
+      c.irr_cell = pl->cellC;
+      c.irr_row = pl->classC;
       const int64_t bc = (nrest + 255) / 256;
       if (pl->R == 3) k_apply_irregular_seg<T, 3, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
       else k_apply_irregular_seg<T, 2, 3><<<(unsigned)bc, 256, 0, st>>>(c, pl->nx, pl->ny, pl->nz);
@@ -276,10 +336,76 @@ static cudaError_t launch_tma(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaSt
   return cudaGetLastError();
 }
 
+// tensor map of phi for the staged planes (TT_OX + 2 TT_XH) x (TT_OY + 2L) of the template passes
+template <typename T, int L>
+static cudaError_t phi_map(const ApplyArgs<T>& a, const ApplyPlan& pl, CUtensorMap* map) {
+  constexpr int PX = TT_OX + 2 * TT_XH, PY = TT_OY + 2 * L;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t gdim[3] = {(cuuint64_t)pl.nx, (cuuint64_t)pl.ny, (cuuint64_t)pl.nz};
+  cuuint64_t gstr[2] = {(cuuint64_t)pl.nx * sizeof(T), (cuuint64_t)pl.nx * pl.ny * sizeof(T)};
+  cuuint32_t box[3] = {PX, PY, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                   (void*)a.phi, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+#ifndef EB_FOLD_PER_SM
+#define EB_FOLD_PER_SM 1  // persistent CTAs per SM of the folded template pass (0: as many as fit)
+#endif
+
+template <typename T, int R>
+static cudaError_t launch_fold(const ApplyArgs<T>& a, const ApplyPlan& pl, cudaStream_t s) {
+  constexpr int L = R + 1, F = L + 1;
+  static_assert(FD_OX == TT_OX && FD_PX == TT_OX + 2 * TT_XH, "staged plane of the tensor map");
+  CUtensorMap map;
+  cudaError_t e = phi_map<T, L>(a, pl, &map);
+  if (e != cudaSuccess) return e;
+  FoldCoef<T, R> cf;
+  for (int i = 0; i < F * F * F; ++i) cf.c[i] = sizeof(T) == 4 ? (T)pl.fold32[i] : (T)pl.fold64[i];
+  TmplArgs<T> ta;
+  ta.nx = pl.nx;
+  ta.ny = pl.ny;
+  ta.nz = pl.nz;
+  ta.ntx = (pl.nx + FD_OX - 1) / FD_OX;
+  ta.nty = (pl.ny + FD_OY - 1) / FD_OY;
+  ta.zchunk = 8;
+  ta.nzc = (pl.nz + ta.zchunk - 1) / ta.zchunk;
+  ta.items = (int64_t)ta.ntx * ta.nty * ta.nzc;
+  ta.kind = a.kind;
+  ta.inv_kappa = a.inv_kappa;
+  ta.y = a.y;
+  ta.kappa_weighted = a.kappa_weighted;
+  ta.err = pl.err;
+  constexpr size_t smem = fold_smem<T, R>();
+  auto kern = k_apply_fold<T, R>;
+  static int cached_dev = -1, cached_per_sm = 0;  // per device: attribute set, occupancy
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev != cached_dev) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_per_sm, kern, FD_THREADS, smem))) return e;
+    cached_dev = dev;
+  }
+  int per_sm = cached_per_sm > 0 ? cached_per_sm : 1;
+  if (EB_FOLD_PER_SM > 0 && per_sm > EB_FOLD_PER_SM) per_sm = EB_FOLD_PER_SM;
+  int64_t grid = (int64_t)pl.nsm * per_sm;
+  if (grid > ta.items) grid = ta.items;
+  kern<<<(unsigned)grid, FD_THREADS, smem, s>>>(map, cf, ta);
+  eb::count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_template_pass(const ApplyArgs<T>& a, cudaStream_t s) {
   const ApplyPlan* pl = a.plan;
   bool tma = pl && (sizeof(T) == 4 ? pl->tma32 : pl->tma64);
+  if (tma && pl->dim == 3 && pl->fsym) {
+    if (pl->R == 3) return launch_fold<T, 3>(a, *pl, s);
+    if (pl->R == 2) return launch_fold<T, 2>(a, *pl, s);
+  }
   if (tma) {
     if (pl->dim == 3 && pl->R == 3)
       return pl->zsym ? launch_tma<T, 3, 3, true>(a, *pl, s) : launch_tma<T, 3, 3, false>(a, *pl, s);
@@ -300,16 +426,22 @@ cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
   cudaError_t e;
   bool fork = pl && pl->side && a.n_irr > 0;
   if (fork) {
-    // the irregular rows run on the side stream, overlapped with the template pass (disjoint cells)
+    // the irregular rows run on the side stream, overlapped with the template pass (disjoint cells).
+    // The template pass is launched first: its persistent grid takes a few CTAs per SM and the
+    // HBM-bound row stream fills the rest of each SM, so the two run at the same time.
     if ((e = cudaEventRecord(pl->fork, s))) return e;
     if ((e = cudaStreamWaitEvent(pl->side, pl->fork, 0))) return e;
   }
+  if ((e = launch_template_pass<T>(a, s))) return e;
   if (a.n_irr > 0) {
     if ((e = launch_irregular<T>(a, fork ? pl->side : s))) return e;
   }
-  if ((e = launch_template_pass<T>(a, s))) return e;
   if (a.n_irr > 0 && use_runs(a)) {
+    // the wall-layer class cells (FMA-bound, rows L2-resident) follow the template pass on the main
+    // stream while the HBM-bound unique-row stream runs on the side stream
     if ((e = launch_runs<T>(a, s))) return e;
+    if (pl->brick && (e = launch_brick<T>(a, s))) return e;
+    if (pl->nL > 0 && (e = launch_seg_rest<T>(a, s))) return e;
   }
   if (fork) {
     if ((e = cudaEventRecord(pl->join, pl->side))) return e;

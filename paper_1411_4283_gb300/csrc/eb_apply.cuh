@@ -49,11 +49,20 @@ struct ApplyPlan {
   int32_t* classL = nullptr;     // [nL] their class row
   float* rowsK32 = nullptr;      // [n_class][nfoot] class rows, class-major
   double* rowsK64 = nullptr;
+  // the class cells outside the runs that lie in the 5 x layers next to each x wall, by x-slab brick
+  // (eb_apply_brick.cuh); cellL/classL then hold only the others
+  int brick = 0;
+  int32_t* slab_class = nullptr; // [2][5][nz][ny] class row of a slab cell, -1 otherwise
+  int32_t* unit_class = nullptr; // [2][5][nzb][nyb] class of a uniform brick unit, -1 otherwise
+  int nyb = 0, nzb = 0, y_org = 0, z_org = 0, y_hi = 0, z_hi = 0;
   std::vector<float> cube32;     // dense (2R+3)^3 template coefficients
   std::vector<double> cube64;
   int zsym = 0;                  // template symmetric in z (to a few ulps): z-folded template pass
   std::vector<float> zcube32;    // the cube with c(., ., a) = c(., ., -a) averaged (entries a >= 0 used)
   std::vector<double> zcube64;
+  int fsym = 0;                  // template even in x, y and z (to a few ulps): fully folded pass (3-D)
+  std::vector<float> fold32;     // T(a, b, c), a, b, c in 0..R+1: the mean of the cube's eight sign images
+  std::vector<double> fold64;
   int32_t* err;                  // device error word (bounded waits)
   cudaStream_t side;             // irregular pass runs here, overlapped with the template pass
   cudaEvent_t fork, join;

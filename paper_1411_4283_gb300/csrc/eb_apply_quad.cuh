@@ -161,26 +161,29 @@ __device__ T canonical_row(const ApplyArgs<T>& a, int64_t c, int64_t row) {
 }
 
 // Row sums (A x)_c over the unique-row cells; the epilogue decides what is stored.
+// Grid-stride over the rows (the stride is a multiple of 32, so a warp keeps 32 consecutive rows):
+// launched with a bounded grid, the pass leaves room on every SM for the template pass that runs
+// beside it.
 template <typename T, int R, class Epi>
 __global__ void __launch_bounds__(128) k_irr_quad(ApplyArgs<T> a, QuadArgs<T> qa, Epi epi) {
   using S = QuadShape<R>;
   constexpr int L = S::L;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= qa.nU) return;
-  const int64_t c = qa.cellU[t];
   const int nx = qa.nx, ny = qa.ny, nz = qa.nz;
-  const int cx = (int)(c % nx);
-  const int64_t cr = c / nx;
-  const int cy = (int)(cr % ny), cz = (int)(cr / ny);
-  T acc;
-  const bool edge = (cy <= L && cz <= L && cx < L) || (cy >= ny - 1 - L && cz >= nz - 1 - L && cx > nx - 1 - L);
-  if (edge) {
-    acc = canonical_row<T>(a, c, qa.n_class + t);
-  } else {
-    const T* q = qa.qU + (((t >> 5) * S::NQ) * 32 + (t & 31)) * 4;
-    acc = quad_row<T, R, 128>(q, a.phi, c, cy, cz, nx, ny, nz);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < qa.nU; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = qa.cellU[t];
+    const int cx = (int)(c % nx);
+    const int64_t cr = c / nx;
+    const int cy = (int)(cr % ny), cz = (int)(cr / ny);
+    T acc;
+    const bool edge = (cy <= L && cz <= L && cx < L) || (cy >= ny - 1 - L && cz >= nz - 1 - L && cx > nx - 1 - L);
+    if (edge) {
+      acc = canonical_row<T>(a, c, qa.n_class + t);
+    } else {
+      const T* q = qa.qU + (((t >> 5) * S::NQ) * 32 + (t & 31)) * 4;
+      acc = quad_row<T, R, 128>(q, a.phi, c, cy, cz, nx, ny, nz);
+    }
+    epi(a, t, c, acc);
   }
-  epi(a, t, c, acc);
 }
 
 template <typename T>

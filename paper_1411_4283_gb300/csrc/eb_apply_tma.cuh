@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(TT_THREADS) k_apply_tma(const __grid_constant_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  uint32_t parity = 0;  // bit p: parity of the next phase of slot p
+  uint32_t parity = 0;   // bit p: parity of the next phase of slot p
+  uint32_t pending = 0;  // bit p: slot p has a copy requested and not yet waited for
   bool failed = false;
   for (int64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
     const int zc = (int)(item % a.nzc);
@@ -155,24 +156,39 @@ __global__ void __launch_bounds__(TT_THREADS) k_apply_tma(const __grid_constant_
     for (int q = 0; q < NPRO; ++q) {
       int zz = D == 3 ? z0 - L + q : 0;
       int slot = D == 3 ? ((zz % NP) + NP) % NP : 0;
-      if (!mbar_wait(&bars[slot], (parity >> slot) & 1u)) failed = true;
-      parity ^= 1u << slot;
+      pending |= 1u << slot;
     }
+    for (int q = 0; q < NPRO; ++q) {
+      int zz = D == 3 ? z0 - L + q : 0;
+      int slot = D == 3 ? ((zz % NP) + NP) % NP : 0;
+      if (!mbar_wait(&bars[slot], (parity >> slot) & 1u)) { failed = true; break; }
+      parity ^= 1u << slot;
+      pending &= ~(1u << slot);
+    }
+    // every thread leaves together: a wait that gave up on any thread ends the CTA's work
+    if (__syncthreads_or(failed)) { failed = true; break; }
     for (int z = z0; z < z1; ++z) {
       if (D == 3) {
         // request plane z+L+1 for the next step into the slot of plane z-L-1 (released by the
         // barrier that ended the previous step), then wait for plane z+L (requested one step ago)
-        if (tid == 0 && z + 1 < z1) {
+        if (z + 1 < z1) {
           int zz = z + L + 1;
           int slot = (zz % NP + NP) % NP;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_expect_tx(&bars[slot], PBYTES);
-          tma_load_3d(ring + (size_t)slot * PLANE, &tmap, &bars[slot], x0 - TT_XH, y0 - L, zz);
+          if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bars[slot], PBYTES);
+            tma_load_3d(ring + (size_t)slot * PLANE, &tmap, &bars[slot], x0 - TT_XH, y0 - L, zz);
+          }
+          pending |= 1u << slot;
         }
         if (z > z0) {
           int slot = ((z + L) % NP + NP) % NP;
-          if (!mbar_wait(&bars[slot], (parity >> slot) & 1u)) failed = true;
-          parity ^= 1u << slot;
+          if (mbar_wait(&bars[slot], (parity >> slot) & 1u)) {
+            parity ^= 1u << slot;
+            pending &= ~(1u << slot);
+          } else {
+            failed = true;  // acted on at the barrier that ends this step, uniformly
+          }
         }
       }
       T acc[2][4];
@@ -235,11 +251,18 @@ __global__ void __launch_bounds__(TT_THREADS) k_apply_tma(const __grid_constant_
           else if (k == 0) a.y[c] = (T)0;
         }
       }
-      __syncthreads();  // every thread is done with plane z - L
+      // every thread is done with plane z - L; a wait that gave up on any thread ends the CTA's work
+      if (__syncthreads_or(failed)) { failed = true; break; }
     }
     if (failed) break;
   }
-  if (failed && tid == 0) atomicExch(a.err, 1);
+  if (failed) {
+    // failed is uniform across the CTA here.  Before the CTA exits, wait (bounded) for the copies
+    // still in flight into its shared memory, then report.
+    for (int p = 0; p < NP; ++p)
+      if ((pending >> p) & 1u) mbar_wait(&bars[p], (parity >> p) & 1u);
+    if (tid == 0) atomicExch(a.err, 1);
+  }
 }
 
 }  // namespace eb

@@ -48,6 +48,7 @@ struct NaSmem {
   double P[32 * NA_KST];
   double vec[5 * NA_MAXK];
 };
+static_assert(NA_WARPS_PER_CTA * sizeof(NaSmem) <= 232448, "dynamic shared memory of one CTA exceeds 227 KB");
 
 __device__ __forceinline__ double na_warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -222,7 +223,11 @@ __global__ void __launch_bounds__(NA_WARPS_PER_CTA * 32, 1)
 }
 
 // Device address of the fixed scratch, looked up once per device with that
-// device current (the symbol itself is only a host-side stand-in).
+// device current (the symbol itself is only a host-side stand-in).  The
+// address and the kernel attribute are cached for the life of the process: a
+// cudaDeviceReset (or any other teardown of the device's primary context)
+// invalidates them, so a process that resets a device must not call this
+// entry point on that device again.
 static std::mutex g_na_mutex;
 static void* g_na_ptr[128];
 static bool g_na_ready[128];

@@ -29,6 +29,9 @@ def parallel_stencils(geom, params, faces, bc_eb=None, procs: int | None = None)
         _init(geom, params, bc_eb)
         return dict(_work(faces))
     chunks = [faces[i::procs * 4] for i in range(procs * 4)]
+    # one BLAS thread per worker (inherited by the spawned processes before they load numpy)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs, initializer=_init, initargs=(geom, params, bc_eb)) as pool:
         out = {}

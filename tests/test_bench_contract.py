@@ -27,10 +27,26 @@ def test_reference_arm_prints_one_contract_line():
     d = json.loads(lines[0])
     assert KEYS <= set(d)
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == cb["host"]["nproc"] >= 1   # one oracle process per core
+    assert cb["host"]["uname_m"] and "lscpu_Architecture" in cb["host"] or "lscpu" in cb["host"]
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 def test_reference_arm_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_pick_tol_takes_the_loosest_target_within_the_error_bound():
+    sys.path.insert(0, ROOT)
+    import bench
+    errs = {1e-7: 3.0, 1e-8: 1.2, 1e-9: 1.005, 1e-10: 1.0, 1e-11: 1.0}
+    seen = []
+
+    def err(c):
+        seen.append(c)
+        return errs[c]
+    assert bench.pick_tol(err, 1.0) == 1e-9
+    assert seen == [1e-7, 1e-8, 1e-9]          # stops at the first (loosest) target that qualifies
+    assert bench.pick_tol(lambda c: 2.0, 1.0) == 1e-12
