@@ -268,6 +268,24 @@ enum { EB_TABLE_CELL_FLAG = 0, EB_TABLE_CUT_CELL = 1, EB_TABLE_VOL_MOM = 2, EB_T
 eb_status eb_geometry_table(const eb_geometry* g, int32_t which, int32_t dir, void* dst_host, int64_t cap_bytes,
                             int64_t* bytes);
 
+/* The objective J = 1/2 sum_v |V_v| phi_v^2 of a solution phi on the stencils
+ * st built from the device geometry g, and (dJ_host != NULL) its derivatives
+ * with respect to the radii of g's circles (dJ_host[n_body]), by the adjoint
+ * method, with phi the solution of kappa L phi = kappa rho for the Dirichlet
+ * problem with homogeneous data (Sec. 2.3): the adjoint solve
+ * (kappa L)^T lam = |V| phi (transposed operator, FP64), then
+ *   dJ/dr = sum_v (h^D phi_v^2 / 2 + lam_v) d kappa_v / dr
+ *           - lam^T (d (kappa L) / dr) phi,
+ * where kappa L changes through every stencil s = W (A^T W)^+ F whose rows
+ * or right-hand side hold moments of the moving boundary (Sec. 2.2.1): the
+ * reverse-mode derivative of each stencil solve with respect to A and F,
+ * contracted with the rows' and F's derivatives, which follow from the shape
+ * derivatives of the moment tables (recomputed on the device, not stored).
+ * The cut-cell and cut-face sets are held fixed.  2-D circles, Dirichlet EB.
+ * phi: [ncell] device (FP64).  Synchronises the stream. */
+eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* st, const double* phi, double* J_host,
+                           double* dJ_host, eb_stream_t stream);
+
 void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);
 const char* eb_last_error_message(void);

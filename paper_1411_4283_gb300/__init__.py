@@ -112,6 +112,7 @@ def load():
         "eb_geometry_circles": (i32, [i32, i32, P(dbl), P(dbl), i32, i32, P(_vp), P(EbGeom), _vp]),
         "eb_geometry_destroy": (None, [_vp]),
         "eb_geometry_table": (i32, [_vp, i32, i32, _vp, i64, P(i64)]),
+        "eb_adjoint_radii": (i32, [_vp, _vp, _vp, P(dbl), P(dbl), _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,7 +255,21 @@ def eb_geometry_circles(N, centers, radii, inside=False, moment_degree=4, stream
     _check(lib.eb_geometry_circles(int(N), len(r), c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                    r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(bool(inside)),
                                    int(moment_degree), ctypes.byref(h), ctypes.byref(desc), _stream(stream)))
-    return GpuGeometry(h, desc)
+    out = GpuGeometry(h, desc)
+    out.centers, out.radii = c, r
+    return out
+
+
+def eb_adjoint_radii(geom: "GpuGeometry", st: "Stencils", phi, gradient=True, stream=None):
+    """(J, dJ/dr) for J = 1/2 sum |V| phi^2 and the radii of the circles of a device geometry (see eb.h)."""
+    import torch
+    assert phi.dtype == torch.float64 and phi.is_cuda and phi.is_contiguous() and phi.numel() == st.ncell
+    J = ctypes.c_double()
+    nb = len(geom.radii)
+    dJ = (ctypes.c_double * max(nb, 1))()
+    _check(load().eb_adjoint_radii(geom.handle, st.handle, _ptr(phi), ctypes.byref(J), dJ if gradient else None,
+                                   _stream(stream)))
+    return J.value, (np.array([dJ[i] for i in range(nb)]) if gradient else None)
 
 
 class Stencils:
@@ -392,5 +407,5 @@ def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "GpuGeometry", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "GpuGeometry", "eb_adjoint_radii", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

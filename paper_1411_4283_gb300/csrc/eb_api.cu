@@ -1954,3 +1954,161 @@ eb_status eb_stencil_query(const eb_stencils* st, int64_t face, int32_t* n, int6
 }
 
 }  // extern "C"
+
+// ================================================================= adjoint with respect to the radii
+
+namespace eb {
+
+// rhs = kappa h^D phi (the gradient of J = 1/2 sum |V| phi^2) and v = (kappa h^D)^(1/2) phi (J = |v|^2 / 2)
+__global__ void k_adj_rhs(int64_t n, const uint8_t* flag, const double* kappa, const double* phi, double hd,
+                          double* rhs, double* v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double w = flag[i] ? kappa[i] * hd : 0.0;
+  rhs[i] = w * phi[i];
+  v[i] = sqrt(w) * phi[i];
+}
+
+__global__ void k_adj_rowmap(int64_t n_irr, const int32_t* irr_cell, const int32_t* irr_row, int32_t* row_of) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_irr) row_of[irr_cell[t]] = irr_row[t];
+}
+
+// sum over the cut cells of (h^D phi^2 / 2 + lam) d kappa (kappa = the zeroth volume moment)
+__global__ void k_adj_kappa(int64_t n_cut, const int32_t* cut_cell, const double* dvol, int KS, const double* phi,
+                            const double* lam, double hd, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (t < n_cut) {
+    const int32_t c = cut_cell[t];
+    v = (0.5 * hd * phi[c] * phi[c] + lam[c]) * dvol[t * KS];
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
+}
+
+}  // namespace eb
+
+extern "C" eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* st, const double* phi, double* J_host,
+                                      double* dJ_host, eb_stream_t stream) {
+  if (!g || !st || !phi || !J_host) { set_error("eb_adjoint_radii: null argument"); return EB_ERR_INVALID; }
+  g_err.clear();
+  const Dims& dm = st->dm;
+  if (dm.dim != 2) { set_error("eb_adjoint_radii: circles (2-D) only"); return EB_ERR_INVALID; }
+  if (!geometry_matches(g, dm.dim, dm.n, dm.n_cut)) {
+    set_error("eb_adjoint_radii: the stencils were not built from this geometry");
+    return EB_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = dm.ncell;
+  const double hd = pow(dm.h, dm.dim);
+  Tmp tmp;
+  tmp.s = s;
+  double *rhs, *v, *dscr;
+  EB_TRY(tmp.get(&rhs, n));
+  EB_TRY(tmp.get(&v, n));
+  EB_TRY(tmp.get(&dscr, 16));
+  k_adj_rhs<<<nblk(n, 256), 256, 0, s>>>(n, st->flag, st->kappa, phi, hd, rhs, v);
+  eb::count_launch();
+  double nv = 0.0;
+  EB_CUDA(norm2_64(n, v, dscr, &nv, s));
+  *J_host = 0.5 * nv * nv;
+  if (!dJ_host) return EB_OK;
+  // ---- adjoint solve (kappa L)^T lam = kappa h^D phi: BiCGStab on the transposed operator (gather
+  // form), Jacobi (the transpose has the same diagonal)
+  double *lam, *work;
+  int32_t* row_of;
+  EB_TRY(tmp.get(&lam, n));
+  EB_TRY(tmp.get(&work, 8 * n));
+  EB_TRY(tmp.get(&row_of, n));
+  EB_CUDA(cudaMemsetAsync(lam, 0, n * 8, s));
+  EB_CUDA(cudaMemsetAsync(row_of, 0xFF, n * 4, s));
+  if (st->n_irr > 0) {
+    k_adj_rowmap<<<nblk(st->n_irr, 256), 256, 0, s>>>(st->n_irr, st->irr_cell, st->irr_row, row_of);
+    eb::count_launch();
+  }
+  ApplyArgs<double> AT = apply_args<double>(st, 1);
+  AT.transpose = 1;
+  AT.row_of_cell = row_of;
+  AT.foot_d = st->foot_d;
+  AT.nx = dm.n[0];
+  AT.ny = dm.n[1];
+  AT.nz = dm.n[2];
+  int it = 0;
+  double rr = 0.0;
+  EB_CUDA(bicgstab<double>(AT, rhs, lam, st->dinv64, work, n, 1e-12, 20000, dscr, &it, &rr, s, nullptr));
+  if (!(rr <= 1e-10)) { set_error("eb_adjoint_radii: the adjoint solve did not converge"); return EB_ERR_NOT_CONVERGED; }
+  // ---- per radius: the kappa terms and the stencil-solve adjoints
+  Tables T;
+  if (!make_tables(dm.dim, dm.order, dm.mdeg, &T)) { set_error("table construction failed"); return EB_ERR_INVALID; }
+  LsArgs la;
+  memset(&la, 0, sizeof(la));
+  la.dm = dm;
+  la.flag = st->flag;
+  la.cut_of_cell = st->cut_of_cell;
+  la.cut_cell = st->cut_cell;
+  la.vol_mom = st->vol_mom;
+  la.eb_mom = st->eb_mom;
+  la.eb_nmom = st->eb_nmom;
+  la.eb_bc = st->eb_bc;
+  for (int d = 0; d < 3; ++d) {
+    la.cutface_of[d] = d < dm.dim ? st->cutface_of[d] : st->cutface_of[0];
+    la.face_mom[d] = d < dm.dim ? st->face_mom[d] : st->face_mom[0];
+  }
+  la.slot_face = st->slot_face;
+  la.row_ptr = st->row_ptr;
+  la.row_desc = st->row_desc;
+  int32_t *next, *lerr;
+  EB_TRY(tmp.get(&next, 1));
+  EB_TRY(tmp.get(&lerr, 1));
+  EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
+  la.err = lerr;
+  int dev = 0, nsm = 0;
+  EB_CUDA(cudaGetDevice(&dev));
+  EB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t nu = st->n_unique;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (nu + ADJ_WARPS - 1) / ADJ_WARPS));
+  double* scratch;
+  EB_TRY(tmp.get(&scratch, (size_t)blocks * ADJ_WARPS * MAXROWS * (2 * MAXK + 2)));
+  const int KS = dm.KS, KFS = dm.KFS, nc = dm.n_cut;
+  double *dvol, *deb, *debn, *dface[3] = {nullptr, nullptr, nullptr}, *acc;
+  EB_TRY(tmp.get(&dvol, (size_t)nc * KS));
+  EB_TRY(tmp.get(&deb, (size_t)nc * KS));
+  EB_TRY(tmp.get(&debn, (size_t)nc * dm.dim * KS));
+  for (int d = 0; d < dm.dim; ++d)
+    EB_TRY(tmp.get(&dface[d], (size_t)std::max<int64_t>(1, geometry_cutfaces(g, d)) * KFS));
+  const int nb = geometry_bodies(g);
+  EB_TRY(tmp.get(&acc, std::max(1, nb)));
+  EB_CUDA(cudaMemsetAsync(acc, 0, std::max(1, nb) * 8, s));
+  for (int b = 0; b < nb; ++b) {
+    EB_CUDA(geometry_radius_derivative(g, b, dvol, deb, debn, dface, s));
+    if (nc > 0) {
+      k_adj_kappa<<<nblk(nc, 256), 256, 0, s>>>(nc, st->cut_cell, dvol, KS, phi, lam, hd, acc + b);
+      eb::count_launch();
+    }
+    AdjArgs ga;
+    ga.lam = lam;
+    ga.phi = phi;
+    ga.dvol = dvol;
+    ga.deb = deb;
+    ga.debn = debn;
+    for (int d = 0; d < 3; ++d) ga.dface[d] = d < dm.dim ? dface[d] : dface[0];
+    ga.n_slots = nu;
+    ga.next = next;
+    ga.scratch = scratch;
+    ga.dJ = acc + b;
+    EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
+    if (nu > 0) {
+      EB_CUDA(stencil_adjoint_launch(blocks, s, la, T, ga));
+      eb::count_launch();
+    }
+  }
+  std::vector<double> h(std::max(1, nb));
+  int32_t herr = 0;
+  EB_CUDA(cudaMemcpyAsync(h.data(), acc, std::max(1, nb) * 8, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(&herr, lerr, 4, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  if (herr) { set_error("eb_adjoint_radii: a stencil system was singular in the adjoint"); return EB_ERR_RANK_DEFICIENT; }
+  for (int b = 0; b < nb; ++b) dJ_host[b] = h[b];
+  return EB_OK;
+}

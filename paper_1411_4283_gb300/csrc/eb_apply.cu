@@ -223,7 +223,6 @@ static cudaError_t launch_seg_rest(const ApplyArgs<T>& a, cudaStream_t st) {
 template <typename T>
 static cudaError_t launch_irregular(const ApplyArgs<T>& a, cudaStream_t st) {
   const ApplyPlan* pl = a.plan;
-  cudaError_t e;
   int64_t nb = (a.n_irr + 255) / 256;
   if (pl && pl->quad) {
     // unique rows (HBM stream) in the quad layout; without the x-runs (phi not 16-byte aligned) the class
@@ -420,8 +419,39 @@ static cudaError_t launch_template_pass(const ApplyArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// y_j = sum_i M_ij phi_i over the cells i whose footprint holds j (M = kappa L, or L when not
+// kappa-weighted: phi_i / kappa_i): the rows read in transposed order, one thread per output cell, no
+// atomics.  Covered cells get 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_transpose(ApplyArgs<T> a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.ncell) return;
+  if (a.kind[j] == 0) {
+    a.y[j] = (T)0;
+    return;
+  }
+  const int jx = (int)(j % a.nx), jy = (int)((j / a.nx) % a.ny), jz = (int)(j / ((int64_t)a.nx * a.ny));
+  T acc = 0;
+  for (int k = 0; k < a.nfoot; ++k) {
+    const int ix = jx - a.foot_d[3 * k], iy = jy - a.foot_d[3 * k + 1], iz = jz - a.foot_d[3 * k + 2];
+    if ((unsigned)ix >= (unsigned)a.nx || (unsigned)iy >= (unsigned)a.ny || (unsigned)iz >= (unsigned)a.nz) continue;
+    const int64_t i = ix + (int64_t)a.nx * (iy + (int64_t)a.ny * iz);
+    const uint8_t ki = a.kind[i];
+    if (ki == 0) continue;
+    const T m = ki == 1 ? a.tmpl[k] : a.rows[(int64_t)k * a.n_rows + a.row_of_cell[i]];
+    const T p = a.kappa_weighted ? a.phi[i] : a.phi[i] * (T)a.inv_kappa[i];
+    acc = fma(m, p, acc);
+  }
+  a.y[j] = acc;
+}
+
 template <typename T>
 cudaError_t launch_apply(const ApplyArgs<T>& a, cudaStream_t s) {
+  if (a.transpose) {
+    k_apply_transpose<T><<<(unsigned)((a.ncell + 255) / 256), 256, 0, s>>>(a);
+    eb::count_launch();
+    return cudaGetLastError();
+  }
   const ApplyPlan* pl = a.plan;
   cudaError_t e;
   bool fork = pl && pl->side && a.n_irr > 0;

@@ -26,6 +26,12 @@ struct ApplyArgs {
   int kappa_weighted;
   // fast template path (TMA tiles); null plan = generic kernels only
   const ApplyPlan* plan;
+  // transposed apply y = (kappa L)^T phi (or L^T phi) in gather form, for the adjoint solve: the row
+  // of every irregular cell (-1 elsewhere), the footprint offsets [nfoot][3] and the grid
+  int transpose = 0;
+  const int32_t* row_of_cell = nullptr;
+  const int8_t* foot_d = nullptr;
+  int nx = 0, ny = 0, nz = 0;
 };
 
 // Host-side launch plan of the apply, owned by eb_stencils.

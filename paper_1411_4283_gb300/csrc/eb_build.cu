@@ -1158,6 +1158,291 @@ cudaError_t lsq_prepare(size_t smem) {
   return cudaFuncSetAttribute(k_lsq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// ============================================================ 4c. adjoint of the stencil solves
+//
+// For J(s) with s_hat = W t, t the least-||t|| solution of B^T t = F, B = W A (Sec. 2.2.1), and sbar =
+// dJ/ds_hat, the reverse-mode derivative with respect to B and F is (y = G^-1 F, G = B^T B,
+// tbar = W sbar, z = G^-1 B^T tbar)
+//     Fbar = z,   Bbar = tbar y^T - B (z y^T + y z^T),
+// so a tangent (dB, dF) of the system changes J by
+//     sum_i [(tbar_i - b_i . z)(y . db_i) - (b_i . y)(z . db_i)] + z . dF.
+// Here J is the Lagrangian term -lam^T (kappa L) phi of the adjoint method: kappa L phi sums
+// (1/h^2) sigma s_hat_f . Phi over the faces of each volume (Sec. 2.3), so for face f with volume
+// columns c_i, sbar_i = -(sum_v sigma_v lam_v) phi_(c_i) / h^2 (boundary columns carry zero data).
+// The tangent rows come from the moment tables' derivatives through the same row construction (the
+// shift to x0 is linear; the row is normalised by its zeroth moment: d(m / m0) = (dm - m dm0 / m0) / m0).
+// One warp per system; G by lanes over its upper-triangle entries, its Cholesky factor in shared memory
+// (the adjoint needs about eight digits, which the normal equations keep for these systems).
+
+// weighted row b and its tangent db of one LS row (Dirichlet rows); returns the weight.  *col: the
+// cell of a volume row, -1 for a boundary row.
+__device__ double row_tangent(const LsArgs& a, const Tables& T, const AdjArgs& g, uint32_t desc, const int* base,
+                              const double* x0s, double* b, double* db, int64_t* col) {
+  const Dims& dm = a.dm;
+  const int K = T.K;
+  const int kind = rd_kind(desc);
+  int c[3], dl[3];
+  for (int d = 0; d < 3; ++d) {
+    dl[d] = d < dm.dim ? rd_off(desc, d) : 0;
+    c[d] = base[d] + dl[d];
+  }
+  const int64_t cid = cell_id(dm, c);
+  double delta[3];
+  for (int d = 0; d < 3; ++d) delta[d] = (double)dl[d] - x0s[d];
+  *col = kind == 0 ? cid : -1;
+  double m[MAXK], dmv[MAXK];
+  const double* src = nullptr;
+  const double* dsrc = nullptr;
+  double w;
+  if (kind == 2) {
+    const int wd = rd_wdir(desc), ws = rd_wside(desc);
+    delta[wd] += ws ? 0.5 : -0.5;
+    int fx[3] = {c[0], c[1], c[2]};
+    if (ws) fx[wd] += 1;
+    const int32_t cf = a.cutface_of[wd][face_local(dm, wd, fx)];
+    double r2 = 0.0;
+    for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
+    w = weight_of(dm, r2);
+    if (cf >= 0) {
+      const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
+      const double* dfm = g.dface[wd] + (int64_t)cf * dm.KFS;
+      for (int i = 0; i < K; ++i) {
+        m[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
+        dmv[i] = T.tang[wd][i] >= 0 ? dfm[T.tang[wd][i]] : 0.0;
+      }
+      src = m;
+      dsrc = dmv;
+    } else {
+      src = T.full_face[wd];
+    }
+  } else {
+    double r2 = 0.0;
+    for (int d = 0; d < dm.dim; ++d) r2 += delta[d] * delta[d];
+    w = weight_of(dm, r2);
+    const int32_t cut = a.cut_of_cell[cid];
+    if (kind == 1) {
+      src = a.eb_mom + (int64_t)cut * dm.KS;
+      dsrc = g.deb + (int64_t)cut * dm.KS;
+    } else if (cut >= 0) {
+      src = a.vol_mom + (int64_t)cut * dm.KS;
+      dsrc = g.dvol + (int64_t)cut * dm.KS;
+    } else {
+      src = T.full_vol;
+    }
+  }
+  double sm[MAXK];
+  shift_moments(T, src, delta, sm);
+  const double sc = w / sm[0];
+  if (dsrc) {
+    double sd[MAXK];
+    shift_moments(T, dsrc, delta, sd);
+    const double r0 = sd[0] / sm[0];
+    for (int i = 0; i < K; ++i) db[i] = sc * (sd[i] - r0 * sm[i]);
+  } else {
+    for (int i = 0; i < K; ++i) db[i] = 0.0;
+  }
+  for (int i = 0; i < K; ++i) b[i] = sc * sm[i];
+  return w;
+}
+
+__global__ void __launch_bounds__(ADJ_WARPS * 32)
+    k_stencil_adjoint(const __grid_constant__ LsArgs a, const __grid_constant__ Tables T, AdjArgs g) {
+  __shared__ double Gs[ADJ_WARPS][MAXK * MAXK];
+  __shared__ double vs[ADJ_WARPS][6 * MAXK];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* G = Gs[warp];
+  double* F = vs[warp];
+  double* dF = F + MAXK;
+  double* y = F + 2 * MAXK;
+  double* z = F + 3 * MAXK;
+  double* u = F + 4 * MAXK;
+  double* rinv = F + 5 * MAXK;
+  const Dims& dm = a.dm;
+  const int K = T.K;
+  const int E = K * (K + 1) / 2;
+  const int gw = blockIdx.x * ADJ_WARPS + warp;
+  double* sb = g.scratch + (int64_t)gw * MAXROWS * (2 * MAXK + 2);  // rows b, column-major
+  double* sdb = sb + (int64_t)MAXROWS * MAXK;                        // tangent rows
+  double* sw = sdb + (int64_t)MAXROWS * MAXK;                        // weights
+  int64_t* scol = reinterpret_cast<int64_t*>(sw + MAXROWS);          // columns
+  while (true) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(g.next, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= g.n_slots) break;
+    const int64_t p0 = a.row_ptr[s];
+    const int n = (int)(a.row_ptr[s + 1] - p0);
+    const int64_t gf = a.slot_face[s];
+    int base[3] = {0, 0, 0};
+    double x0s[3] = {0.0, 0.0, 0.0};
+    int dface = -1;
+    int64_t cut_self = -1, flocal = -1;
+    if (gf >= dm.n_grid_faces) {
+      cut_self = gf - dm.n_grid_faces;
+      cell_xyz(dm, a.cut_cell[cut_self], base);
+    } else {
+      for (int d = 0; d < dm.dim; ++d)
+        if (gf >= dm.face_base[d]) dface = d;
+      flocal = gf - dm.face_base[dface];
+      face_xyz(dm, dface, flocal, base);
+      x0s[dface] = -0.5;
+    }
+    if (n < K) continue;
+    // rows, tangents, weights, columns
+    int any_t = 0;
+    for (int i = lane; i < n; i += 32) {
+      double b[MAXK], db[MAXK];
+      int64_t col;
+      sw[i] = row_tangent(a, T, g, a.row_desc[p0 + i], base, x0s, b, db, &col);
+      scol[i] = col;
+      for (int k = 0; k < K; ++k) {
+        sb[(int64_t)k * MAXROWS + i] = b[k];
+        sdb[(int64_t)k * MAXROWS + i] = db[k];
+        any_t |= db[k] != 0.0;
+      }
+    }
+    // F and its tangent (Sec. 2.2.1): grid face p_d m_f^{p-e_d}; EB face sum_d p_d m_{d,f}^{p-e_d}
+    for (int i = lane; i < K; i += 32) {
+      double f = 0.0, df = 0.0;
+      if (cut_self >= 0) {
+        for (int d = 0; d < dm.dim; ++d) {
+          const int lo = T.lower[d][i];
+          if (lo < 0) continue;
+          const int64_t off = ((int64_t)cut_self * dm.dim + d) * dm.KS + lo;
+          f += (double)T.mon[i][d] * a.eb_nmom[off];
+          df += (double)T.mon[i][d] * g.debn[off];
+        }
+      } else {
+        const int q = T.lower[dface][i];
+        if (q >= 0) {
+          const int32_t cf = a.cutface_of[dface][flocal];
+          if (cf >= 0) {
+            if (T.tang[dface][q] >= 0) {
+              const int64_t off = (int64_t)cf * dm.KFS + T.tang[dface][q];
+              f = (double)T.mon[i][dface] * a.face_mom[dface][off];
+              df = (double)T.mon[i][dface] * g.dface[dface][off];
+            }
+          } else {
+            f = (double)T.mon[i][dface] * T.full_face[dface][q];
+          }
+        }
+      }
+      F[i] = f;
+      dF[i] = df;
+      any_t |= df != 0.0;
+    }
+    if (!__any_sync(0xffffffffu, any_t)) continue;  // this system does not move with the parameter
+    __syncwarp();
+    // G = B^T B (upper triangle, lanes over entries), then its Cholesky factor in place
+    for (int e = lane; e < E; e += 32) {
+      int j = 0, rem = e;
+      while (rem >= K - j) {
+        rem -= K - j;
+        ++j;
+      }
+      const int k = j + rem;
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) acc = fma(sb[(int64_t)j * MAXROWS + i], sb[(int64_t)k * MAXROWS + i], acc);
+      G[j * K + k] = acc;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < K; ++k) {
+      const double piv = G[k * K + k];
+      if (!(piv > 0.0)) {
+        ok = false;
+        break;
+      }
+      const double rk = sqrt(piv), ik = 1.0 / rk;
+      __syncwarp();
+      if (lane == 0) {
+        G[k * K + k] = rk;
+        rinv[k] = ik;
+      }
+      for (int j = k + 1 + lane; j < K; j += 32) G[k * K + j] *= ik;
+      __syncwarp();
+      for (int j = k + 1 + lane; j < K; j += 32) {
+        const double rkj = G[k * K + j];
+        for (int i = k + 1; i <= j; ++i) G[i * K + j] = fma(-G[k * K + i], rkj, G[i * K + j]);
+      }
+      __syncwarp();
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(a.err, 1);  // a system the forward build solved cannot be singular here
+      continue;
+    }
+    // y = G^-1 F and z = G^-1 B^T tbar, by one lane each (K <= 35: serial triangular solves)
+    double lam_face = 0.0;  // sum over the face's volumes of sigma lam
+    if (cut_self >= 0) {
+      lam_face = g.lam[a.cut_cell[cut_self]];
+    } else {
+      int lo[3] = {base[0], base[1], base[2]};
+      lo[dface] -= 1;
+      if (lo[dface] >= 0) {
+        const int64_t cl = cell_id(dm, lo);
+        if (a.flag[cl]) lam_face += g.lam[cl];
+      }
+      if (base[dface] < dm.n[dface]) {
+        const int64_t ch = cell_id(dm, base);
+        if (a.flag[ch]) lam_face -= g.lam[ch];
+      }
+    }
+    const double ih2 = 1.0 / (dm.h * dm.h);
+    for (int k = lane; k < K; k += 32) {  // u = B^T tbar, tbar_i = w_i sbar_i
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t col = scol[i];
+        if (col < 0) continue;
+        const double tb = sw[i] * (-lam_face * g.phi[col] * ih2);
+        acc = fma(sb[(int64_t)k * MAXROWS + i], tb, acc);
+      }
+      u[k] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        double* v = pass ? z : y;
+        const double* rhs = pass ? u : F;
+        for (int k = 0; k < K; ++k) {  // R^T w = rhs
+          double acc = rhs[k];
+          for (int j = 0; j < k; ++j) acc = fma(-G[j * K + k], v[j], acc);
+          v[k] = acc * rinv[k];
+        }
+        for (int k = K - 1; k >= 0; --k) {  // R v = w
+          double acc = v[k];
+          for (int j = k + 1; j < K; ++j) acc = fma(-G[k * K + j], v[j], acc);
+          v[k] = acc * rinv[k];
+        }
+      }
+    }
+    __syncwarp();
+    double dj = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      double by = 0.0, bz = 0.0, ydb = 0.0, zdb = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const double bk = sb[(int64_t)k * MAXROWS + i], dk = sdb[(int64_t)k * MAXROWS + i];
+        by = fma(bk, y[k], by);
+        bz = fma(bk, z[k], bz);
+        ydb = fma(y[k], dk, ydb);
+        zdb = fma(z[k], dk, zdb);
+      }
+      const int64_t col = scol[i];
+      const double tb = col >= 0 ? sw[i] * (-lam_face * g.phi[col] * ih2) : 0.0;
+      dj += (tb - bz) * ydb - by * zdb;
+    }
+    for (int k = lane; k < K; k += 32) dj = fma(z[k], dF[k], dj);
+    dj = warp_sum(dj);
+    if (lane == 0) atomicAdd(g.dJ, dj);
+    __syncwarp();
+  }
+}
+
+cudaError_t stencil_adjoint_launch(unsigned blocks, cudaStream_t s, const LsArgs& a, const Tables& T,
+                                   const AdjArgs& g) {
+  k_stencil_adjoint<<<blocks, ADJ_WARPS * 32, 0, s>>>(a, T, g);
+  return cudaGetLastError();
+}
+
 cudaError_t lsq_launch(unsigned blocks, size_t smem, cudaStream_t s, const LsArgs& a0, const Tables& T,
                        const LsArgs* batch, const int64_t* slot_base, int n_geom) {
   if (batch) k_lsq<true><<<blocks, LS_WARPS * 32, smem, s>>>(a0, T, batch, slot_base, n_geom);

@@ -115,6 +115,22 @@ __global__ void k_face_slots(Dims dm, int d, const int32_t* state, const int64_t
 __global__ void k_reach(Dims dm, const int32_t* cells, int64_t ncells, const uint8_t* flag, const uint8_t* ff0,
                         const uint8_t* ff1, const uint8_t* ff2, Mask* out);
 __global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* cut_cell);
+// Adjoint of the stencil solves with respect to the moment tables (k_stencil_adjoint, eb_build.cu)
+struct AdjArgs {
+  const double* lam;        // [ncell] adjoint solution
+  const double* phi;        // [ncell] forward solution
+  const double* dvol;       // [n_cut][KS] derivative of the volume moments
+  const double* deb;        // [n_cut][KS] of the EB moments
+  const double* debn;       // [n_cut][dim][KS] of the normal-weighted EB moments
+  const double* dface[3];   // [n_cutface[d]][KFS] of the face moments
+  int64_t n_slots;          // systems [0, n_slots) (the individually solved ones)
+  int32_t* next;            // work counter
+  double* scratch;          // per warp: MAXROWS * (2 MAXK + 2) doubles
+  double* dJ;               // accumulated derivative (one double)
+};
+constexpr int ADJ_WARPS = 4;
+cudaError_t stencil_adjoint_launch(unsigned blocks, cudaStream_t s, const LsArgs& a, const Tables& T,
+                                   const AdjArgs& g);
 // k_lsq launchers (eb_build.cu): shared-memory attribute, then one launch over the systems of one
 // geometry (batch == null) or of several (batch[g] per geometry, slot_base prefix sums of their systems)
 cudaError_t lsq_prepare(size_t smem);

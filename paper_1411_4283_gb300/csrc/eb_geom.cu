@@ -37,6 +37,13 @@
 struct eb_geometry {
   eb_geom desc;
   std::vector<void*> allocs;  // device arrays the descriptor points into
+  // the shape parameters and, per cell and per face, the body whose boundary cuts it (-1: none); the
+  // moment tables' shape derivatives are recomputed from these
+  int n_body = 0, inside = 0;
+  double centers[64][3] = {};
+  double radii[64] = {};
+  int32_t* cell_body = nullptr;     // [ncell]
+  int32_t* face_body[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace eb {
@@ -406,9 +413,212 @@ __global__ void k_geo_pack_idx(const int32_t* keep, const int64_t* pos, int64_t 
   if (t < n && keep[t]) dst[pos[t]] = src[t];
 }
 
+// ---------------------------------------------------------------- shape derivatives (radius)
+//
+// d/dr of the moment tables of the cells and faces cut by circle b, the fluid outside the circle (the
+// boundary moves with unit normal speed into the fluid as r grows); the cut sets are held fixed:
+//   volume moments  d/dr int_V xi^p dV / h^2 = - int_patch xi^p ds / h^2 = - eb / h   (transport);
+//   EB moments      the arc {c + r e(t)}: d/dr int f r dt = int (r grad f . e + f) dt
+//                   + f(t_b) r t_b' - f(t_a) r t_a', the ends sliding along the cell edges they lie on
+//                   (t' = cos t / (r sin t) on an x edge, -sin t / (r cos t) on a y edge); the normal
+//                   at fixed t does not turn;
+//   face moments    the covered chord |t - c_t| < s, s = (r^2 - d^2)^(1/2), grows at both ends with
+//                   speed r / s.
+__global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int body, const int32_t* __restrict__ cells,
+                                  int64_t n, const int32_t* __restrict__ cbody, const double* __restrict__ eb_mom,
+                                  int q, int K, double* dvol, double* deb, double* debn) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int c = cells[t];
+  double dv[28], de[28], dn[2][28];
+  for (int k = 0; k < K; ++k) dv[k] = de[k] = dn[0][k] = dn[1][k] = 0.0;
+  if (cbody[c] == body) {
+    const int ix = c % nx, iy = c / nx;
+    const double cx = (B.c[body][0] - (ix + 0.5) * h) / h, cy = (B.c[body][1] - (iy + 0.5) * h) / h;
+    const double R = B.r[body] / h;
+    // arc ends: angle, d(angle)/dR (R in units of h), sorted by angle
+    double ang[8], dang[8];
+    int na = 0;
+    for (int sd = -1; sd <= 1; sd += 2) {
+      const double e = 0.5 * sd;
+      double d2 = R * R - (e - cx) * (e - cx);
+      if (d2 > 0.0) {
+        const double w = sqrt(d2);
+        for (int u = -1; u <= 1; u += 2) {
+          const double yy = cy + u * w;
+          if (yy > -0.5 && yy < 0.5) {
+            const double th = atan2(yy - cy, e - cx);
+            ang[na] = th;
+            dang[na++] = cos(th) / (R * sin(th));
+          }
+        }
+      }
+      d2 = R * R - (e - cy) * (e - cy);
+      if (d2 > 0.0) {
+        const double w = sqrt(d2);
+        for (int u = -1; u <= 1; u += 2) {
+          const double xx = cx + u * w;
+          if (xx > -0.5 && xx < 0.5) {
+            const double th = atan2(e - cy, xx - cx);
+            ang[na] = th;
+            dang[na++] = -sin(th) / (R * cos(th));
+          }
+        }
+      }
+    }
+    for (int i = 1; i < na; ++i)
+      for (int j = i; j > 0 && ang[j] < ang[j - 1]; --j) {
+        double tmp = ang[j];
+        ang[j] = ang[j - 1];
+        ang[j - 1] = tmp;
+        tmp = dang[j];
+        dang[j] = dang[j - 1];
+        dang[j - 1] = tmp;
+      }
+    const double sgn = B.inside ? 1.0 : -1.0;  // normal out of the fluid
+    for (int i = 0; i < na; ++i) {
+      const double a = ang[i], e = i + 1 < na ? ang[i + 1] : ang[0] + 2.0 * M_PI;
+      const double da = dang[i], dE = i + 1 < na ? dang[i + 1] : dang[0];
+      if (e - a <= 0.0) continue;
+      const double m = 0.5 * (a + e);
+      const double px = cx + R * cos(m), py = cy + R * sin(m);
+      if (!(px > -0.5 && px < 0.5 && py > -0.5 && py < 0.5)) continue;
+      const int npc = (int)ceil((e - a) / (0.25 * M_PI));
+      const double span = (e - a) / npc;
+      for (int pc = 0; pc < npc; ++pc) {
+        const double mm = a + (pc + 0.5) * span, hw = 0.5 * span;
+        for (int g = 0; g < GEO_GL; ++g) {
+          const double th = mm + hw * gl.x[g], wt = gl.w[g] * hw;  // d theta
+          const double ct = cos(th), st = sin(th);
+          const double x = cx + R * ct, y = cy + R * st;
+          double xp[GEO_MAXQ + 1], yp[GEO_MAXQ + 1];
+          xp[0] = yp[0] = 1.0;
+          for (int k = 1; k <= q; ++k) {
+            xp[k] = xp[k - 1] * x;
+            yp[k] = yp[k - 1] * y;
+          }
+          for (int k = 0; k < K; ++k) {
+            int p0, p1;
+            mon2(k, &p0, &p1);
+            const double f = xp[p0] * yp[p1];
+            // R grad_xi f . e (the h of grad_x and of R cancel)
+            double ge = 0.0;
+            if (p0 > 0) ge += p0 * xp[p0 - 1] * yp[p1] * ct;
+            if (p1 > 0) ge += p1 * xp[p0] * yp[p1 - 1] * st;
+            const double v = wt * (R * ge + f);
+            de[k] += v;
+            dn[0][k] += v * sgn * ct;
+            dn[1][k] += v * sgn * st;
+          }
+        }
+      }
+      // ends: + f(t_b) R t_b' - f(t_a) R t_a'
+      for (int end = 0; end < 2; ++end) {
+        const double th = end ? e : a, dth = end ? dE : da, sg = end ? 1.0 : -1.0;
+        const double ct = cos(th), st = sin(th);
+        const double x = cx + R * ct, y = cy + R * st;
+        for (int k = 0; k < K; ++k) {
+          int p0, p1;
+          mon2(k, &p0, &p1);
+          const double v = sg * pow(x, p0) * pow(y, p1) * R * dth;
+          de[k] += v;
+          dn[0][k] += v * sgn * ct;
+          dn[1][k] += v * sgn * st;
+        }
+      }
+    }
+    // d/dr with r = h R: the tables above are d/dR; d/dr = (1/h) d/dR.  Volume: -eb / h.
+    for (int k = 0; k < K; ++k) {
+      dv[k] = (B.inside ? 1.0 : -1.0) * eb_mom[t * K + k] / h;
+      de[k] /= h;
+      dn[0][k] /= h;
+      dn[1][k] /= h;
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    dvol[t * K + k] = dv[k];
+    deb[t * K + k] = de[k];
+    debn[(t * 2 + 0) * K + k] = dn[0][k];
+    debn[(t * 2 + 1) * K + k] = dn[1][k];
+  }
+}
+
+__global__ void k_circle_faces_dr(Circles B, int nx, int dir, double h, int body, const int32_t* __restrict__ faces,
+                                  int64_t n, const int32_t* __restrict__ fbody, int q, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int f = faces[t];
+  double acc[GEO_MAXQ + 1];
+  for (int k = 0; k <= q; ++k) acc[k] = 0.0;
+  if (fbody[f] == body) {
+    const int mx = nx + (dir == 0), ix = f % mx, iy = f / mx;
+    const double fc[2] = {dir == 0 ? ix * h : (ix + 0.5) * h, dir == 1 ? iy * h : (iy + 0.5) * h};
+    const double dn = (fc[dir] - B.c[body][dir]) / h, ct = (B.c[body][1 - dir] - fc[1 - dir]) / h;
+    const double R = B.r[body] / h, s2 = R * R - dn * dn;
+    if (s2 > 0.0) {
+      const double s = sqrt(s2), speed = R / s;  // d(end)/dR for both chord ends
+      // outside fluid loses length at both ends; inside fluid gains it
+      const double sg = B.inside ? 1.0 : -1.0;
+      for (int e = -1; e <= 1; e += 2) {
+        const double end = ct + e * s;
+        if (end > -0.5 && end < 0.5) {
+          double p = 1.0;
+          for (int k = 0; k <= q; ++k) {
+            acc[k] += sg * p * speed;
+            p *= end;
+          }
+        }
+      }
+    }
+    for (int k = 0; k <= q; ++k) acc[k] /= h;
+  }
+  for (int k = 0; k <= q; ++k) out[t * (q + 1) + k] = acc[k];
+}
+
 }  // namespace eb
 
 using namespace eb;
+
+namespace eb {
+int geometry_bodies(const eb_geometry* g) { return g->n_body; }
+int64_t geometry_cutfaces(const eb_geometry* g, int d) { return g->desc.n_cutface[d]; }
+bool geometry_matches(const eb_geometry* g, int dim, const int* n, int n_cut) {
+  const eb_geom& d = g->desc;
+  return d.dim == dim && d.n[0] == n[0] && d.n[1] == n[1] && (dim < 3 || d.n[2] == n[2]) && d.n_cut == n_cut;
+}
+
+// d/dr of the moment tables of a device geometry for the radius of circle `body` (2-D), into caller
+// arrays laid out like the tables (dface[d]: [n_cutface[d]][K_F]); stream-ordered
+cudaError_t geometry_radius_derivative(const eb_geometry* g, int body, double* dvol, double* deb, double* debn,
+                                       double* const* dface, cudaStream_t s) {
+  static const GlRule gl = gl_rule();
+  const eb_geom& d = g->desc;
+  if (d.dim != 2 || body < 0 || body >= g->n_body) return cudaErrorInvalidValue;
+  Circles B;
+  B.n = g->n_body;
+  B.inside = g->inside;
+  for (int b = 0; b < g->n_body; ++b) {
+    B.c[b][0] = g->centers[b][0];
+    B.c[b][1] = g->centers[b][1];
+    B.r[b] = g->radii[b];
+  }
+  const int q = d.moment_degree, K = (q + 1) * (q + 2) / 2;
+  const int N = d.n[0];
+  const double h = d.h;
+  if (d.n_cut > 0) {
+    k_circle_cells_dr<<<(unsigned)((d.n_cut + 127) / 128), 128, 0, s>>>(B, gl, N, h, body, d.cut_cell, d.n_cut,
+                                                                       g->cell_body, d.eb_mom, q, K, dvol, deb, debn);
+    eb::count_launch();
+  }
+  for (int dir = 0; dir < 2; ++dir) {
+    if (d.n_cutface[dir] == 0) continue;
+    k_circle_faces_dr<<<(unsigned)((d.n_cutface[dir] + 127) / 128), 128, 0, s>>>(
+        B, N, dir, h, body, d.cutface[dir], d.n_cutface[dir], g->face_body[dir], q, dface[dir]);
+    eb::count_launch();
+  }
+  return cudaGetLastError();
+}
+}  // namespace eb
 
 namespace {
 
@@ -515,7 +725,8 @@ extern "C" eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double
     if ((e = (x)) != cudaSuccess) goto cuda_fail;  \
   } while (0)
     GEO_TRY(A.keep(&cflag, ncell));
-    GEO_TRY(A.temp(&cbody, ncell));
+    GEO_TRY(A.keep(&cbody, ncell));
+    G->cell_body = cbody;
     GEO_TRY(A.temp(&err, 1));
     GEO_TRY(cudaMemsetAsync(err, 0, 4, s));
     k_geo_classify2<<<nb256(ncell), 256, 0, s>>>(B, N, N, h, -1, ncell, cflag, cbody, err);
@@ -586,7 +797,8 @@ extern "C" eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double
       uint8_t* ff;
       int32_t* fbody;
       GEO_TRY(A.keep(&ff, nf));
-      GEO_TRY(A.temp(&fbody, nf));
+      GEO_TRY(A.keep(&fbody, nf));
+      G->face_body[d] = fbody;
       GEO_TRY(cudaMemsetAsync(err, 0, 4, s));
       k_geo_classify2<<<nb256(nf), 256, 0, s>>>(B, N, N, h, d, nf, ff, fbody, err);
       eb::count_launch();
@@ -650,6 +862,13 @@ extern "C" eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double
     return st;
   }
   G->desc = *desc;
+  G->n_body = n_body;
+  G->inside = B.inside;
+  for (int b = 0; b < n_body; ++b) {
+    G->centers[b][0] = B.c[b][0];
+    G->centers[b][1] = B.c[b][1];
+    G->radii[b] = B.r[b];
+  }
   *out = G;
   return EB_OK;
 }

@@ -13,7 +13,16 @@
 #include "eb_apply.cuh"
 #include "eb_mg.cuh"
 
+struct eb_geometry;
+
 namespace eb {
+
+// d/dr of a device geometry's moment tables for the radius of circle `body` (eb_geom.cu)
+cudaError_t geometry_radius_derivative(const eb_geometry* g, int body, double* dvol, double* deb, double* debn,
+                                       double* const* dface, cudaStream_t s);
+int geometry_bodies(const eb_geometry* g);
+int64_t geometry_cutfaces(const eb_geometry* g, int d);
+bool geometry_matches(const eb_geometry* g, int dim, const int* n, int n_cut);
 
 constexpr int MAXK = 35;        // monomials of degree <= 4 in 3-D
 constexpr int MAXK_STORE = 84;  // stored moment tables up to degree 6 in 3-D
