@@ -255,6 +255,16 @@ eb_status eb_lsq_batch_noalloc(const double* B, const double* w, const double* F
  * eb_geometry_destroy (which synchronises the device) after the last use of
  * desc. */
 typedef struct eb_geometry eb_geometry; /* opaque, library-owned */
+/* The same for the unit cube [0,1]^3 on an N^3 grid minus n_body spheres
+ * (centers_host [n_body][3]) or inside one sphere; moment_degree 0..4.  Face
+ * moments by the disk each sphere cuts from the face plane (closed form in
+ * one tangential coordinate, sin^2-mapped Gauss-Legendre in the other), EB
+ * moments by the sphere's area element R^2 sin(th) dth dphi on polar-angle
+ * panels split at the patch's tangencies, volume moments by the divergence
+ * theorem. */
+eb_status eb_geometry_spheres(int32_t N, int32_t n_body, const double* centers_host, const double* radii_host,
+                              int32_t inside, int32_t moment_degree, eb_geometry** out, eb_geom* desc,
+                              eb_stream_t stream);
 eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double* centers_host, const double* radii_host,
                               int32_t inside, int32_t moment_degree, eb_geometry** out, eb_geom* desc,
                               eb_stream_t stream);

@@ -111,6 +111,7 @@ def load():
         "eb_lsq_batch_noalloc": (i32, [_vp, _vp, _vp, _vp, i32, i32, i32, _vp, _vp, _vp]),
         "eb_geometry_circles": (i32, [i32, i32, P(dbl), P(dbl), i32, i32, P(_vp), P(EbGeom), _vp]),
         "eb_geometry_destroy": (None, [_vp]),
+        "eb_geometry_spheres": (i32, [i32, i32, P(dbl), P(dbl), i32, i32, P(_vp), P(EbGeom), _vp]),
         "eb_geometry_table": (i32, [_vp, i32, i32, _vp, i64, P(i64)]),
         "eb_adjoint_radii": (i32, [_vp, _vp, _vp, P(dbl), P(dbl), _vp]),
     }
@@ -243,6 +244,21 @@ class GpuGeometry:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.eb_geometry_destroy(self.handle)
             self.handle = None
+
+
+def eb_geometry_spheres(N, centers, radii, inside=False, moment_degree=4, stream=None) -> GpuGeometry:
+    """Moment tables of the unit cube minus spheres (or inside one sphere), computed on the device."""
+    lib = load()
+    c = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, 3))
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+    h = ctypes.c_void_p()
+    desc = EbGeom()
+    _check(lib.eb_geometry_spheres(int(N), len(r), c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(bool(inside)),
+                                   int(moment_degree), ctypes.byref(h), ctypes.byref(desc), _stream(stream)))
+    out = GpuGeometry(h, desc)
+    out.centers, out.radii = c, r
+    return out
 
 
 def eb_geometry_circles(N, centers, radii, inside=False, moment_degree=4, stream=None) -> GpuGeometry:
@@ -407,5 +423,5 @@ def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "GpuGeometry", "eb_adjoint_radii", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "eb_geometry_spheres", "GpuGeometry", "eb_adjoint_radii", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

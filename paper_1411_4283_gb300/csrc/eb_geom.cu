@@ -18,9 +18,11 @@
 //                   angle on pieces of at most pi/4: the integrand is a
 //                   trigonometric polynomial of low degree, integrated to
 //                   rounding; the normal points out of the fluid;
-//   volume moments  the divergence theorem with the x-derivative,
-//                   int_V xi^p = 1/(p_0+1) oint xi^(p+e_0) n_0: the fluid parts
-//                   of the two x edges in closed form and the arcs.
+//   volume moments  the divergence theorem, int_V xi^p = 1/(p_d+1) oint
+//                   xi^(p+e_d) n_d, in the direction d most tangent to the
+//                   boundary in the cell (so that a thin sliver is not the small
+//                   difference of terms of size one): the fluid parts of the two
+//                   edges normal to d in closed form and the arcs.
 // Cells whose volume fraction is at most 1e-14 count as covered and those at
 // least 1 - 1e-14 as full, faces likewise; a face next to a covered cell is
 // closed.  The lists of cut cells and cut faces are ascending.
@@ -59,14 +61,19 @@ struct Circles {
   double r[GEO_MAXB];
 };
 
-struct GlRule {
-  double x[GEO_GL], w[GEO_GL];  // nodes and weights on [-1, 1]
+template <int NG>
+struct GlRuleN {
+  double x[NG], w[NG];  // nodes and weights on [-1, 1]
 };
+using GlRule = GlRuleN<GEO_GL>;
+constexpr int GEO_GLT = 48;  // sin^2-mapped panels in the polar angle and along face chords
+using GlRuleT = GlRuleN<GEO_GLT>;
 
 // Gauss-Legendre rule by Newton's method on P_n (three-term recurrence), from the Chebyshev guesses
-static GlRule gl_rule() {
-  GlRule g;
-  const int n = GEO_GL;
+template <int NG = GEO_GL>
+static GlRuleN<NG> gl_rule() {
+  GlRuleN<NG> g;
+  const int n = NG;
   for (int i = 0; i < (n + 1) / 2; ++i) {
     double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
     for (int it = 0; it < 100; ++it) {
@@ -288,7 +295,11 @@ __global__ void k_circle_cells(Circles B, GlRule gl, int nx, double h, const int
     }
   }
   const double sgn = inside ? 1.0 : -1.0;  // normal out of the fluid: +radial inside the circle, -radial outside
-  double arcx[28];                         // int xi^(p + e_0) n_0 ds over the arcs
+  // divergence-theorem direction dd: the one most tangent to the boundary in this cell (the smaller
+  // component of the centre offset), so that a thin sliver of fluid along an edge is not the small
+  // difference of edge and arc terms of size one
+  const int dd = fabs(cx) <= fabs(cy) ? 0 : 1;
+  double arcx[28];                         // int xi^(p + e_dd) n_dd ds over the arcs
   for (int k = 0; k < K; ++k) arcx[k] = 0.0;
   for (int a = 0; a < narc; ++a) {
     const int npc = (int)ceil((arc1[a] - arc0[a]) / (0.25 * M_PI));
@@ -299,10 +310,12 @@ __global__ void k_circle_cells(Circles B, GlRule gl, int nx, double h, const int
         const double th = m + hw * gl.x[g], wt = gl.w[g] * hw * R;  // ds = R dtheta
         const double ct = cos(th), st = sin(th);
         const double x = cx + R * ct, y = cy + R * st, n0 = sgn * ct, n1 = sgn * st;
-        double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 1];
+        double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 2];
         xp[0] = yp[0] = 1.0;
-        for (int k = 1; k <= q + 1; ++k) xp[k] = xp[k - 1] * x;
-        for (int k = 1; k <= q; ++k) yp[k] = yp[k - 1] * y;
+        for (int k = 1; k <= q + 1; ++k) {
+          xp[k] = xp[k - 1] * x;
+          yp[k] = yp[k - 1] * y;
+        }
         for (int k = 0; k < K; ++k) {
           int p0, p1;
           mon2(k, &p0, &p1);
@@ -310,30 +323,31 @@ __global__ void k_circle_cells(Circles B, GlRule gl, int nx, double h, const int
           eb[k] += v;
           ebn[0][k] += v * n0;
           ebn[1][k] += v * n1;
-          arcx[k] += wt * xp[p0 + 1] * yp[p1] * n0;
+          arcx[k] += dd == 0 ? wt * xp[p0 + 1] * yp[p1] * n0 : wt * xp[p0] * yp[p1 + 1] * n1;
         }
       }
     }
   }
-  // ---- volume moments: x edges (fluid intervals, closed form) and the arcs
+  // ---- volume moments: the two edges normal to dd (fluid intervals, closed form) and the arcs
   for (int s = -1; s <= 1; s += 2) {
     const double e = 0.5 * s;
     double ia[2], ib[2];
-    const int ni = fluid_intervals(e - cx, cy, R, inside, ia, ib);
+    const int ni = dd == 0 ? fluid_intervals(e - cx, cy, R, inside, ia, ib) : fluid_intervals(e - cy, cx, R, inside, ia, ib);
     for (int j = 0; j < ni; ++j) {
       double sp[GEO_MAXQ + 1];
       seg_powers(ia[j], ib[j], q, sp);
       for (int k = 0; k < K; ++k) {
         int p0, p1;
         mon2(k, &p0, &p1);
-        vol[k] += s * pow(e, p0 + 1) * sp[p1];  // n_0 = s on the edge x = s/2
+        // n_dd = s on the edge xi_dd = s/2; the tangential exponent is the other one
+        vol[k] += dd == 0 ? s * pow(e, p0 + 1) * sp[p1] : s * pow(e, p1 + 1) * sp[p0];
       }
     }
   }
   for (int k = 0; k < K; ++k) {
     int p0, p1;
     mon2(k, &p0, &p1);
-    vol[k] = (vol[k] + arcx[k]) / (p0 + 1);
+    vol[k] = (vol[k] + arcx[k]) / ((dd == 0 ? p0 : p1) + 1);
   }
   for (int k = 0; k < K; ++k) {
     o.vol[t * K + k] = vol[k];
@@ -575,6 +589,426 @@ __global__ void k_circle_faces_dr(Circles B, int nx, int dir, double h, int body
   for (int k = 0; k <= q; ++k) out[t * (q + 1) + k] = acc[k];
 }
 
+// ---------------------------------------------------------------- 3-D: the cube minus spheres
+//
+// Face moments: the fluid part of a face square is the square minus (inside fluid: intersected with)
+// the disk the sphere cuts from the face plane; in tangential coordinates (u, v) the disk's chord at u
+// is |v - c_v| < (rho^2 - (u - c_u)^2)^(1/2): the v-integral in closed form, the u-integral by
+// Gauss-Legendre on panels split where the chord ends cross v = +-1/2 and mapped by
+// u = a + (b - a) sin^2(pi s / 2), which flattens the square-root behaviour at the disk's edge.
+// EB moments: the area element of a sphere in (z, phi) is R dz dphi (Archimedes); at each z the patch
+// is the arcs of the circle of radius (R^2 - (z - c_z)^2)^(1/2) inside the cell's x-y square.  The
+// outer integral runs over the polar angle th (z = c_z + R cos th, dA = R^2 sin th dth dphi), split
+// where the arcs change (tangencies with the square's edge lines and corners) and mapped by the same
+// sin^2 substitution with 48 points per panel: in z the circle's radius has a square-root branch at
+// the poles, which slows convergence in the cells next to them; in th it is R sin th.  Volume moments: the divergence theorem with the
+// x-derivative, int_V xi^p = 1/(p_0+1) oint xi^(p+e_0) n_0 dA, over the two x faces' fluid parts and
+// the patch.
+
+struct Spheres {
+  int n, inside;
+  double c[GEO_MAXB][3];
+  double r[GEO_MAXB];
+};
+
+__device__ __forceinline__ void box_dist3(const double* c, const double* lo, const double* hi, double* dmin,
+                                          double* dmax) {
+  double a = 0.0, b = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double n = fmin(fmax(c[d], lo[d]), hi[d]) - c[d];
+    const double f = fmax(fabs(c[d] - lo[d]), fabs(c[d] - hi[d]));
+    a += n * n;
+    b += f * f;
+  }
+  *dmin = sqrt(a);
+  *dmax = sqrt(b);
+}
+
+__device__ int classify_box3(const Spheres& B, const double* lo, const double* hi, int* body) {
+  *body = -1;
+  if (B.n == 0) return 1;
+  double dmin, dmax;
+  if (B.inside) {
+    box_dist3(B.c[0], lo, hi, &dmin, &dmax);
+    if (dmax <= B.r[0]) return 1;
+    if (dmin >= B.r[0]) return 0;
+    *body = 0;
+    return 2;
+  }
+  int ncut = 0;
+  for (int b = 0; b < B.n; ++b) {
+    box_dist3(B.c[b], lo, hi, &dmin, &dmax);
+    if (dmax <= B.r[b]) {
+      *body = -1;
+      return 0;
+    }
+    if (dmin < B.r[b]) {
+      ++ncut;
+      *body = b;
+    }
+  }
+  if (ncut > 1) return 3;
+  return ncut ? 2 : 1;
+}
+
+__global__ void k_geo_classify3(Spheres B, int N, double h, int dir, int64_t n, uint8_t* flag, int32_t* body,
+                                int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m0 = N + (dir == 0), m1 = N + (dir == 1);
+  const int ix = (int)(i % m0), iy = (int)((i / m0) % m1), iz = (int)(i / ((int64_t)m0 * m1));
+  double lo[3] = {ix * h, iy * h, iz * h}, hi[3] = {(ix + 1) * h, (iy + 1) * h, (iz + 1) * h};
+  if (dir >= 0) hi[dir] = lo[dir];
+  int b;
+  int f = classify_box3(B, lo, hi, &b);
+  if (f == 3) {
+    atomicExch(err, 1);
+    f = 2;
+  }
+  flag[i] = (uint8_t)f;
+  body[i] = b;
+}
+
+// graded monomials of degree <= q in 3-D: degree by degree, p0 descending, then p1 descending
+__device__ __forceinline__ void mon3(int i, int* p) {
+  int q = 0;
+  while (i >= (q + 1) * (q + 2) / 2) {
+    i -= (q + 1) * (q + 2) / 2;
+    ++q;
+  }
+  int a = 0;  // within degree q: p0 = q - a, then p1 from a down to 0
+  while (i > a) {
+    i -= a + 1;
+    ++a;
+  }
+  p[0] = q - a;
+  p[1] = a - i;
+  p[2] = i;
+}
+
+__device__ __forceinline__ void sort_small(double* v, int n) {
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && v[j] < v[j - 1]; --j) {
+      const double t = v[j];
+      v[j] = v[j - 1];
+      v[j - 1] = t;
+    }
+}
+
+// arcs of the circle (cx, cy, rho) inside the square [-1/2, 1/2]^2: angle intervals; returns the count
+__device__ int square_arcs(double cx, double cy, double rho, double* a0, double* a1) {
+  double ang[8];
+  int na = 0;
+  for (int s = -1; s <= 1; s += 2) {
+    const double e = 0.5 * s;
+    double d2 = rho * rho - (e - cx) * (e - cx);
+    if (d2 >= 0.0) {
+      const double w = sqrt(d2);
+      for (int u = -1; u <= 1; u += 2) {
+        const double yy = cy + u * w;
+        if (yy >= -0.5 && yy <= 0.5) ang[na++] = atan2(yy - cy, e - cx);
+      }
+    }
+    d2 = rho * rho - (e - cy) * (e - cy);
+    if (d2 >= 0.0) {
+      const double w = sqrt(d2);
+      for (int u = -1; u <= 1; u += 2) {
+        const double xx = cx + u * w;
+        if (xx >= -0.5 && xx <= 0.5) ang[na++] = atan2(e - cy, xx - cx);
+      }
+    }
+  }
+  if (na == 0) {  // the circle lies inside the square, or outside it (or around it)
+    if (cx - rho > -0.5 && cx + rho < 0.5 && cy - rho > -0.5 && cy + rho < 0.5) {
+      a0[0] = -M_PI;
+      a1[0] = M_PI;
+      return 1;
+    }
+    return 0;
+  }
+  sort_small(ang, na);
+  int narc = 0;
+  for (int i = 0; i < na; ++i) {
+    const double a = ang[i], e = i + 1 < na ? ang[i + 1] : ang[0] + 2.0 * M_PI;
+    if (e - a <= 0.0) continue;
+    const double m = 0.5 * (a + e);
+    const double px = cx + rho * cos(m), py = cy + rho * sin(m);
+    if (px > -0.5 && px < 0.5 && py > -0.5 && py < 0.5) {
+      a0[narc] = a;
+      a1[narc] = e;
+      ++narc;
+    }
+  }
+  return narc;
+}
+
+// sin^2-mapped Gauss-Legendre node g on the panel [a, b]: position and weight
+__device__ __forceinline__ void sin2_node(const GlRuleT& gl, int g, double a, double b, double* t, double* w) {
+  const double s = 0.5 * gl.x[g] + 0.5;
+  const double sn = sin(0.5 * M_PI * s), cs = cos(0.5 * M_PI * s);
+  *t = a + (b - a) * sn * sn;
+  *w = 0.5 * gl.w[g] * (b - a) * M_PI * sn * cs;
+}
+
+// moments int u^a v^b over the fluid part of the square [-1/2,1/2]^2 of a plane the sphere cuts in the
+// disk (cu, cv, rho) (rho <= 0: no disk), for the graded 2-D monomials of degree <= q; disk[] holds the
+// quadrature over the disk's u-range of the chord (inside fluid) or of the column minus the chord
+__device__ void disk_square(double cu, double cv, double rho, int inside, int q, const GlRuleT& gl, double* out) {
+  const int K2 = (q + 1) * (q + 2) / 2;
+  double su[GEO_MAXQ + 2], sv[GEO_MAXQ + 2];
+  seg_powers(-0.5, 0.5, q, su);
+  seg_powers(-0.5, 0.5, q, sv);
+  double disk[28];
+  int pa[28], pb[28];
+  for (int k = 0; k < K2; ++k) {
+    disk[k] = 0.0;
+    mon2(k, &pa[k], &pb[k]);
+  }
+  const double lo = fmax(-0.5, cu - rho), hi = fmin(0.5, cu + rho);
+  if (rho > 0.0 && hi > lo) {
+    double br[6];
+    int nb = 0;
+    br[nb++] = lo;
+    br[nb++] = hi;
+    for (int e = -1; e <= 1; e += 2) {
+      const double dv = 0.5 * e - cv;
+      if (fabs(dv) < rho) {
+        const double w = sqrt(rho * rho - dv * dv);
+        for (int sg = -1; sg <= 1; sg += 2) {
+          const double uu = cu + sg * w;
+          if (uu > lo && uu < hi) br[nb++] = uu;
+        }
+      }
+    }
+    sort_small(br, nb);
+    for (int pnl = 0; pnl + 1 < nb; ++pnl) {
+      if (br[pnl + 1] <= br[pnl]) continue;
+      for (int g = 0; g < GEO_GLT; ++g) {
+        double u, wu;
+        sin2_node(gl, g, br[pnl], br[pnl + 1], &u, &wu);
+        const double hw = sqrt(fmax(rho * rho - (u - cu) * (u - cu), 0.0));
+        const double va = fmin(fmax(cv - hw, -0.5), 0.5), vb = fmin(fmax(cv + hw, -0.5), 0.5);
+        double vp[GEO_MAXQ + 2];
+        if (inside) {
+          seg_powers(va, vb, q, vp);
+        } else {  // [-1/2, va] and [vb, 1/2]
+          double v1[GEO_MAXQ + 2], v2[GEO_MAXQ + 2];
+          seg_powers(-0.5, va, q, v1);
+          seg_powers(vb, 0.5, q, v2);
+          for (int k = 0; k <= q; ++k) vp[k] = v1[k] + v2[k];
+        }
+        double up = 1.0, upow[GEO_MAXQ + 1];
+        for (int k = 0; k <= q; ++k) {
+          upow[k] = up;
+          up *= u;
+        }
+        for (int k = 0; k < K2; ++k) disk[k] += wu * upow[pa[k]] * vp[pb[k]];
+      }
+    }
+  }
+  if (inside) {
+    for (int k = 0; k < K2; ++k) out[k] = disk[k];
+    return;
+  }
+  // outside fluid, integrated directly (a nearly closed face is not the small difference of the square
+  // and the disk): the full columns outside the disk's u-range in closed form, and inside it the parts
+  // of the column outside the chord
+  double full[28];
+  for (int k = 0; k < K2; ++k) full[k] = 0.0;
+  {
+    double ua[2], ub[2];
+    int nu = 0;
+    if (!(rho > 0.0) || hi <= lo) {
+      ua[0] = -0.5;
+      ub[0] = 0.5;
+      nu = 1;
+    } else {
+      if (lo > -0.5) { ua[nu] = -0.5; ub[nu] = lo; ++nu; }
+      if (hi < 0.5) { ua[nu] = hi; ub[nu] = 0.5; ++nu; }
+    }
+    for (int j = 0; j < nu; ++j) {
+      double up2[GEO_MAXQ + 2];
+      seg_powers(ua[j], ub[j], q, up2);
+      for (int k = 0; k < K2; ++k) full[k] += up2[pa[k]] * sv[pb[k]];
+    }
+  }
+  for (int k = 0; k < K2; ++k) out[k] = full[k] + disk[k];
+}
+
+// one table of a cut cell's EB patch integrals (thread per cell and table): t = 0 int xi^p dA, t = 1..3
+// int xi^p n_(t-1) dA, t = 4 int xi^(p+e_d) n_d dA (the patch part of the volume moments, d the cell's
+// divergence direction); divided by h^2
+__global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double h, const int32_t* __restrict__ cells, int64_t n,
+                               const int32_t* __restrict__ cbody, int q, int K, double* eb, double* ebn,
+                               double* volp) {
+  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= 5 * n) return;
+  const int64_t t = tt / 5;
+  const int table = (int)(tt % 5);
+  const int c = cells[t];
+  const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
+  const int b = cbody[c];
+  const double cx = (B.c[b][0] - (ix + 0.5) * h) / h, cy = (B.c[b][1] - (iy + 0.5) * h) / h;
+  const double cz = (B.c[b][2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
+  const double sgn = B.inside ? 1.0 : -1.0;  // normal out of the fluid: sgn (x - c) / R
+  // divergence-theorem direction (table 4): the smallest component of the centre offset, the direction
+  // most tangent to the patch (see k_sphere_vol)
+  const int dd = (fabs(cx) <= fabs(cy) && fabs(cx) <= fabs(cz)) ? 0 : (fabs(cy) <= fabs(cz) ? 1 : 2);
+  double acc[35];
+  int pk[35];  // exponents of monomial k, packed p0 | p1 << 4 | p2 << 8
+  for (int k = 0; k < K; ++k) {
+    int p[3];
+    mon3(k, p);
+    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
+    acc[k] = 0.0;
+  }
+  // z breakpoints: the range ends, tangencies with the edge lines x, y = +-1/2 and passes through the
+  // square's corners
+  const double zl = fmax(-0.5, cz - R), zh = fmin(0.5, cz + R);
+  double br[20];
+  int nb = 0;
+  br[nb++] = zl;
+  br[nb++] = zh;
+  for (int e = -1; e <= 1; e += 2) {
+    const double dd[2] = {(0.5 * e - cx) * (0.5 * e - cx), (0.5 * e - cy) * (0.5 * e - cy)};
+    for (int j = 0; j < 2; ++j) {
+      const double qq = R * R - dd[j];
+      if (qq > 0.0)
+        for (int sg = -1; sg <= 1; sg += 2) {
+          const double zz = cz + sg * sqrt(qq);
+          if (zz > zl && zz < zh) br[nb++] = zz;
+        }
+    }
+    for (int e2 = -1; e2 <= 1; e2 += 2) {
+      const double qq = R * R - (0.5 * e - cx) * (0.5 * e - cx) - (0.5 * e2 - cy) * (0.5 * e2 - cy);
+      if (qq > 0.0)
+        for (int sg = -1; sg <= 1; sg += 2) {
+          const double zz = cz + sg * sqrt(qq);
+          if (zz > zl && zz < zh) br[nb++] = zz;
+        }
+    }
+  }
+  // the z breakpoints as polar angles from the +z axis: z = cz + R cos(th), rho = R sin(th), and
+  // dA = R dz dphi = R^2 sin(th) dth dphi; the angle keeps the integrand analytic up to the poles
+  // (rho = (R^2 - (z - cz)^2)^(1/2) is not at z = cz +- R)
+  for (int i = 0; i < nb; ++i) br[i] = acos(fmin(1.0, fmax(-1.0, (br[i] - cz) / R)));
+  sort_small(br, nb);
+  for (int pnl = 0; pnl + 1 < nb; ++pnl) {
+    if (br[pnl + 1] <= br[pnl]) continue;
+    for (int gz = 0; gz < GEO_GLT; ++gz) {
+      double th, wth;
+      sin2_node(glt, gz, br[pnl], br[pnl + 1], &th, &wth);
+      const double z = cz + R * cos(th), rho = R * sin(th);
+      const double wz = wth * rho;  // R dz = R^2 sin(th) dth: the factor R is applied with dphi below
+      if (rho <= 0.0) continue;
+      double a0[4], a1[4];
+      const int narc = square_arcs(cx, cy, rho, a0, a1);
+      double zp[GEO_MAXQ + 2];
+      zp[0] = 1.0;
+      for (int k = 1; k <= q + 1; ++k) zp[k] = zp[k - 1] * z;
+      for (int a = 0; a < narc; ++a) {
+        const int npc = (int)ceil((a1[a] - a0[a]) / (0.25 * M_PI));
+        const double span = (a1[a] - a0[a]) / npc;
+        for (int pc = 0; pc < npc; ++pc) {
+          const double mm = a0[a] + (pc + 0.5) * span, hw = 0.5 * span;
+          for (int g = 0; g < GEO_GL; ++g) {
+            const double ph = mm + hw * gl.x[g];
+            const double w = wz * gl.w[g] * hw * R;  // dA = R dz dphi
+            const double cp = cos(ph), sp = sin(ph);
+            const double x = cx + rho * cp, y = cy + rho * sp;
+            double f = w;
+            if (table >= 1 && table <= 3) {
+              const double e = table == 1 ? rho * cp : (table == 2 ? rho * sp : z - cz);
+              f *= sgn * e / R;
+            } else if (table == 4) {
+              f *= sgn * (dd == 0 ? rho * cp : (dd == 1 ? rho * sp : z - cz)) / R;
+            }
+            double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 2];
+            xp[0] = yp[0] = 1.0;
+            for (int k = 1; k <= q + 1; ++k) {
+              xp[k] = xp[k - 1] * x;
+              yp[k] = yp[k - 1] * y;
+            }
+            const int ex = table == 4 && dd == 0, ey = table == 4 && dd == 1, ez = table == 4 && dd == 2;
+            for (int k = 0; k < K; ++k)
+              acc[k] += f * xp[(pk[k] & 15) + ex] * yp[((pk[k] >> 4) & 15) + ey] * zp[(pk[k] >> 8) + ez];
+          }
+        }
+      }
+    }
+  }
+  double* dst = table == 0 ? eb + t * K : (table == 4 ? volp + t * K : ebn + (t * 3 + table - 1) * K);
+  for (int k = 0; k < K; ++k) dst[k] = acc[k];
+}
+
+// volume moments from the patch part and the two x faces' fluid parts (thread per cell)
+__global__ void k_sphere_vol(Spheres B, GlRuleT gl, int N, double h, const int32_t* __restrict__ cells, int64_t n,
+                             const int32_t* __restrict__ cbody, int q, int K, const double* __restrict__ volp,
+                             double* vol) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int c = cells[t];
+  const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
+  const int b = cbody[c];
+  const double cx = (B.c[b][0] - (ix + 0.5) * h) / h, cy = (B.c[b][1] - (iy + 0.5) * h) / h;
+  const double cz = (B.c[b][2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
+  // the direction most tangent to the patch (as in k_sphere_patch) and the two faces normal to it
+  const double cc[3] = {cx, cy, cz};
+  const int dd = (fabs(cx) <= fabs(cy) && fabs(cx) <= fabs(cz)) ? 0 : (fabs(cy) <= fabs(cz) ? 1 : 2);
+  const int u = dd == 0 ? 1 : 0, v = dd == 2 ? 1 : 2;
+  double acc[35];
+  for (int k = 0; k < K; ++k) acc[k] = volp[t * K + k];
+  for (int s = -1; s <= 1; s += 2) {
+    const double xe = 0.5 * s, d2 = R * R - (xe - cc[dd]) * (xe - cc[dd]);
+    double fm[28];
+    disk_square(cc[u], cc[v], d2 > 0.0 ? sqrt(d2) : 0.0, B.inside, q, gl, fm);
+    for (int k = 0; k < K; ++k) {
+      int p[3];
+      mon3(k, p);
+      const int dg = p[u] + p[v];
+      const int k2 = dg * (dg + 1) / 2 + p[v];  // (p_u, p_v) in the graded 2-D order
+      acc[k] += s * pow(xe, p[dd] + 1) * fm[k2];
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    int p[3];
+    mon3(k, p);
+    vol[t * K + k] = acc[k] / (p[dd] + 1);
+  }
+}
+
+// tangential moments of the cut faces normal to dir (thread per face)
+__global__ void k_sphere_faces(Spheres B, GlRuleT gl, int N, int dir, double h, const int32_t* __restrict__ faces,
+                               int64_t n, const int32_t* __restrict__ fbody, int q, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int f = faces[t];
+  const int m0 = N + (dir == 0), m1 = N + (dir == 1);
+  const int i3[3] = {f % m0, (f / m0) % m1, f / (m0 * m1)};
+  const int b = fbody[f];
+  const int u = dir == 0 ? 1 : 0, v = dir == 2 ? 1 : 2;  // tangential dims, ascending
+  const double dn = (i3[dir] * h - B.c[b][dir]) / h;
+  const double cu = (B.c[b][u] - (i3[u] + 0.5) * h) / h, cv = (B.c[b][v] - (i3[v] + 0.5) * h) / h;
+  const double R = B.r[b] / h, d2 = R * R - dn * dn;
+  const int K2 = (q + 1) * (q + 2) / 2;
+  double fm[28];
+  disk_square(cu, cv, d2 > 0.0 ? sqrt(d2) : 0.0, B.inside, q, gl, fm);
+  for (int k = 0; k < K2; ++k) out[t * K2 + k] = fm[k];
+}
+
+// a face next to a covered cell closes (3-D)
+__global__ void k_geo_close_faces3(const uint8_t* __restrict__ cflag, int N, int dir, int64_t n, uint8_t* fflag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || fflag[i] == 0) return;
+  const int m0 = N + (dir == 0), m1 = N + (dir == 1);
+  int c[3] = {(int)(i % m0), (int)((i / m0) % m1), (int)(i / ((int64_t)m0 * m1))};
+  bool cov = false;
+  if (c[dir] < N) cov |= cflag[c[0] + (int64_t)N * (c[1] + (int64_t)N * c[2])] == 0;
+  c[dir] -= 1;
+  if (c[dir] >= 0) cov |= cflag[c[0] + (int64_t)N * (c[1] + (int64_t)N * c[2])] == 0;
+  if (cov) fflag[i] = 0;
+}
+
 }  // namespace eb
 
 using namespace eb;
@@ -591,7 +1025,7 @@ bool geometry_matches(const eb_geometry* g, int dim, const int* n, int n_cut) {
 // arrays laid out like the tables (dface[d]: [n_cutface[d]][K_F]); stream-ordered
 cudaError_t geometry_radius_derivative(const eb_geometry* g, int body, double* dvol, double* deb, double* debn,
                                        double* const* dface, cudaStream_t s) {
-  static const GlRule gl = gl_rule();
+  static const GlRule gl = gl_rule<GEO_GL>();
   const eb_geom& d = g->desc;
   if (d.dim != 2 || body < 0 || body >= g->n_body) return cudaErrorInvalidValue;
   Circles B;
@@ -708,7 +1142,7 @@ extern "C" eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double
     B.r[b] = radii_host[b];
     if (!(B.r[b] > 0.0)) { set_error("eb_geometry_circles: radii must be positive"); return EB_ERR_INVALID; }
   }
-  static const GlRule gl = gl_rule();
+  static const GlRule gl = gl_rule<GEO_GL>();
   const double h = 1.0 / N;
   const int q = moment_degree, K = mono_count(2, q), KF = q + 1;
   cudaStream_t s = (cudaStream_t)stream;
@@ -867,6 +1301,187 @@ extern "C" eb_status eb_geometry_circles(int32_t N, int32_t n_body, const double
   for (int b = 0; b < n_body; ++b) {
     G->centers[b][0] = B.c[b][0];
     G->centers[b][1] = B.c[b][1];
+    G->radii[b] = B.r[b];
+  }
+  *out = G;
+  return EB_OK;
+}
+
+extern "C" eb_status eb_geometry_spheres(int32_t N, int32_t n_body, const double* centers_host,
+                                         const double* radii_host, int32_t inside, int32_t moment_degree,
+                                         eb_geometry** out, eb_geom* desc, eb_stream_t stream) {
+  if (!out || !desc) { set_error("eb_geometry_spheres: out and desc are required"); return EB_ERR_INVALID; }
+  *out = nullptr;
+  if (N < 2 || N > 1290 || n_body < 0 || n_body > GEO_MAXB || (n_body > 0 && (!centers_host || !radii_host)) ||
+      moment_degree < 0 || moment_degree > 4 || (inside && n_body != 1)) {
+    set_error("eb_geometry_spheres: 2 <= N <= 1290, 0 <= n_body <= 64 (exactly 1 when inside), moment_degree in 0..4");
+    return EB_ERR_INVALID;
+  }
+  Spheres B;
+  B.n = n_body;
+  B.inside = inside ? 1 : 0;
+  for (int b = 0; b < n_body; ++b) {
+    for (int d = 0; d < 3; ++d) B.c[b][d] = centers_host[3 * b + d];
+    B.r[b] = radii_host[b];
+    if (!(B.r[b] > 0.0)) { set_error("eb_geometry_spheres: radii must be positive"); return EB_ERR_INVALID; }
+  }
+  static const GlRule gl = gl_rule<GEO_GL>();
+  static const GlRuleT glt = gl_rule<GEO_GLT>();
+  const double h = 1.0 / N;
+  const int q = moment_degree, K = mono_count(3, q), KF = mono_count(2, q);
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_geometry* G = new eb_geometry();
+  eb_status st = EB_OK;
+  cudaError_t e = cudaSuccess;
+  {
+    GeoAlloc A{s, G, {}};
+    const int64_t ncell = (int64_t)N * N * N;
+    uint8_t* cflag;
+    int32_t *cbody, *err;
+#define GEO_TRY(x)                                 \
+  do {                                             \
+    if ((e = (x)) != cudaSuccess) goto cuda_fail;  \
+  } while (0)
+    GEO_TRY(A.keep(&cflag, ncell));
+    GEO_TRY(A.keep(&cbody, ncell));
+    G->cell_body = cbody;
+    GEO_TRY(A.temp(&err, 1));
+    GEO_TRY(cudaMemsetAsync(err, 0, 4, s));
+    k_geo_classify3<<<nb256(ncell), 256, 0, s>>>(B, N, h, -1, ncell, cflag, cbody, err);
+    eb::count_launch();
+    {
+      int32_t* cut0;
+      int64_t nc0 = 0;
+      GEO_TRY(geo_list(cflag, ncell, 2, &cut0, &nc0, A, false));
+      int32_t herr = 0;
+      GEO_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+      GEO_TRY(cudaStreamSynchronize(s));
+      if (herr) {
+        st = EB_ERR_MULTIVALUED;
+        set_error("eb_geometry_spheres: two spheres reach into one cell or face");
+        goto done;
+      }
+      double *vol0, *eb0, *ebn0, *volp;
+      GEO_TRY(A.temp(&vol0, nc0 * K));
+      GEO_TRY(A.temp(&eb0, nc0 * K));
+      GEO_TRY(A.temp(&ebn0, nc0 * 3 * K));
+      GEO_TRY(A.temp(&volp, nc0 * K));
+      if (nc0 > 0) {
+        k_sphere_patch<<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, q, K, eb0, ebn0, volp);
+        k_sphere_vol<<<nb256(nc0), 256, 0, s>>>(B, glt, N, h, cut0, nc0, cbody, q, K, volp, vol0);
+        eb::count_launch();
+        eb::count_launch();
+      }
+      int32_t* keep;
+      int64_t* pos;
+      int64_t nc = 0;
+      GEO_TRY(A.temp(&keep, nc0));
+      GEO_TRY(A.temp(&pos, nc0));
+      if (nc0 > 0) {
+        k_geo_settle<<<nb256(nc0), 256, 0, s>>>(cut0, nc0, vol0, K, cflag, keep);
+        eb::count_launch();
+      }
+      GEO_TRY(geo_scan(keep, nc0, pos, &nc, A));
+      int32_t* cut;
+      double *vol, *ebm, *ebn;
+      GEO_TRY(A.keep(&cut, nc));
+      GEO_TRY(A.keep(&vol, nc * K));
+      GEO_TRY(A.keep(&ebm, nc * K));
+      GEO_TRY(A.keep(&ebn, nc * 3 * K));
+      if (nc0 > 0) {
+        k_geo_pack_idx<<<nb256(nc0), 256, 0, s>>>(keep, pos, nc0, cut0, cut);
+        k_geo_pack<<<nb256(nc0 * K), 256, 0, s>>>(keep, pos, nc0, K, vol0, vol);
+        k_geo_pack<<<nb256(nc0 * K), 256, 0, s>>>(keep, pos, nc0, K, eb0, ebm);
+        k_geo_pack<<<nb256(nc0 * 3 * K), 256, 0, s>>>(keep, pos, nc0, 3 * K, ebn0, ebn);
+        for (int i = 0; i < 4; ++i) eb::count_launch();
+      }
+      memset(desc, 0, sizeof(*desc));
+      desc->dim = 3;
+      desc->n[0] = desc->n[1] = desc->n[2] = N;
+      desc->h = h;
+      desc->moment_degree = q;
+      desc->cell_flag = cflag;
+      desc->n_cut = (int32_t)nc;
+      desc->cut_cell = cut;
+      desc->vol_mom = vol;
+      desc->eb_mom = ebm;
+      desc->eb_nmom = ebn;
+      desc->eb_bc = nullptr;
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int64_t nf = (int64_t)(N + (d == 0)) * (N + (d == 1)) * (N + (d == 2));
+      uint8_t* ff;
+      int32_t* fbody;
+      GEO_TRY(A.keep(&ff, nf));
+      GEO_TRY(A.keep(&fbody, nf));
+      G->face_body[d] = fbody;
+      GEO_TRY(cudaMemsetAsync(err, 0, 4, s));
+      k_geo_classify3<<<nb256(nf), 256, 0, s>>>(B, N, h, d, nf, ff, fbody, err);
+      eb::count_launch();
+      int32_t* cf0;
+      int64_t nf0 = 0;
+      GEO_TRY(geo_list(ff, nf, 2, &cf0, &nf0, A, false));
+      int32_t herr = 0;
+      GEO_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+      GEO_TRY(cudaStreamSynchronize(s));
+      if (herr) {
+        st = EB_ERR_MULTIVALUED;
+        set_error("eb_geometry_spheres: two spheres reach into one cell or face");
+        goto done;
+      }
+      double* fm0;
+      GEO_TRY(A.temp(&fm0, nf0 * KF));
+      int32_t* keep;
+      int64_t* pos;
+      int64_t nfc = 0;
+      GEO_TRY(A.temp(&keep, nf0));
+      GEO_TRY(A.temp(&pos, nf0));
+      if (nf0 > 0) {
+        k_sphere_faces<<<nb256(nf0), 256, 0, s>>>(B, glt, N, d, h, cf0, nf0, fbody, q, fm0);
+        k_geo_settle<<<nb256(nf0), 256, 0, s>>>(cf0, nf0, fm0, KF, ff, keep);
+        eb::count_launch();
+        eb::count_launch();
+      }
+      k_geo_close_faces3<<<nb256(nf), 256, 0, s>>>(cflag, N, d, nf, ff);
+      eb::count_launch();
+      if (nf0 > 0) {
+        k_geo_keep_open<<<nb256(nf0), 256, 0, s>>>(cf0, nf0, ff, keep);
+        eb::count_launch();
+      }
+      GEO_TRY(geo_scan(keep, nf0, pos, &nfc, A));
+      int32_t* cf;
+      double* fm;
+      GEO_TRY(A.keep(&cf, nfc));
+      GEO_TRY(A.keep(&fm, nfc * KF));
+      if (nf0 > 0) {
+        k_geo_pack_idx<<<nb256(nf0), 256, 0, s>>>(keep, pos, nf0, cf0, cf);
+        k_geo_pack<<<nb256(nf0 * KF), 256, 0, s>>>(keep, pos, nf0, KF, fm0, fm);
+        eb::count_launch();
+        eb::count_launch();
+      }
+      desc->face_flag[d] = ff;
+      desc->n_cutface[d] = (int32_t)nfc;
+      desc->cutface[d] = cf;
+      desc->face_mom[d] = fm;
+    }
+    GEO_TRY(cudaGetLastError());
+    GEO_TRY(cudaStreamSynchronize(s));
+    goto done;
+  cuda_fail:
+    st = e == cudaErrorMemoryAllocation ? EB_ERR_OOM : cuda_status(e, "eb_geometry_spheres");
+  done:;
+#undef GEO_TRY
+  }
+  if (st != EB_OK) {
+    eb_geometry_destroy(G);
+    memset(desc, 0, sizeof(*desc));
+    return st;
+  }
+  G->desc = *desc;
+  G->n_body = n_body;
+  G->inside = B.inside;
+  for (int b = 0; b < n_body; ++b) {
+    for (int d = 0; d < 3; ++d) G->centers[b][d] = B.c[b][d];
     G->radii[b] = B.r[b];
   }
   *out = G;
