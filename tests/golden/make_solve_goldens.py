@@ -12,6 +12,9 @@ LU of the kappa-weighted operator, Sec. 2.3), and its error norms (Sec. 3.3):
                              (the benchmark geometry), Q = 4, N = 16, Dirichlet EB and walls
   sphere_box_n16_neumann.npz the same with Neumann data on the EB (Sec. 2.2.1 Neumann rows; the
                              flux through a Neumann EB face is its datum), Dirichlet walls
+  five_circles_n128_q4.npz   the 2-D convergence-sweep geometry (the circle r = 0.3 at (0.51, 0.49)
+  five_circles_n128_q2.npz   and four seeded circles), N = 128, phi = sin(2 pi x) cos(3 pi y), Q = 4
+                             and Q = 2
 
 The sphere-inside case takes ~20 minutes on 8 cores (each 3-D face costs ~0.2 s in the oracle),
 each N = 16 case a few minutes.
@@ -33,6 +36,8 @@ def cases():
         "sphere_inside_n32": (lambda: E.sphere_inside_config(32), False),
         "sphere_box_n16": (lambda: E.sphere_box_config(16, seed=2), False),
         "sphere_box_n16_neumann": (lambda: E.sphere_box_config(16, seed=2), True),
+        "five_circles_n128_q4": (lambda: E.multi_circle_config(128), False),
+        "five_circles_n128_q2": (lambda: E.multi_circle_config(128), False),
     }
 
 
@@ -42,16 +47,16 @@ def make(name):
     from oracle_pool import parallel_stencils
     mk, neumann = cases()[name]
     g = mk()
-    man = E.Manufactured(g, E.sin_product("paper3d"))
+    man = E.Manufactured(g, E.sin_product("paper3d" if g.dim == 3 else "config2d"))
     bc = np.ones(len(g.cut_cells), np.uint8) if neumann else None
-    p = Params(order=4)
+    p = Params(order=2 if name.endswith("_q2") else 4)
     t0 = time.time()
     st = parallel_stencils(g, p, Oracle(g, p, bc).flux_faces(), bc_eb=bc)
     r = run_problem(g, man, p, bc_eb=bc, stencils=st)
     cells = np.nonzero(g.flag > 0)[0].astype(np.int32)
     np.savez_compressed(os.path.join(HERE, name + ".npz"), cells=cells, phi=r["phi"][cells],
                         sol=np.array([r["sol"][k] for k in ("linf", "l1", "l2")]),
-                        trunc=np.array([r["trunc"][k] for k in ("linf", "l1", "l2")]), N=g.N, order=4,
+                        trunc=np.array([r["trunc"][k] for k in ("linf", "l1", "l2")]), N=g.N, order=p.order,
                         neumann=int(neumann),
                         source="oracle/eb_oracle.py run_problem via tests/golden/make_solve_goldens.py")
     print(name, f"{time.time() - t0:.0f} s", r["sol"], flush=True)
