@@ -65,10 +65,11 @@ def parse():
     p.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 GPU solve timed once")
     p.add_argument("--out", default=None)
     p.add_argument("--batch", type=int, default=256, help="geometries of --mode batch")
-    p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch", "sweep"],
+    p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch", "sweep", "adjoint"],
                    help="build: one stencil build and exit; apply: build plus 3 FP32 applies (profiling cases); "
                         "sweep: the 2-D convergence sweep (five circles, 128^2..1024^2, Q = 2 and 4)")
     p.add_argument("--sweep-n", default="128,256,512,1024", help="grids of --mode sweep")
+    p.add_argument("--adjoint-n", type=int, default=128, help="grid of --mode adjoint")
     return p.parse_args()
 
 
@@ -323,6 +324,9 @@ def main():
     if args.mode == "sweep":
         run_sweep(args, P, torch)
         return
+    if args.mode == "adjoint":
+        run_adjoint(args, P, torch)
+        return
     if g is None:
         g, man, rho_h, Phi_h, geb_h, gw_h, t_geom = make_problem(args.n)
     # the same moment tables generated on the device (eb_geometry_spheres), timed once: the host generator's
@@ -563,6 +567,47 @@ def run_sweep(args, P, torch):
             del st
     print(json.dumps({"mode": "sweep", "workload": "2-D unit square minus five circles (config 2), phi = "
                       "sin(2 pi x) cos(3 pi y), refined solve to 1e-12", "data": "synthetic", "rows": rows}))
+
+
+def run_adjoint(args, P, torch):
+    """The shape-gradient workload: the unit cube minus eight seeded spheres (r ~ U[0.08, 0.2), clearance 2h
+    from each other and the box, SplitMix64(4)) at N^3 (default 128), Q = 4, J = 1/2 sum |V| phi^2 for
+    kappa L phi = kappa with homogeneous Dirichlet data, and its gradient with respect to the eight radii
+    and the amplitudes of 16 seeded level-set modes sin(2 pi k . x + theta) (k ~ U{1..4}^3, theta ~
+    U[0, 2 pi), SplitMix64(5)) at zero amplitude, plus the mode k = 0, theta = -pi/2 (unit speed on every
+    body), whose derivative is the sum of the radius derivatives.  Times (device): moment tables, stencil
+    build, forward refined solve, and the adjoint's transposed solve, derivative tables and stencil-solve
+    adjoints; the whole gradient by wall clock."""
+    import eb_inputs as E
+    N = args.adjoint_n
+    g = E.multi_sphere_config(N)
+    modes = np.vstack([E.level_set_modes(16, seed=5), [[0.0, 0.0, 0.0, -0.5 * math.pi]]])
+    cen = [tuple(c) for c in g.centers]
+    f64 = dict(dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    G = P.eb_geometry_spheres(N, cen, g.radii, moment_degree=4)
+    ev[1].record()
+    st = P.eb_build_stencils(G, order=4)
+    ev[2].record()
+    phi = torch.zeros(st.ncell, **f64)
+    sinfo = P.eb_solve(st, torch.ones(st.ncell, **f64), torch.zeros(max(G.n_cut, 1), **f64),
+                       torch.zeros(max(len(P.eb_wall_faces(st)), 1), **f64), phi, tol=1e-12)
+    ev[3].record()
+    ev[3].synchronize()
+    t0 = time.perf_counter()
+    ainfo = {}
+    J, dr, da = P.eb_adjoint_shape(G, st, phi, modes, info=ainfo)
+    t_adj = time.perf_counter() - t0
+    print(json.dumps({
+        "mode": "adjoint", "workload": f"unit cube minus eight seeded spheres at {N}^3, Q = 4, gradient of "
+        "J = 1/2 sum |V| phi^2 with respect to 8 radii and 16 + 1 level-set mode amplitudes",
+        "data": "synthetic", "N": N, "n_cut": int(G.n_cut), "unique_systems": st.info["n_unique"],
+        "geometry_ms": ev[0].elapsed_time(ev[1]), "build_ms": ev[1].elapsed_time(ev[2]),
+        "solve_ms": ev[2].elapsed_time(ev[3]), "solve_iterations": sinfo["iterations"],
+        "adjoint_s": t_adj, "adjoint": ainfo, "J": J, "dJ_dr": list(dr), "dJ_da": list(da[:-1]),
+        "uniform_mode_minus_sum_dr": float(da[-1] - dr.sum()), "sum_dr": float(dr.sum())}))
 
 
 def run_batch(args, P, torch):

@@ -12,10 +12,10 @@ geometry generator (Sec. 2.1, volume / face / normal-weighted moments; Sec. 3.1
 asks for O(h^{6+D}) accurate moments).  Here they are exact to rounding.
 """
 from .geometry import (Geometry, monomials, circle_config, four_circles_config, multi_circle_config, multi_sphere_config,
-                       sphere_box_config, sphere_inside_config, line_config, ProductFn)
+                       sphere_box_config, sphere_inside_config, line_config, ProductFn, level_set_modes)
 from .rng import SplitMix64, uniform, seeded_field
 from .manufactured import Manufactured, sin_product
 
 __all__ = ["Geometry", "monomials", "circle_config", "four_circles_config", "multi_circle_config", "multi_sphere_config",
-           "sphere_box_config", "sphere_inside_config", "line_config", "ProductFn", "SplitMix64", "uniform",
+           "sphere_box_config", "sphere_inside_config", "line_config", "ProductFn", "level_set_modes", "SplitMix64", "uniform",
            "seeded_field", "Manufactured", "sin_product"]

@@ -403,6 +403,19 @@ def multi_sphere_config(N: int, n: int = 8, seed: int = 4, rmin: float = 0.08, r
     return Geometry(3, N, np.array(centers), np.array(radii), False, qmax, name=f"multi-sphere-{N}", seed=seed)
 
 
+def level_set_modes(n: int = 16, seed: int = 5, dim: int = 3) -> np.ndarray:
+    """Rows (k_x, k_y, k_z, theta) of n seeded level-set modes sin(2 pi k . x + theta) of the shape-
+    gradient workload: k_i ~ U{1, ..., 4} in the first `dim` components (0 beyond), theta ~ U[0, 2 pi),
+    drawn from SplitMix64(seed) four numbers per mode."""
+    u = uniform(seed, 4 * n)
+    out = np.zeros((n, 4))
+    for m in range(n):
+        for d in range(dim):
+            out[m, d] = 1.0 + min(3.0, math.floor(4.0 * u[4 * m + d]))
+        out[m, 3] = 2.0 * math.pi * u[4 * m + 3]
+    return out
+
+
 def sphere_box_config(N: int, seed: int = 2, r: float = 0.35, qmax: int = 4) -> Geometry:
     """Unit cube minus a sphere of radius r centred at 0.5 + delta, delta_i ~ U[-h/2, h/2) from seed."""
     h = 1.0 / N

@@ -278,9 +278,21 @@ enum { EB_TABLE_CELL_FLAG = 0, EB_TABLE_CUT_CELL = 1, EB_TABLE_VOL_MOM = 2, EB_T
 eb_status eb_geometry_table(const eb_geometry* g, int32_t which, int32_t dir, void* dst_host, int64_t cap_bytes,
                             int64_t* bytes);
 
+/* One table of the shape derivatives of g's moment tables (d/dt of the table
+ * when the boundary moves with a normal speed, the cut sets held fixed), as
+ * the adjoint entry points below compute them: kind 0 the radius of body
+ * `body`; kind 1 the amplitude of the level-set mode mode_host = (k_x, k_y,
+ * k_z, theta) at zero amplitude (see eb_adjoint_shape).  which:
+ * EB_TABLE_VOL_MOM, EB_TABLE_EB_MOM, EB_TABLE_EB_NMOM or EB_TABLE_FACE_MOM
+ * (dir: face direction); laid out like the table.  *bytes receives the size;
+ * with dst_host == NULL nothing is computed.  Synchronous; for tests and
+ * inspection (it allocates and frees its work arrays). */
+eb_status eb_geometry_shape_table(const eb_geometry* g, int32_t kind, int32_t body, const double* mode_host,
+                                  int32_t which, int32_t dir, double* dst_host, int64_t cap_bytes, int64_t* bytes);
+
 /* The objective J = 1/2 sum_v |V_v| phi_v^2 of a solution phi on the stencils
  * st built from the device geometry g, and (dJ_host != NULL) its derivatives
- * with respect to the radii of g's circles (dJ_host[n_body]), by the adjoint
+ * with respect to the radii of g's bodies (dJ_host[n_body]), by the adjoint
  * method, with phi the solution of kappa L phi = kappa rho for the Dirichlet
  * problem with homogeneous data (Sec. 2.3): the adjoint solve
  * (kappa L)^T lam = |V| phi (transposed operator, FP64), then
@@ -291,10 +303,33 @@ eb_status eb_geometry_table(const eb_geometry* g, int32_t which, int32_t dir, vo
  * reverse-mode derivative of each stencil solve with respect to A and F,
  * contracted with the rows' and F's derivatives, which follow from the shape
  * derivatives of the moment tables (recomputed on the device, not stored).
- * The cut-cell and cut-face sets are held fixed.  2-D circles, Dirichlet EB.
- * phi: [ncell] device (FP64).  Synchronises the stream. */
+ * The cut-cell and cut-face sets are held fixed.  Circles (2-D) and spheres
+ * (3-D), Dirichlet EB.  phi: [ncell] device (FP64).  Synchronises the stream. */
 eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* st, const double* phi, double* J_host,
                            double* dJ_host, eb_stream_t stream);
+
+/* eb_adjoint_radii with level-set modes as further parameters: the boundary
+ * is the zero set of psi + sum_m a_m sin(2 pi k_m . x + theta_m), psi the
+ * signed distance of g's bodies (positive in the fluid), and the derivatives
+ * are taken at a = 0 (g's geometry): mode m moves the boundary with the
+ * normal speed -sin(2 pi k_m . x + theta_m) along the direction out of each
+ * body (+ for the inside of one body).  modes_host: [n_modes][4] host
+ * (k_x, k_y, k_z, theta; k_z ignored in 2-D).  dJ_radii_host[n_body] and
+ * dJ_modes_host[n_modes] receive the derivatives (both NULL: J only).  One
+ * adjoint solve serves all parameters; the stencil-solve adjoints run in one
+ * pass over the systems for all parameters.  info (may be NULL) receives the
+ * transposed solve's iterations and the phases' device times when the
+ * derivatives are asked for.  Synchronises the stream. */
+typedef struct eb_adjoint_info {
+  int32_t iterations;     /* BiCGStab iterations of the transposed solve */
+  double rel_residual;    /* its final relative residual */
+  double solve_ms;        /* device time of the transposed solve */
+  double tables_ms;       /* of the moment tables' derivatives and kappa terms, all parameters */
+  double stencils_ms;     /* of the stencil-solve adjoints, all parameters */
+} eb_adjoint_info;
+eb_status eb_adjoint_shape(const eb_geometry* g, const eb_stencils* st, const double* phi, int32_t n_modes,
+                           const double* modes_host, double* J_host, double* dJ_radii_host, double* dJ_modes_host,
+                           eb_adjoint_info* info, eb_stream_t stream);
 
 void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);

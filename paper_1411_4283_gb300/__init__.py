@@ -71,6 +71,11 @@ class EbSolveInfo(ctypes.Structure):
                 "apply_ms": self.apply_ms, "precond_blocks": self.precond_blocks}
 
 
+class EbAdjointInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("tables_ms", ctypes.c_double), ("stencils_ms", ctypes.c_double)]
+
+
 class EbError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -113,7 +118,9 @@ def load():
         "eb_geometry_destroy": (None, [_vp]),
         "eb_geometry_spheres": (i32, [i32, i32, P(dbl), P(dbl), i32, i32, P(_vp), P(EbGeom), _vp]),
         "eb_geometry_table": (i32, [_vp, i32, i32, _vp, i64, P(i64)]),
+        "eb_geometry_shape_table": (i32, [_vp, i32, i32, P(dbl), i32, i32, P(dbl), i64, P(i64)]),
         "eb_adjoint_radii": (i32, [_vp, _vp, _vp, P(dbl), P(dbl), _vp]),
+        "eb_adjoint_shape": (i32, [_vp, _vp, _vp, i32, P(dbl), P(dbl), P(dbl), P(dbl), P(EbAdjointInfo), _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -240,6 +247,28 @@ class GpuGeometry:
             out = out.reshape(self.desc.n_cutface[d], -1)
         return out
 
+    def shape_table(self, name: str, body: int = 0, mode=None, d: int = 0) -> np.ndarray:
+        """The derivative of table `name` (vol_mom, eb_mom, eb_nmom, face_mom) for the radius of `body`
+        (mode None) or for the amplitude of the level-set mode (k_x, k_y, k_z, theta) at zero amplitude,
+        shaped like table(name, d)."""
+        lib = load()
+        w = self.TABLES[name]
+        kind = 0 if mode is None else 1
+        m = np.ascontiguousarray(np.zeros(4) if mode is None else np.asarray(mode, dtype=np.float64).reshape(4))
+        mp = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        nb = ctypes.c_int64()
+        _check(lib.eb_geometry_shape_table(self.handle, kind, int(body), mp, w, d, None, 0, ctypes.byref(nb)))
+        out = np.zeros(max(nb.value // 8, 1))
+        _check(lib.eb_geometry_shape_table(self.handle, kind, int(body), mp, w, d,
+                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.nbytes,
+                                           ctypes.byref(nb)))
+        out = out[:nb.value // 8]
+        if name in ("vol_mom", "eb_mom"):
+            return out.reshape(self.n_cut, -1)
+        if name == "eb_nmom":
+            return out.reshape(self.n_cut, self.dim, -1)
+        return out.reshape(self.desc.n_cutface[d], -1)
+
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.eb_geometry_destroy(self.handle)
@@ -286,6 +315,30 @@ def eb_adjoint_radii(geom: "GpuGeometry", st: "Stencils", phi, gradient=True, st
     _check(load().eb_adjoint_radii(geom.handle, st.handle, _ptr(phi), ctypes.byref(J), dJ if gradient else None,
                                    _stream(stream)))
     return J.value, (np.array([dJ[i] for i in range(nb)]) if gradient else None)
+
+
+def eb_adjoint_shape(geom: "GpuGeometry", st: "Stencils", phi, modes=(), gradient=True, stream=None, info=None):
+    """(J, dJ/dr, dJ/da) for J = 1/2 sum |V| phi^2, the radii of a device geometry's bodies and the
+    amplitudes a_m of level-set modes sin(2 pi k_m . x + theta_m) at a = 0 (see eb.h).  modes: rows
+    (k_x, k_y, k_z, theta) (k_z ignored in 2-D).  info: a dict that receives the transposed solve's
+    iterations and the phases' device times."""
+    import torch
+    assert phi.dtype == torch.float64 and phi.is_cuda and phi.is_contiguous() and phi.numel() == st.ncell
+    m = np.ascontiguousarray(np.asarray(modes, dtype=np.float64).reshape(-1, 4))
+    nb, nm = len(geom.radii), len(m)
+    J = ctypes.c_double()
+    dr = (ctypes.c_double * max(nb, 1))()
+    da = (ctypes.c_double * max(nm, 1))()
+    mp = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if nm else None
+    ai = EbAdjointInfo()
+    _check(load().eb_adjoint_shape(geom.handle, st.handle, _ptr(phi), nm, mp, ctypes.byref(J),
+                                   dr if gradient else None, da if gradient else None, ctypes.byref(ai),
+                                   _stream(stream)))
+    if info is not None:
+        info.update({k: getattr(ai, k) for k, _ in EbAdjointInfo._fields_})
+    if not gradient:
+        return J.value, None, None
+    return J.value, np.array([dr[i] for i in range(nb)]), np.array([da[i] for i in range(nm)])
 
 
 class Stencils:
@@ -423,5 +476,5 @@ def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "eb_geometry_spheres", "GpuGeometry", "eb_adjoint_radii", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "eb_geometry_spheres", "GpuGeometry", "eb_adjoint_radii", "eb_adjoint_shape", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

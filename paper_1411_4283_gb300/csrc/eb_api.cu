@@ -1989,17 +1989,34 @@ __global__ void k_adj_kappa(int64_t n_cut, const int32_t* cut_cell, const double
 
 }  // namespace eb
 
-extern "C" eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* st, const double* phi, double* J_host,
-                                      double* dJ_host, eb_stream_t stream) {
-  if (!g || !st || !phi || !J_host) { set_error("eb_adjoint_radii: null argument"); return EB_ERR_INVALID; }
+namespace {
+
+// timing events, destroyed with the scope
+struct Events {
+  cudaEvent_t e[4] = {};
+  int n = 0;
+  cudaError_t create(int k) {
+    for (; n < k; ++n) {
+      const cudaError_t r = cudaEventCreate(&e[n]);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+  ~Events() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(e[i]);
+  }
+};
+
+// J and, when dJ_host is given, dJ/dp for the boundary velocities vel (one parameter each)
+eb_status adjoint_shape(const eb_geometry* g, const eb_stencils* st, const double* phi,
+                        const std::vector<ShapeVel>& vel, double* J_host, double* dJ_host, eb_adjoint_info* info,
+                        cudaStream_t s) {
   g_err.clear();
   const Dims& dm = st->dm;
-  if (dm.dim != 2) { set_error("eb_adjoint_radii: circles (2-D) only"); return EB_ERR_INVALID; }
   if (!geometry_matches(g, dm.dim, dm.n, dm.n_cut)) {
-    set_error("eb_adjoint_radii: the stencils were not built from this geometry");
+    set_error("eb_adjoint: the stencils were not built from this geometry");
     return EB_ERR_INVALID;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = dm.ncell;
   const double hd = pow(dm.h, dm.dim);
   Tmp tmp;
@@ -2036,9 +2053,18 @@ extern "C" eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* s
   AT.nz = dm.n[2];
   int it = 0;
   double rr = 0.0;
+  Events ev;
+  EB_CUDA(ev.create(4));
+  EB_CUDA(cudaEventRecord(ev.e[0], s));
   EB_CUDA(bicgstab<double>(AT, rhs, lam, st->dinv64, work, n, 1e-12, 20000, dscr, &it, &rr, s, nullptr));
-  if (!(rr <= 1e-10)) { set_error("eb_adjoint_radii: the adjoint solve did not converge"); return EB_ERR_NOT_CONVERGED; }
-  // ---- per radius: the kappa terms and the stencil-solve adjoints
+  EB_CUDA(cudaEventRecord(ev.e[1], s));
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rr;
+  }
+  if (!(rr <= 1e-10)) { set_error("eb_adjoint: the adjoint solve did not converge"); return EB_ERR_NOT_CONVERGED; }
+  // ---- per parameter: the moment tables' derivatives and the kappa terms; then one pass of the
+  // stencil-solve adjoints over all parameters
   Tables T;
   if (!make_tables(dm.dim, dm.order, dm.mdeg, &T)) { set_error("table construction failed"); return EB_ERR_INVALID; }
   LsArgs la;
@@ -2069,46 +2095,117 @@ extern "C" eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* s
   const int64_t nu = st->n_unique;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (nu + ADJ_WARPS - 1) / ADJ_WARPS));
   double* scratch;
-  EB_TRY(tmp.get(&scratch, (size_t)blocks * ADJ_WARPS * MAXROWS * (2 * MAXK + 2)));
+  EB_TRY(tmp.get(&scratch, (size_t)blocks * ADJ_WARPS * MAXROWS * ADJ_SCRATCH));
   const int KS = dm.KS, KFS = dm.KFS, nc = dm.n_cut;
-  double *dvol, *deb, *debn, *dface[3] = {nullptr, nullptr, nullptr}, *acc;
-  EB_TRY(tmp.get(&dvol, (size_t)nc * KS));
-  EB_TRY(tmp.get(&deb, (size_t)nc * KS));
-  EB_TRY(tmp.get(&debn, (size_t)nc * dm.dim * KS));
-  for (int d = 0; d < dm.dim; ++d)
-    EB_TRY(tmp.get(&dface[d], (size_t)std::max<int64_t>(1, geometry_cutfaces(g, d)) * KFS));
-  const int nb = geometry_bodies(g);
-  EB_TRY(tmp.get(&acc, std::max(1, nb)));
-  EB_CUDA(cudaMemsetAsync(acc, 0, std::max(1, nb) * 8, s));
-  for (int b = 0; b < nb; ++b) {
-    EB_CUDA(geometry_radius_derivative(g, b, dvol, deb, debn, dface, s));
+  const int np = (int)vel.size();
+  AdjArgs ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.s_vol = (int64_t)std::max(1, nc) * KS;
+  ga.s_ebn = ga.s_vol * dm.dim;
+  double *dvol, *deb, *debn, *acc;
+  EB_TRY(tmp.get(&dvol, (size_t)np * ga.s_vol));
+  EB_TRY(tmp.get(&deb, (size_t)np * ga.s_vol));
+  EB_TRY(tmp.get(&debn, (size_t)np * ga.s_ebn));
+  double* dface[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < dm.dim; ++d) {
+    ga.s_face[d] = std::max<int64_t>(1, geometry_cutfaces(g, d)) * KFS;
+    EB_TRY(tmp.get(&dface[d], (size_t)np * ga.s_face[d]));
+  }
+  EB_TRY(tmp.get(&acc, std::max(1, np)));
+  EB_CUDA(cudaMemsetAsync(acc, 0, std::max(1, np) * 8, s));
+  for (int p = 0; p < np; ++p) {
+    double* dfp[3] = {nullptr, nullptr, nullptr};
+    for (int d = 0; d < dm.dim; ++d) dfp[d] = dface[d] + p * ga.s_face[d];
+    EB_CUDA(geometry_shape_derivative(g, vel[p], dvol + p * ga.s_vol, deb + p * ga.s_vol, debn + p * ga.s_ebn, dfp, s));
     if (nc > 0) {
-      k_adj_kappa<<<nblk(nc, 256), 256, 0, s>>>(nc, st->cut_cell, dvol, KS, phi, lam, hd, acc + b);
-      eb::count_launch();
-    }
-    AdjArgs ga;
-    ga.lam = lam;
-    ga.phi = phi;
-    ga.dvol = dvol;
-    ga.deb = deb;
-    ga.debn = debn;
-    for (int d = 0; d < 3; ++d) ga.dface[d] = d < dm.dim ? dface[d] : dface[0];
-    ga.n_slots = nu;
-    ga.next = next;
-    ga.scratch = scratch;
-    ga.dJ = acc + b;
-    EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
-    if (nu > 0) {
-      EB_CUDA(stencil_adjoint_launch(blocks, s, la, T, ga));
+      k_adj_kappa<<<nblk(nc, 256), 256, 0, s>>>(nc, st->cut_cell, dvol + p * ga.s_vol, KS, phi, lam, hd, acc + p);
       eb::count_launch();
     }
   }
-  std::vector<double> h(std::max(1, nb));
+  EB_CUDA(cudaEventRecord(ev.e[2], s));
+  ga.lam = lam;
+  ga.phi = phi;
+  ga.dvol = dvol;
+  ga.deb = deb;
+  ga.debn = debn;
+  for (int d = 0; d < 3; ++d) {
+    ga.dface[d] = d < dm.dim ? dface[d] : dface[0];
+    if (d >= dm.dim) ga.s_face[d] = ga.s_face[0];
+  }
+  ga.n_par = np;
+  ga.n_slots = nu;
+  ga.next = next;
+  ga.scratch = scratch;
+  ga.dJ = acc;
+  EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
+  if (nu > 0 && np > 0) {
+    EB_CUDA(stencil_adjoint_launch(blocks, s, la, T, ga));
+    eb::count_launch();
+  }
+  EB_CUDA(cudaEventRecord(ev.e[3], s));
+  std::vector<double> h(std::max(1, np));
   int32_t herr = 0;
-  EB_CUDA(cudaMemcpyAsync(h.data(), acc, std::max(1, nb) * 8, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(h.data(), acc, std::max(1, np) * 8, cudaMemcpyDeviceToHost, s));
   EB_CUDA(cudaMemcpyAsync(&herr, lerr, 4, cudaMemcpyDeviceToHost, s));
   EB_CUDA(cudaStreamSynchronize(s));
-  if (herr) { set_error("eb_adjoint_radii: a stencil system was singular in the adjoint"); return EB_ERR_RANK_DEFICIENT; }
-  for (int b = 0; b < nb; ++b) dJ_host[b] = h[b];
+  if (info) {
+    float ms[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k) EB_CUDA(cudaEventElapsedTime(&ms[k], ev.e[k], ev.e[k + 1]));
+    info->solve_ms = ms[0];
+    info->tables_ms = ms[1];
+    info->stencils_ms = ms[2];
+  }
+  if (herr) { set_error("eb_adjoint: a stencil system was singular in the adjoint"); return EB_ERR_RANK_DEFICIENT; }
+  for (int p = 0; p < np; ++p) dJ_host[p] = h[p];
+  return EB_OK;
+}
+
+}  // namespace
+
+extern "C" eb_status eb_adjoint_radii(const eb_geometry* g, const eb_stencils* st, const double* phi, double* J_host,
+                                      double* dJ_host, eb_stream_t stream) {
+  if (!g || !st || !phi || !J_host) { set_error("eb_adjoint_radii: null argument"); return EB_ERR_INVALID; }
+  std::vector<ShapeVel> vel(geometry_bodies(g));
+  for (size_t b = 0; b < vel.size(); ++b) {
+    memset(&vel[b], 0, sizeof(ShapeVel));
+    vel[b].kind = 0;
+    vel[b].body = (int)b;
+  }
+  return adjoint_shape(g, st, phi, vel, J_host, dJ_host, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" eb_status eb_adjoint_shape(const eb_geometry* g, const eb_stencils* st, const double* phi,
+                                      int32_t n_modes, const double* modes_host, double* J_host,
+                                      double* dJ_radii_host, double* dJ_modes_host, eb_adjoint_info* info,
+                                      eb_stream_t stream) {
+  if (!g || !st || !phi || !J_host || n_modes < 0 || (n_modes > 0 && !modes_host)) {
+    set_error("eb_adjoint_shape: null argument or negative mode count");
+    return EB_ERR_INVALID;
+  }
+  const int nb = geometry_bodies(g);
+  const bool want = dJ_radii_host || dJ_modes_host;
+  if (want && ((!dJ_radii_host && nb > 0) || (!dJ_modes_host && n_modes > 0))) {
+    set_error("eb_adjoint_shape: give the derivative arrays of both the radii and the modes, or neither");
+    return EB_ERR_INVALID;
+  }
+  std::vector<ShapeVel> vel(nb + n_modes);
+  for (int p = 0; p < nb + n_modes; ++p) {
+    memset(&vel[p], 0, sizeof(ShapeVel));
+    if (p < nb) {
+      vel[p].kind = 0;
+      vel[p].body = p;
+    } else {
+      const double* m = modes_host + 4 * (p - nb);
+      vel[p].kind = 1;
+      for (int d = 0; d < 3; ++d) vel[p].k[d] = m[d];
+      vel[p].theta = m[3];
+    }
+  }
+  if (!want) return adjoint_shape(g, st, phi, vel, J_host, nullptr, info, (cudaStream_t)stream);
+  std::vector<double> dj(std::max<size_t>(1, vel.size()));
+  const eb_status r = adjoint_shape(g, st, phi, vel, J_host, dj.data(), info, (cudaStream_t)stream);
+  if (r != EB_OK) return r;
+  for (int b = 0; b < nb; ++b) dJ_radii_host[b] = dj[b];
+  for (int m = 0; m < n_modes; ++m) dJ_modes_host[m] = dj[nb + m];
   return EB_OK;
 }

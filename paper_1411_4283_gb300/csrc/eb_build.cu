@@ -1174,10 +1174,18 @@ cudaError_t lsq_prepare(size_t smem) {
 // One warp per system; G by lanes over its upper-triangle entries, its Cholesky factor in shared memory
 // (the adjoint needs about eight digits, which the normal equations keep for these systems).
 
-// weighted row b and its tangent db of one LS row (Dirichlet rows); returns the weight.  *col: the
-// cell of a volume row, -1 for a boundary row.
-__device__ double row_tangent(const LsArgs& a, const Tables& T, const AdjArgs& g, uint32_t desc, const int* base,
-                              const double* x0s, double* b, double* db, int64_t* col) {
+// Several parameters share one pass: the rows, G's factor, y and z do not depend on the parameter, and
+// each parameter adds its tangent's contraction (dJ[p]).  Systems without a cut cell, cut face or EB
+// face among their rows and right-hand side do not move and are skipped.
+
+// source of a row's moments: none (a full cell or face), a cut cell's volume or EB moments, or a cut face
+enum : int { ROW_SRC_NONE = 0, ROW_SRC_VOL = 1, ROW_SRC_EB = 2, ROW_SRC_FACE = 3 };  // + wall direction
+
+// weighted row b of one LS row (Dirichlet rows); returns the weight.  *col: the cell of a volume row, -1
+// for a boundary row; *sc: w / m0 (b = sc m, m the moments shifted to x0); delta: the shift; *src: the
+// table and entry its moments come from (kind << 56 | entry, kind ROW_SRC_*, 0 for full rows)
+__device__ double row_build(const LsArgs& a, const Tables& T, uint32_t desc, const int* base, const double* x0s,
+                            double* b, double* sc, double* delta, int64_t* col, int64_t* src) {
   const Dims& dm = a.dm;
   const int K = T.K;
   const int kind = rd_kind(desc);
@@ -1187,12 +1195,11 @@ __device__ double row_tangent(const LsArgs& a, const Tables& T, const AdjArgs& g
     c[d] = base[d] + dl[d];
   }
   const int64_t cid = cell_id(dm, c);
-  double delta[3];
   for (int d = 0; d < 3; ++d) delta[d] = (double)dl[d] - x0s[d];
   *col = kind == 0 ? cid : -1;
-  double m[MAXK], dmv[MAXK];
-  const double* src = nullptr;
-  const double* dsrc = nullptr;
+  *src = 0;
+  double m[MAXK];
+  const double* mp = nullptr;
   double w;
   if (kind == 2) {
     const int wd = rd_wdir(desc), ws = rd_wside(desc);
@@ -1205,15 +1212,11 @@ __device__ double row_tangent(const LsArgs& a, const Tables& T, const AdjArgs& g
     w = weight_of(dm, r2);
     if (cf >= 0) {
       const double* fm = a.face_mom[wd] + (int64_t)cf * dm.KFS;
-      const double* dfm = g.dface[wd] + (int64_t)cf * dm.KFS;
-      for (int i = 0; i < K; ++i) {
-        m[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
-        dmv[i] = T.tang[wd][i] >= 0 ? dfm[T.tang[wd][i]] : 0.0;
-      }
-      src = m;
-      dsrc = dmv;
+      for (int i = 0; i < K; ++i) m[i] = T.tang[wd][i] >= 0 ? fm[T.tang[wd][i]] : 0.0;
+      mp = m;
+      *src = ((int64_t)(ROW_SRC_FACE + wd) << 56) | cf;
     } else {
-      src = T.full_face[wd];
+      mp = T.full_face[wd];
     }
   } else {
     double r2 = 0.0;
@@ -1221,50 +1224,69 @@ __device__ double row_tangent(const LsArgs& a, const Tables& T, const AdjArgs& g
     w = weight_of(dm, r2);
     const int32_t cut = a.cut_of_cell[cid];
     if (kind == 1) {
-      src = a.eb_mom + (int64_t)cut * dm.KS;
-      dsrc = g.deb + (int64_t)cut * dm.KS;
+      mp = a.eb_mom + (int64_t)cut * dm.KS;
+      *src = ((int64_t)ROW_SRC_EB << 56) | cut;
     } else if (cut >= 0) {
-      src = a.vol_mom + (int64_t)cut * dm.KS;
-      dsrc = g.dvol + (int64_t)cut * dm.KS;
+      mp = a.vol_mom + (int64_t)cut * dm.KS;
+      *src = ((int64_t)ROW_SRC_VOL << 56) | cut;
     } else {
-      src = T.full_vol;
+      mp = T.full_vol;
     }
   }
   double sm[MAXK];
-  shift_moments(T, src, delta, sm);
-  const double sc = w / sm[0];
-  if (dsrc) {
-    double sd[MAXK];
-    shift_moments(T, dsrc, delta, sd);
-    const double r0 = sd[0] / sm[0];
-    for (int i = 0; i < K; ++i) db[i] = sc * (sd[i] - r0 * sm[i]);
-  } else {
-    for (int i = 0; i < K; ++i) db[i] = 0.0;
-  }
-  for (int i = 0; i < K; ++i) b[i] = sc * sm[i];
+  shift_moments(T, mp, delta, sm);
+  *sc = w / sm[0];
+  for (int i = 0; i < K; ++i) b[i] = *sc * sm[i];
   return w;
+}
+
+// tangent db of a row built by row_build (b at stride MAXROWS) for parameter p
+__device__ void row_dtangent(const LsArgs& a, const Tables& T, const AdjArgs& g, int p, int64_t src,
+                             const double* delta, double sc, double w, const double* b, double* db) {
+  const Dims& dm = a.dm;
+  const int K = T.K;
+  const int kind = (int)(src >> 56);
+  const int64_t e = src & ((1ll << 56) - 1);
+  double m[MAXK];
+  const double* dp;
+  if (kind >= ROW_SRC_FACE) {
+    const int wd = kind - ROW_SRC_FACE;
+    const double* dfm = g.dface[wd] + p * g.s_face[wd] + e * dm.KFS;
+    for (int i = 0; i < K; ++i) m[i] = T.tang[wd][i] >= 0 ? dfm[T.tang[wd][i]] : 0.0;
+    dp = m;
+  } else {
+    dp = (kind == ROW_SRC_EB ? g.deb : g.dvol) + p * g.s_vol + e * dm.KS;
+  }
+  double sd[MAXK];
+  shift_moments(T, dp, delta, sd);
+  const double r0 = sd[0] * sc / w;  // dm0 / m0
+  for (int i = 0; i < K; ++i) db[i] = sc * sd[i] - r0 * b[(int64_t)i * MAXROWS];
 }
 
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
     k_stencil_adjoint(const __grid_constant__ LsArgs a, const __grid_constant__ Tables T, AdjArgs g) {
   __shared__ double Gs[ADJ_WARPS][MAXK * MAXK];
-  __shared__ double vs[ADJ_WARPS][6 * MAXK];
+  __shared__ double vs[ADJ_WARPS][5 * MAXK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* G = Gs[warp];
   double* F = vs[warp];
-  double* dF = F + MAXK;
-  double* y = F + 2 * MAXK;
-  double* z = F + 3 * MAXK;
-  double* u = F + 4 * MAXK;
-  double* rinv = F + 5 * MAXK;
+  double* y = F + MAXK;
+  double* z = F + 2 * MAXK;
+  double* u = F + 3 * MAXK;
+  double* rinv = F + 4 * MAXK;
   const Dims& dm = a.dm;
   const int K = T.K;
   const int E = K * (K + 1) / 2;
   const int gw = blockIdx.x * ADJ_WARPS + warp;
-  double* sb = g.scratch + (int64_t)gw * MAXROWS * (2 * MAXK + 2);  // rows b, column-major
-  double* sdb = sb + (int64_t)MAXROWS * MAXK;                        // tangent rows
-  double* sw = sdb + (int64_t)MAXROWS * MAXK;                        // weights
-  int64_t* scol = reinterpret_cast<int64_t*>(sw + MAXROWS);          // columns
+  double* sb = g.scratch + (int64_t)gw * MAXROWS * ADJ_SCRATCH;  // rows b, column-major
+  double* sw = sb + (int64_t)MAXROWS * MAXK;                     // weights
+  double* ssc = sw + MAXROWS;                                    // w / m0
+  double* sby = ssc + MAXROWS;                                   // b_i . y
+  double* sbz = sby + MAXROWS;                                   // b_i . z
+  double* stb = sbz + MAXROWS;                                   // tbar_i
+  double* sdl = stb + MAXROWS;                                   // shifts, [3][MAXROWS]
+  int64_t* scol = reinterpret_cast<int64_t*>(sdl + 3 * MAXROWS);  // columns
+  int64_t* ssrc = scol + MAXROWS;                                 // moment sources
   while (true) {
     int s = 0;
     if (lane == 0) s = atomicAdd(g.next, 1);
@@ -1288,50 +1310,44 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       x0s[dface] = -0.5;
     }
     if (n < K) continue;
-    // rows, tangents, weights, columns
-    int any_t = 0;
+    // rows, weights, columns and moment sources
+    int moving = 0;
     for (int i = lane; i < n; i += 32) {
-      double b[MAXK], db[MAXK];
-      int64_t col;
-      sw[i] = row_tangent(a, T, g, a.row_desc[p0 + i], base, x0s, b, db, &col);
+      double b[MAXK], dl[3], sc;
+      int64_t col, src;
+      sw[i] = row_build(a, T, a.row_desc[p0 + i], base, x0s, b, &sc, dl, &col, &src);
+      ssc[i] = sc;
       scol[i] = col;
-      for (int k = 0; k < K; ++k) {
-        sb[(int64_t)k * MAXROWS + i] = b[k];
-        sdb[(int64_t)k * MAXROWS + i] = db[k];
-        any_t |= db[k] != 0.0;
-      }
+      ssrc[i] = src;
+      for (int d = 0; d < 3; ++d) sdl[d * MAXROWS + i] = dl[d];
+      for (int k = 0; k < K; ++k) sb[(int64_t)k * MAXROWS + i] = b[k];
+      moving |= src != 0;
     }
-    // F and its tangent (Sec. 2.2.1): grid face p_d m_f^{p-e_d}; EB face sum_d p_d m_{d,f}^{p-e_d}
+    // F (Sec. 2.2.1): grid face p_d m_f^{p-e_d}; EB face sum_d p_d m_{d,f}^{p-e_d}
+    int32_t cf_self = -1;
+    if (cut_self < 0) cf_self = a.cutface_of[dface][flocal];
+    moving |= cut_self >= 0 || cf_self >= 0;
     for (int i = lane; i < K; i += 32) {
-      double f = 0.0, df = 0.0;
+      double f = 0.0;
       if (cut_self >= 0) {
         for (int d = 0; d < dm.dim; ++d) {
           const int lo = T.lower[d][i];
-          if (lo < 0) continue;
-          const int64_t off = ((int64_t)cut_self * dm.dim + d) * dm.KS + lo;
-          f += (double)T.mon[i][d] * a.eb_nmom[off];
-          df += (double)T.mon[i][d] * g.debn[off];
+          if (lo >= 0) f += (double)T.mon[i][d] * a.eb_nmom[((int64_t)cut_self * dm.dim + d) * dm.KS + lo];
         }
       } else {
         const int q = T.lower[dface][i];
         if (q >= 0) {
-          const int32_t cf = a.cutface_of[dface][flocal];
-          if (cf >= 0) {
-            if (T.tang[dface][q] >= 0) {
-              const int64_t off = (int64_t)cf * dm.KFS + T.tang[dface][q];
-              f = (double)T.mon[i][dface] * a.face_mom[dface][off];
-              df = (double)T.mon[i][dface] * g.dface[dface][off];
-            }
+          if (cf_self >= 0) {
+            if (T.tang[dface][q] >= 0)
+              f = (double)T.mon[i][dface] * a.face_mom[dface][(int64_t)cf_self * dm.KFS + T.tang[dface][q]];
           } else {
             f = (double)T.mon[i][dface] * T.full_face[dface][q];
           }
         }
       }
       F[i] = f;
-      dF[i] = df;
-      any_t |= df != 0.0;
     }
-    if (!__any_sync(0xffffffffu, any_t)) continue;  // this system does not move with the parameter
+    if (!__any_sync(0xffffffffu, moving)) continue;  // this system does not move with the geometry
     __syncwarp();
     // G = B^T B (upper triangle, lanes over entries), then its Cholesky factor in place
     for (int e = lane; e < E; e += 32) {
@@ -1388,14 +1404,14 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       }
     }
     const double ih2 = 1.0 / (dm.h * dm.h);
+    for (int i = lane; i < n; i += 32) {
+      const int64_t col = scol[i];
+      stb[i] = col >= 0 ? sw[i] * (-lam_face * g.phi[col] * ih2) : 0.0;
+    }
+    __syncwarp();
     for (int k = lane; k < K; k += 32) {  // u = B^T tbar, tbar_i = w_i sbar_i
       double acc = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const int64_t col = scol[i];
-        if (col < 0) continue;
-        const double tb = sw[i] * (-lam_face * g.phi[col] * ih2);
-        acc = fma(sb[(int64_t)k * MAXROWS + i], tb, acc);
-      }
+      for (int i = 0; i < n; ++i) acc = fma(sb[(int64_t)k * MAXROWS + i], stb[i], acc);
       u[k] = acc;
     }
     __syncwarp();
@@ -1416,23 +1432,51 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       }
     }
     __syncwarp();
-    double dj = 0.0;
     for (int i = lane; i < n; i += 32) {
-      double by = 0.0, bz = 0.0, ydb = 0.0, zdb = 0.0;
+      double by = 0.0, bz = 0.0;
       for (int k = 0; k < K; ++k) {
-        const double bk = sb[(int64_t)k * MAXROWS + i], dk = sdb[(int64_t)k * MAXROWS + i];
+        const double bk = sb[(int64_t)k * MAXROWS + i];
         by = fma(bk, y[k], by);
         bz = fma(bk, z[k], bz);
-        ydb = fma(y[k], dk, ydb);
-        zdb = fma(z[k], dk, zdb);
       }
-      const int64_t col = scol[i];
-      const double tb = col >= 0 ? sw[i] * (-lam_face * g.phi[col] * ih2) : 0.0;
-      dj += (tb - bz) * ydb - by * zdb;
+      sby[i] = by;
+      sbz[i] = bz;
     }
-    for (int k = lane; k < K; k += 32) dj = fma(z[k], dF[k], dj);
-    dj = warp_sum(dj);
-    if (lane == 0) atomicAdd(g.dJ, dj);
+    __syncwarp();
+    for (int p = 0; p < g.n_par; ++p) {
+      double dj = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        if (ssrc[i] == 0) continue;
+        double dl[3], db[MAXK];
+        for (int d = 0; d < 3; ++d) dl[d] = sdl[d * MAXROWS + i];
+        row_dtangent(a, T, g, p, ssrc[i], dl, ssc[i], sw[i], sb + i, db);
+        double ydb = 0.0, zdb = 0.0;
+        for (int k = 0; k < K; ++k) {
+          ydb = fma(y[k], db[k], ydb);
+          zdb = fma(z[k], db[k], zdb);
+        }
+        dj += (stb[i] - sbz[i]) * ydb - sby[i] * zdb;
+      }
+      // + z . dF
+      for (int i = lane; i < K; i += 32) {
+        double df = 0.0;
+        if (cut_self >= 0) {
+          for (int d = 0; d < dm.dim; ++d) {
+            const int lo = T.lower[d][i];
+            if (lo >= 0)
+              df += (double)T.mon[i][d] * g.debn[p * g.s_ebn + ((int64_t)cut_self * dm.dim + d) * dm.KS + lo];
+          }
+        } else if (cf_self >= 0) {
+          const int q = T.lower[dface][i];
+          if (q >= 0 && T.tang[dface][q] >= 0)
+            df = (double)T.mon[i][dface] *
+                 g.dface[dface][p * g.s_face[dface] + (int64_t)cf_self * dm.KFS + T.tang[dface][q]];
+        }
+        dj = fma(z[i], df, dj);
+      }
+      dj = warp_sum(dj);
+      if (lane == 0 && dj != 0.0) atomicAdd(g.dJ + p, dj);
+    }
     __syncwarp();
   }
 }

@@ -119,16 +119,20 @@ __global__ void k_gather(GatherArgs a, int64_t n_slots, const int32_t* cut_cell)
 struct AdjArgs {
   const double* lam;        // [ncell] adjoint solution
   const double* phi;        // [ncell] forward solution
-  const double* dvol;       // [n_cut][KS] derivative of the volume moments
-  const double* deb;        // [n_cut][KS] of the EB moments
-  const double* debn;       // [n_cut][dim][KS] of the normal-weighted EB moments
-  const double* dface[3];   // [n_cutface[d]][KFS] of the face moments
+  // derivatives of the moment tables for parameter 0; parameter p's at + p * the stride
+  const double* dvol;       // [n_cut][KS] of the volume moments (stride s_vol)
+  const double* deb;        // [n_cut][KS] of the EB moments (stride s_vol)
+  const double* debn;       // [n_cut][dim][KS] of the normal-weighted EB moments (stride s_ebn)
+  const double* dface[3];   // [n_cutface[d]][KFS] of the face moments (stride s_face[d])
+  int n_par;                // parameters
+  int64_t s_vol, s_ebn, s_face[3];
   int64_t n_slots;          // systems [0, n_slots) (the individually solved ones)
   int32_t* next;            // work counter
-  double* scratch;          // per warp: MAXROWS * (2 MAXK + 2) doubles
-  double* dJ;               // accumulated derivative (one double)
+  double* scratch;          // per warp: MAXROWS * ADJ_SCRATCH doubles
+  double* dJ;               // [n_par] accumulated derivatives
 };
 constexpr int ADJ_WARPS = 4;
+constexpr int ADJ_SCRATCH = MAXK + 10;  // doubles per row of a warp's scratch
 cudaError_t stencil_adjoint_launch(unsigned blocks, cudaStream_t s, const LsArgs& a, const Tables& T,
                                    const AdjArgs& g);
 // k_lsq launchers (eb_build.cu): shared-memory attribute, then one launch over the systems of one

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -427,29 +428,56 @@ __global__ void k_geo_pack_idx(const int32_t* keep, const int64_t* pos, int64_t 
   if (t < n && keep[t]) dst[pos[t]] = src[t];
 }
 
-// ---------------------------------------------------------------- shape derivatives (radius)
+// ---------------------------------------------------------------- shape derivatives
 //
-// d/dr of the moment tables of the cells and faces cut by circle b, the fluid outside the circle (the
-// boundary moves with unit normal speed into the fluid as r grows); the cut sets are held fixed:
-//   volume moments  d/dr int_V xi^p dV / h^2 = - int_patch xi^p ds / h^2 = - eb / h   (transport);
-//   EB moments      the arc {c + r e(t)}: d/dr int f r dt = int (r grad f . e + f) dt
-//                   + f(t_b) r t_b' - f(t_a) r t_a', the ends sliding along the cell edges they lie on
-//                   (t' = cos t / (r sin t) on an x edge, -sin t / (r cos t) on a y edge); the normal
-//                   at fixed t does not turn;
-//   face moments    the covered chord |t - c_t| < s, s = (r^2 - d^2)^(1/2), grows at both ends with
-//                   speed r / s.
-__global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int body, const int32_t* __restrict__ cells,
-                                  int64_t n, const int32_t* __restrict__ cbody, const double* __restrict__ eb_mom,
+// Derivatives of the moment tables when the boundary moves with a normal speed V(x) along
+// N = (x - c)/r, the direction out of the body (ShapeVel: V = 1 on one body for its radius; V = -/+ f for
+// the amplitude of a level-set mode psi + a f with f = sin(2 pi k . x + theta), at a = 0, the sign
+// that of -psi's gradient along N: - for the outside of the bodies, + for the inside of one).  The cut
+// sets are held fixed.  With n = sgn N the normal out of the fluid (sgn = -1 outside, +1 inside), the
+// transport theorem on the patch gives (curvature 1/r in 2-D, mean curvature sum 2/r in 3-D)
+//   volume moments  d int_V xi^p = sgn int_patch xi^p V dA;
+//   EB moments      d int_patch F dA = int (grad F . N + curv F) V dA + oint_edges F V_e dl;
+//   normal moments  d int_patch F n dA = sgn [int (grad F . N + curv F) V N dA - int F grad_G V dA
+//                   + oint_edges F V_e N dl]   (d N = -grad_G V, the surface gradient);
+//   face moments    the disk (chord) the body cuts from a face plane grows along its rim with speed
+//                   V r / rho (rho its radius, its half-length in 2-D), the fluid part by sgn times that.
+// The edges of a patch lie on the cell's faces; an edge point moves within its face plane with the
+// in-surface speed V_e = -V (N . n_p) / (1 - (N . n_p)^2)^(1/2), n_p the face's normal out of the cell;
+// in 2-D the edges are the arc ends, which slide along the cell edges they lie on with the arc-angle
+// speed V t' (t' = cos t / (r sin t) on an x edge, -sin t / (r cos t) on a y edge).
+
+// the normal speed of sv at the physical point X of body b's boundary, and its gradient
+__device__ __forceinline__ double shape_speed(const ShapeVel& sv, int inside, int b, const double* X, int D,
+                                              double* gV) {
+  if (sv.kind == 0) {
+    for (int d = 0; d < D; ++d) gV[d] = 0.0;
+    return b == sv.body ? 1.0 : 0.0;
+  }
+  double a = sv.theta;
+  for (int d = 0; d < D; ++d) a += 2.0 * M_PI * sv.k[d] * X[d];
+  const double sg = inside ? 1.0 : -1.0, ca = cos(a);
+  for (int d = 0; d < D; ++d) gV[d] = sg * 2.0 * M_PI * sv.k[d] * ca;
+  return sg * sin(a);
+}
+
+__device__ __forceinline__ bool shape_moves(const ShapeVel& sv, int b) {
+  return b >= 0 && (sv.kind != 0 || b == sv.body);
+}
+
+__global__ void k_circle_cells_dv(Circles B, GlRule gl, int nx, double h, ShapeVel sv,
+                                  const int32_t* __restrict__ cells, int64_t n, const int32_t* __restrict__ cbody,
                                   int q, int K, double* dvol, double* deb, double* debn) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int c = cells[t];
+  const int b = cbody[c];
   double dv[28], de[28], dn[2][28];
   for (int k = 0; k < K; ++k) dv[k] = de[k] = dn[0][k] = dn[1][k] = 0.0;
-  if (cbody[c] == body) {
+  if (shape_moves(sv, b)) {
     const int ix = c % nx, iy = c / nx;
-    const double cx = (B.c[body][0] - (ix + 0.5) * h) / h, cy = (B.c[body][1] - (iy + 0.5) * h) / h;
-    const double R = B.r[body] / h;
+    const double cx = (B.c[b][0] - (ix + 0.5) * h) / h, cy = (B.c[b][1] - (iy + 0.5) * h) / h;
+    const double R = B.r[b] / h;
     // arc ends: angle, d(angle)/dR (R in units of h), sorted by angle
     double ang[8], dang[8];
     int na = 0;
@@ -489,7 +517,7 @@ __global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int bo
         dang[j] = dang[j - 1];
         dang[j - 1] = tmp;
       }
-    const double sgn = B.inside ? 1.0 : -1.0;  // normal out of the fluid
+    const double sgn = B.inside ? 1.0 : -1.0;  // n = sgn N, out of the fluid
     for (int i = 0; i < na; ++i) {
       const double a = ang[i], e = i + 1 < na ? ang[i + 1] : ang[0] + 2.0 * M_PI;
       const double da = dang[i], dE = i + 1 < na ? dang[i + 1] : dang[0];
@@ -502,9 +530,14 @@ __global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int bo
       for (int pc = 0; pc < npc; ++pc) {
         const double mm = a + (pc + 0.5) * span, hw = 0.5 * span;
         for (int g = 0; g < GEO_GL; ++g) {
-          const double th = mm + hw * gl.x[g], wt = gl.w[g] * hw;  // d theta
+          const double th = mm + hw * gl.x[g], ds = gl.w[g] * hw * R;  // arc length / h
           const double ct = cos(th), st = sin(th);
           const double x = cx + R * ct, y = cy + R * st;
+          const double X[2] = {B.c[b][0] + h * R * ct, B.c[b][1] + h * R * st};
+          double gv[2];
+          const double V = shape_speed(sv, B.inside, b, X, 2, gv);
+          const double gn = gv[0] * ct + gv[1] * st;
+          const double gG[2] = {h * (gv[0] - gn * ct), h * (gv[1] - gn * st)};
           double xp[GEO_MAXQ + 1], yp[GEO_MAXQ + 1];
           xp[0] = yp[0] = 1.0;
           for (int k = 1; k <= q; ++k) {
@@ -515,35 +548,38 @@ __global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int bo
             int p0, p1;
             mon2(k, &p0, &p1);
             const double f = xp[p0] * yp[p1];
-            // R grad_xi f . e (the h of grad_x and of R cancel)
-            double ge = 0.0;
-            if (p0 > 0) ge += p0 * xp[p0 - 1] * yp[p1] * ct;
-            if (p1 > 0) ge += p1 * xp[p0] * yp[p1 - 1] * st;
-            const double v = wt * (R * ge + f);
+            double gN = 0.0;  // grad_xi f . N
+            if (p0 > 0) gN += p0 * xp[p0 - 1] * yp[p1] * ct;
+            if (p1 > 0) gN += p1 * xp[p0] * yp[p1 - 1] * st;
+            const double v = ds * V * (gN + f / R);
+            dv[k] += sgn * ds * f * V;
             de[k] += v;
-            dn[0][k] += v * sgn * ct;
-            dn[1][k] += v * sgn * st;
+            dn[0][k] += sgn * (v * ct - ds * f * gG[0]);
+            dn[1][k] += sgn * (v * st - ds * f * gG[1]);
           }
         }
       }
-      // ends: + f(t_b) R t_b' - f(t_a) R t_a'
+      // ends: + f(t_b) V R t_b' - f(t_a) V R t_a'
       for (int end = 0; end < 2; ++end) {
         const double th = end ? e : a, dth = end ? dE : da, sg = end ? 1.0 : -1.0;
         const double ct = cos(th), st = sin(th);
         const double x = cx + R * ct, y = cy + R * st;
+        const double X[2] = {B.c[b][0] + h * R * ct, B.c[b][1] + h * R * st};
+        double gv[2];
+        const double se = sg * shape_speed(sv, B.inside, b, X, 2, gv) * R * dth;
         for (int k = 0; k < K; ++k) {
           int p0, p1;
           mon2(k, &p0, &p1);
-          const double v = sg * pow(x, p0) * pow(y, p1) * R * dth;
+          const double v = pow(x, p0) * pow(y, p1) * se;
           de[k] += v;
           dn[0][k] += v * sgn * ct;
           dn[1][k] += v * sgn * st;
         }
       }
     }
-    // d/dr with r = h R: the tables above are d/dR; d/dr = (1/h) d/dR.  Volume: -eb / h.
+    // the integrals above are per unit h (lengths in units of h): d/dt of the tables is (1/h) times them
     for (int k = 0; k < K; ++k) {
-      dv[k] = (B.inside ? 1.0 : -1.0) * eb_mom[t * K + k] / h;
+      dv[k] /= h;
       de[k] /= h;
       dn[0][k] /= h;
       dn[1][k] /= h;
@@ -557,25 +593,30 @@ __global__ void k_circle_cells_dr(Circles B, GlRule gl, int nx, double h, int bo
   }
 }
 
-__global__ void k_circle_faces_dr(Circles B, int nx, int dir, double h, int body, const int32_t* __restrict__ faces,
+__global__ void k_circle_faces_dv(Circles B, int nx, int dir, double h, ShapeVel sv, const int32_t* __restrict__ faces,
                                   int64_t n, const int32_t* __restrict__ fbody, int q, double* out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int f = faces[t];
+  const int b = fbody[f];
   double acc[GEO_MAXQ + 1];
   for (int k = 0; k <= q; ++k) acc[k] = 0.0;
-  if (fbody[f] == body) {
+  if (shape_moves(sv, b)) {
     const int mx = nx + (dir == 0), ix = f % mx, iy = f / mx;
     const double fc[2] = {dir == 0 ? ix * h : (ix + 0.5) * h, dir == 1 ? iy * h : (iy + 0.5) * h};
-    const double dn = (fc[dir] - B.c[body][dir]) / h, ct = (B.c[body][1 - dir] - fc[1 - dir]) / h;
-    const double R = B.r[body] / h, s2 = R * R - dn * dn;
+    const double dn = (fc[dir] - B.c[b][dir]) / h, ct = (B.c[b][1 - dir] - fc[1 - dir]) / h;
+    const double R = B.r[b] / h, s2 = R * R - dn * dn;
     if (s2 > 0.0) {
-      const double s = sqrt(s2), speed = R / s;  // d(end)/dR for both chord ends
-      // outside fluid loses length at both ends; inside fluid gains it
+      const double s = sqrt(s2);
+      // outside fluid loses length at both chord ends; inside fluid gains it
       const double sg = B.inside ? 1.0 : -1.0;
       for (int e = -1; e <= 1; e += 2) {
         const double end = ct + e * s;
         if (end > -0.5 && end < 0.5) {
+          double X[2], gv[2];
+          X[dir] = fc[dir];
+          X[1 - dir] = fc[1 - dir] + h * end;
+          const double speed = shape_speed(sv, B.inside, b, X, 2, gv) * R / s;  // d(end) per unit parameter / h
           double p = 1.0;
           for (int k = 0; k <= q; ++k) {
             acc[k] += sg * p * speed;
@@ -835,33 +876,12 @@ __device__ void disk_square(double cu, double cv, double rho, int inside, int q,
   for (int k = 0; k < K2; ++k) out[k] = full[k] + disk[k];
 }
 
-// one table of a cut cell's EB patch integrals (thread per cell and table): t = 0 int xi^p dA, t = 1..3
-// int xi^p n_(t-1) dA, t = 4 int xi^(p+e_d) n_d dA (the patch part of the volume moments, d the cell's
-// divergence direction); divided by h^2
-__global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double h, const int32_t* __restrict__ cells, int64_t n,
-                               const int32_t* __restrict__ cbody, int q, int K, double* eb, double* ebn,
-                               double* volp) {
-  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tt >= 5 * n) return;
-  const int64_t t = tt / 5;
-  const int table = (int)(tt % 5);
-  const int c = cells[t];
-  const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
-  const int b = cbody[c];
-  const double cx = (B.c[b][0] - (ix + 0.5) * h) / h, cy = (B.c[b][1] - (iy + 0.5) * h) / h;
-  const double cz = (B.c[b][2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
-  const double sgn = B.inside ? 1.0 : -1.0;  // normal out of the fluid: sgn (x - c) / R
-  // divergence-theorem direction (table 4): the smallest component of the centre offset, the direction
-  // most tangent to the patch (see k_sphere_vol)
-  const int dd = (fabs(cx) <= fabs(cy) && fabs(cx) <= fabs(cz)) ? 0 : (fabs(cy) <= fabs(cz) ? 1 : 2);
-  double acc[35];
-  int pk[35];  // exponents of monomial k, packed p0 | p1 << 4 | p2 << 8
-  for (int k = 0; k < K; ++k) {
-    int p[3];
-    mon3(k, p);
-    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
-    acc[k] = 0.0;
-  }
+// fn(x, y, z, ex, ey, ez, w) at the quadrature nodes of the patch of the sphere (cx, cy, cz, R) inside
+// the cell [-1/2, 1/2]^3 (cell-centred coordinates in units of h): (x, y, z) the node, (ex, ey, ez) =
+// node - centre = R N, w its area weight in units of h^2 (the rule of k_sphere_patch)
+template <class Fn>
+__device__ void sphere_patch_quad(double cx, double cy, double cz, double R, const GlRule& gl, const GlRuleT& glt,
+                                  Fn&& fn) {
   // z breakpoints: the range ends, tangencies with the edge lines x, y = +-1/2 and passes through the
   // square's corners
   const double zl = fmax(-0.5, cz - R), zh = fmin(0.5, cz + R);
@@ -903,9 +923,6 @@ __global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double 
       if (rho <= 0.0) continue;
       double a0[4], a1[4];
       const int narc = square_arcs(cx, cy, rho, a0, a1);
-      double zp[GEO_MAXQ + 2];
-      zp[0] = 1.0;
-      for (int k = 1; k <= q + 1; ++k) zp[k] = zp[k - 1] * z;
       for (int a = 0; a < narc; ++a) {
         const int npc = (int)ceil((a1[a] - a0[a]) / (0.25 * M_PI));
         const double span = (a1[a] - a0[a]) / npc;
@@ -913,30 +930,62 @@ __global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double 
           const double mm = a0[a] + (pc + 0.5) * span, hw = 0.5 * span;
           for (int g = 0; g < GEO_GL; ++g) {
             const double ph = mm + hw * gl.x[g];
-            const double w = wz * gl.w[g] * hw * R;  // dA = R dz dphi
             const double cp = cos(ph), sp = sin(ph);
-            const double x = cx + rho * cp, y = cy + rho * sp;
-            double f = w;
-            if (table >= 1 && table <= 3) {
-              const double e = table == 1 ? rho * cp : (table == 2 ? rho * sp : z - cz);
-              f *= sgn * e / R;
-            } else if (table == 4) {
-              f *= sgn * (dd == 0 ? rho * cp : (dd == 1 ? rho * sp : z - cz)) / R;
-            }
-            double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 2];
-            xp[0] = yp[0] = 1.0;
-            for (int k = 1; k <= q + 1; ++k) {
-              xp[k] = xp[k - 1] * x;
-              yp[k] = yp[k - 1] * y;
-            }
-            const int ex = table == 4 && dd == 0, ey = table == 4 && dd == 1, ez = table == 4 && dd == 2;
-            for (int k = 0; k < K; ++k)
-              acc[k] += f * xp[(pk[k] & 15) + ex] * yp[((pk[k] >> 4) & 15) + ey] * zp[(pk[k] >> 8) + ez];
+            fn(cx + rho * cp, cy + rho * sp, z, rho * cp, rho * sp, z - cz, wz * gl.w[g] * hw * R);  // dA = R dz dphi
           }
         }
       }
     }
   }
+}
+
+// one table of a cut cell's EB patch integrals (thread per cell and table): t = 0 int xi^p dA, t = 1..3
+// int xi^p n_(t-1) dA, t = 4 int xi^(p+e_d) n_d dA (the patch part of the volume moments, d the cell's
+// divergence direction); divided by h^2
+__global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double h, const int32_t* __restrict__ cells, int64_t n,
+                               const int32_t* __restrict__ cbody, int q, int K, double* eb, double* ebn,
+                               double* volp) {
+  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= 5 * n) return;
+  const int64_t t = tt / 5;
+  const int table = (int)(tt % 5);
+  const int c = cells[t];
+  const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
+  const int b = cbody[c];
+  const double cx = (B.c[b][0] - (ix + 0.5) * h) / h, cy = (B.c[b][1] - (iy + 0.5) * h) / h;
+  const double cz = (B.c[b][2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
+  const double sgn = B.inside ? 1.0 : -1.0;  // normal out of the fluid: sgn (x - c) / R
+  // divergence-theorem direction (table 4): the smallest component of the centre offset, the direction
+  // most tangent to the patch (see k_sphere_vol)
+  const int dd = (fabs(cx) <= fabs(cy) && fabs(cx) <= fabs(cz)) ? 0 : (fabs(cy) <= fabs(cz) ? 1 : 2);
+  double acc[35];
+  int pk[35];  // exponents of monomial k, packed p0 | p1 << 4 | p2 << 8
+  for (int k = 0; k < K; ++k) {
+    int p[3];
+    mon3(k, p);
+    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
+    acc[k] = 0.0;
+  }
+  sphere_patch_quad(cx, cy, cz, R, gl, glt,
+                    [&](double x, double y, double z, double ex, double ey, double ez, double w) {
+                      double f = w;
+                      if (table >= 1 && table <= 3) {
+                        const double e = table == 1 ? ex : (table == 2 ? ey : ez);
+                        f *= sgn * e / R;
+                      } else if (table == 4) {
+                        f *= sgn * (dd == 0 ? ex : (dd == 1 ? ey : ez)) / R;
+                      }
+                      double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 2], zp[GEO_MAXQ + 2];
+                      xp[0] = yp[0] = zp[0] = 1.0;
+                      for (int k = 1; k <= q + 1; ++k) {
+                        xp[k] = xp[k - 1] * x;
+                        yp[k] = yp[k - 1] * y;
+                        zp[k] = zp[k - 1] * z;
+                      }
+                      const int ex4 = table == 4 && dd == 0, ey4 = table == 4 && dd == 1, ez4 = table == 4 && dd == 2;
+                      for (int k = 0; k < K; ++k)
+                        acc[k] += f * xp[(pk[k] & 15) + ex4] * yp[((pk[k] >> 4) & 15) + ey4] * zp[(pk[k] >> 8) + ez4];
+                    });
   double* dst = table == 0 ? eb + t * K : (table == 4 ? volp + t * K : ebn + (t * 3 + table - 1) * K);
   for (int k = 0; k < K; ++k) dst[k] = acc[k];
 }
@@ -1009,6 +1058,180 @@ __global__ void k_geo_close_faces3(const uint8_t* __restrict__ cflag, int N, int
   if (cov) fflag[i] = 0;
 }
 
+// ---------------------------------------------------------------- 3-D shape derivatives
+//
+// The formulas at the 2-D derivative kernels above with the sphere's patch quadrature (k_sphere_patch)
+// and, for the edge terms, the arcs the sphere cuts from the cell's six face planes: on the face plane
+// xi_d = e the circle has radius rho = (R^2 - (e - c_d)^2)^(1/2), N . n_p = sign(e) (e - c_d) / R is
+// constant along it, and V_e dl = -V (N . n_p) R dt in the arc angle t.
+
+// fn(pos, ev, wl) at the quadrature nodes of the patch's edges: pos the node, ev = pos - centre = R N,
+// wl = -(N . n_p) R dt (V wl = V_e dl / h)
+template <class Fn>
+__device__ void sphere_edge_quad(const double* cc, double R, const GlRule& gl, Fn&& fn) {
+  for (int dd = 0; dd < 3; ++dd) {
+    const int u = dd == 0 ? 1 : 0, v = dd == 2 ? 1 : 2;
+    for (int s = -1; s <= 1; s += 2) {
+      const double e = 0.5 * s, dn = e - cc[dd], r2 = R * R - dn * dn;
+      if (!(r2 > 0.0)) continue;
+      const double rho = sqrt(r2), en = s * dn / R;
+      double a0[4], a1[4];
+      const int narc = square_arcs(cc[u], cc[v], rho, a0, a1);
+      for (int a = 0; a < narc; ++a) {
+        const int npc = (int)ceil((a1[a] - a0[a]) / (0.25 * M_PI));
+        const double span = (a1[a] - a0[a]) / npc;
+        for (int pc = 0; pc < npc; ++pc) {
+          const double mm = a0[a] + (pc + 0.5) * span, hw = 0.5 * span;
+          for (int g = 0; g < GEO_GL; ++g) {
+            const double tt = mm + hw * gl.x[g];
+            double pos[3], ev[3];
+            pos[dd] = e;
+            pos[u] = cc[u] + rho * cos(tt);
+            pos[v] = cc[v] + rho * sin(tt);
+            for (int d = 0; d < 3; ++d) ev[d] = pos[d] - cc[d];
+            fn(pos, ev, -en * R * gl.w[g] * hw);
+          }
+        }
+      }
+    }
+  }
+}
+
+// one derivative table of a cut cell (thread per cell and table): t = 0 the volume moments, t = 1 the EB
+// moments, t = 2..4 the EB moments weighted by n_(t-2)
+__global__ void k_sphere_cells_dv(Spheres B, GlRule gl, GlRuleT glt, int N, double h, ShapeVel sv,
+                                  const int32_t* __restrict__ cells, int64_t n, const int32_t* __restrict__ cbody,
+                                  int q, int K, double* dvol, double* deb, double* debn) {
+  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= 5 * n) return;
+  const int64_t t = tt / 5;
+  const int table = (int)(tt % 5);
+  const int c = cells[t];
+  const int b = cbody[c];
+  double acc[35];
+  int pk[35];
+  for (int k = 0; k < K; ++k) {
+    int p[3];
+    mon3(k, p);
+    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
+    acc[k] = 0.0;
+  }
+  if (shape_moves(sv, b)) {
+    const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
+    const double* C = B.c[b];
+    const double cx = (C[0] - (ix + 0.5) * h) / h, cy = (C[1] - (iy + 0.5) * h) / h;
+    const double cz = (C[2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
+    const double sgn = B.inside ? 1.0 : -1.0;
+    const int dn = table - 2;
+    auto add = [&](double x, double y, double z, const double* Nv, double cf, double cg) {
+      double xp[GEO_MAXQ + 1], yp[GEO_MAXQ + 1], zp[GEO_MAXQ + 1];
+      xp[0] = yp[0] = zp[0] = 1.0;
+      for (int k = 1; k <= q; ++k) {
+        xp[k] = xp[k - 1] * x;
+        yp[k] = yp[k - 1] * y;
+        zp[k] = zp[k - 1] * z;
+      }
+      for (int k = 0; k < K; ++k) {
+        const int p0 = pk[k] & 15, p1 = (pk[k] >> 4) & 15, p2 = pk[k] >> 8;
+        double v = cf * xp[p0] * yp[p1] * zp[p2];
+        if (cg != 0.0) {
+          double gN = 0.0;  // grad_xi f . N
+          if (p0 > 0) gN += p0 * xp[p0 - 1] * yp[p1] * zp[p2] * Nv[0];
+          if (p1 > 0) gN += p1 * xp[p0] * yp[p1 - 1] * zp[p2] * Nv[1];
+          if (p2 > 0) gN += p2 * xp[p0] * yp[p1] * zp[p2 - 1] * Nv[2];
+          v += cg * gN;
+        }
+        acc[k] += v;
+      }
+    };
+    sphere_patch_quad(cx, cy, cz, R, gl, glt,
+                      [&](double x, double y, double z, double ex, double ey, double ez, double w) {
+                        const double Nv[3] = {ex / R, ey / R, ez / R};
+                        const double X[3] = {C[0] + h * ex, C[1] + h * ey, C[2] + h * ez};
+                        double gv[3];
+                        const double V = shape_speed(sv, B.inside, b, X, 3, gv);
+                        if (table == 0) {
+                          add(x, y, z, Nv, sgn * w * V, 0.0);
+                        } else if (table == 1) {
+                          add(x, y, z, Nv, w * V * 2.0 / R, w * V);
+                        } else {
+                          const double gn = gv[0] * Nv[0] + gv[1] * Nv[1] + gv[2] * Nv[2];
+                          const double gG = h * (gv[dn] - gn * Nv[dn]);
+                          add(x, y, z, Nv, sgn * w * (V * 2.0 / R * Nv[dn] - gG), sgn * w * V * Nv[dn]);
+                        }
+                      });
+    if (table >= 1) {
+      const double cc[3] = {cx, cy, cz};
+      sphere_edge_quad(cc, R, gl, [&](const double* pos, const double* ev, double wl) {
+        const double X[3] = {C[0] + h * ev[0], C[1] + h * ev[1], C[2] + h * ev[2]};
+        double gv[3];
+        double cf = shape_speed(sv, B.inside, b, X, 3, gv) * wl;
+        if (table >= 2) cf *= sgn * ev[dn] / R;
+        add(pos[0], pos[1], pos[2], ev, cf, 0.0);
+      });
+    }
+    for (int k = 0; k < K; ++k) acc[k] /= h;
+  }
+  double* dst = table == 0 ? dvol + t * K : (table == 1 ? deb + t * K : debn + (t * 3 + table - 2) * K);
+  for (int k = 0; k < K; ++k) dst[k] = acc[k];
+}
+
+// derivative of the tangential moments of the cut faces normal to dir (thread per face)
+__global__ void k_sphere_faces_dv(Spheres B, GlRule gl, int N, int dir, double h, ShapeVel sv,
+                                  const int32_t* __restrict__ faces, int64_t n, const int32_t* __restrict__ fbody,
+                                  int q, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int f = faces[t];
+  const int b = fbody[f];
+  const int K2 = (q + 1) * (q + 2) / 2;
+  double acc[28];
+  for (int k = 0; k < K2; ++k) acc[k] = 0.0;
+  if (shape_moves(sv, b)) {
+    const int m0 = N + (dir == 0), m1 = N + (dir == 1);
+    const int i3[3] = {f % m0, (f / m0) % m1, f / (m0 * m1)};
+    const int u = dir == 0 ? 1 : 0, v = dir == 2 ? 1 : 2;
+    const double dn = (i3[dir] * h - B.c[b][dir]) / h;
+    const double cu = (B.c[b][u] - (i3[u] + 0.5) * h) / h, cv = (B.c[b][v] - (i3[v] + 0.5) * h) / h;
+    const double R = B.r[b] / h, r2 = R * R - dn * dn;
+    if (r2 > 0.0) {
+      const double rho = sqrt(r2), sg = B.inside ? 1.0 : -1.0;
+      double a0[4], a1[4];
+      const int narc = square_arcs(cu, cv, rho, a0, a1);
+      for (int a = 0; a < narc; ++a) {
+        const int npc = (int)ceil((a1[a] - a0[a]) / (0.25 * M_PI));
+        const double span = (a1[a] - a0[a]) / npc;
+        for (int pc = 0; pc < npc; ++pc) {
+          const double mm = a0[a] + (pc + 0.5) * span, hw = 0.5 * span;
+          for (int g = 0; g < GEO_GL; ++g) {
+            const double tt = mm + hw * gl.x[g];
+            const double uu = cu + rho * cos(tt), vv = cv + rho * sin(tt);
+            double X[3], gv[3];
+            X[dir] = i3[dir] * h;
+            X[u] = (i3[u] + 0.5) * h + h * uu;
+            X[v] = (i3[v] + 0.5) * h + h * vv;
+            // the rim moves with V R / rho; dl / h = rho dt
+            const double c0 = sg * shape_speed(sv, B.inside, b, X, 3, gv) * R * gl.w[g] * hw;
+            double up[GEO_MAXQ + 1], vp[GEO_MAXQ + 1];
+            up[0] = vp[0] = 1.0;
+            for (int k = 1; k <= q; ++k) {
+              up[k] = up[k - 1] * uu;
+              vp[k] = vp[k - 1] * vv;
+            }
+            for (int k = 0; k < K2; ++k) {
+              int pa, pb;
+              mon2(k, &pa, &pb);
+              acc[k] += c0 * up[pa] * vp[pb];
+            }
+          }
+        }
+      }
+    }
+    for (int k = 0; k < K2; ++k) acc[k] /= h;
+  }
+  for (int k = 0; k < K2; ++k) out[t * K2 + k] = acc[k];
+}
+
 }  // namespace eb
 
 using namespace eb;
@@ -1021,33 +1244,58 @@ bool geometry_matches(const eb_geometry* g, int dim, const int* n, int n_cut) {
   return d.dim == dim && d.n[0] == n[0] && d.n[1] == n[1] && (dim < 3 || d.n[2] == n[2]) && d.n_cut == n_cut;
 }
 
-// d/dr of the moment tables of a device geometry for the radius of circle `body` (2-D), into caller
-// arrays laid out like the tables (dface[d]: [n_cutface[d]][K_F]); stream-ordered
-cudaError_t geometry_radius_derivative(const eb_geometry* g, int body, double* dvol, double* deb, double* debn,
-                                       double* const* dface, cudaStream_t s) {
+// derivatives of the moment tables of a device geometry for the boundary velocity sv, into caller arrays
+// laid out like the tables (dface[d]: [n_cutface[d]][K_F]); stream-ordered
+cudaError_t geometry_shape_derivative(const eb_geometry* g, const ShapeVel& sv, double* dvol, double* deb,
+                                      double* debn, double* const* dface, cudaStream_t s) {
   static const GlRule gl = gl_rule<GEO_GL>();
+  static const GlRuleT glt = gl_rule<GEO_GLT>();
   const eb_geom& d = g->desc;
-  if (d.dim != 2 || body < 0 || body >= g->n_body) return cudaErrorInvalidValue;
-  Circles B;
+  if ((sv.kind == 0 && (sv.body < 0 || sv.body >= g->n_body)) || sv.kind < 0 || sv.kind > 1)
+    return cudaErrorInvalidValue;
+  const int q = d.moment_degree;
+  const int N = d.n[0];
+  const double h = d.h;
+  if (d.dim == 2) {
+    Circles B;
+    B.n = g->n_body;
+    B.inside = g->inside;
+    for (int b = 0; b < g->n_body; ++b) {
+      B.c[b][0] = g->centers[b][0];
+      B.c[b][1] = g->centers[b][1];
+      B.r[b] = g->radii[b];
+    }
+    const int K = (q + 1) * (q + 2) / 2;
+    if (d.n_cut > 0) {
+      k_circle_cells_dv<<<(unsigned)((d.n_cut + 127) / 128), 128, 0, s>>>(B, gl, N, h, sv, d.cut_cell, d.n_cut,
+                                                                         g->cell_body, q, K, dvol, deb, debn);
+      eb::count_launch();
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      if (d.n_cutface[dir] == 0) continue;
+      k_circle_faces_dv<<<(unsigned)((d.n_cutface[dir] + 127) / 128), 128, 0, s>>>(
+          B, N, dir, h, sv, d.cutface[dir], d.n_cutface[dir], g->face_body[dir], q, dface[dir]);
+      eb::count_launch();
+    }
+    return cudaGetLastError();
+  }
+  Spheres B;
   B.n = g->n_body;
   B.inside = g->inside;
   for (int b = 0; b < g->n_body; ++b) {
-    B.c[b][0] = g->centers[b][0];
-    B.c[b][1] = g->centers[b][1];
+    for (int k = 0; k < 3; ++k) B.c[b][k] = g->centers[b][k];
     B.r[b] = g->radii[b];
   }
-  const int q = d.moment_degree, K = (q + 1) * (q + 2) / 2;
-  const int N = d.n[0];
-  const double h = d.h;
+  const int K = (q + 1) * (q + 2) * (q + 3) / 6;
   if (d.n_cut > 0) {
-    k_circle_cells_dr<<<(unsigned)((d.n_cut + 127) / 128), 128, 0, s>>>(B, gl, N, h, body, d.cut_cell, d.n_cut,
-                                                                       g->cell_body, d.eb_mom, q, K, dvol, deb, debn);
+    k_sphere_cells_dv<<<(unsigned)((5 * (int64_t)d.n_cut + 127) / 128), 128, 0, s>>>(
+        B, gl, glt, N, h, sv, d.cut_cell, d.n_cut, g->cell_body, q, K, dvol, deb, debn);
     eb::count_launch();
   }
-  for (int dir = 0; dir < 2; ++dir) {
+  for (int dir = 0; dir < 3; ++dir) {
     if (d.n_cutface[dir] == 0) continue;
-    k_circle_faces_dr<<<(unsigned)((d.n_cutface[dir] + 127) / 128), 128, 0, s>>>(
-        B, N, dir, h, body, d.cutface[dir], d.n_cutface[dir], g->face_body[dir], q, dface[dir]);
+    k_sphere_faces_dv<<<(unsigned)((d.n_cutface[dir] + 127) / 128), 128, 0, s>>>(
+        B, gl, N, dir, h, sv, d.cutface[dir], d.n_cutface[dir], g->face_body[dir], q, dface[dir]);
     eb::count_launch();
   }
   return cudaGetLastError();
@@ -1532,5 +1780,60 @@ extern "C" eb_status eb_geometry_table(const eb_geometry* g, int32_t which, int3
   if (!dst_host) return EB_OK;
   if (cap_bytes < nb) { set_error("eb_geometry_table: destination too small"); return EB_ERR_INVALID; }
   if (nb > 0) EB_CUDA(cudaMemcpy(dst_host, src, (size_t)nb, cudaMemcpyDeviceToHost));
+  return EB_OK;
+}
+
+extern "C" eb_status eb_geometry_shape_table(const eb_geometry* g, int32_t kind, int32_t body, const double* mode_host,
+                                             int32_t which, int32_t dir, double* dst_host, int64_t cap_bytes,
+                                             int64_t* bytes) {
+  if (!g || !bytes) { set_error("eb_geometry_shape_table: null argument"); return EB_ERR_INVALID; }
+  const eb_geom& d = g->desc;
+  const int D = d.dim, q = d.moment_degree;
+  const int KS = D == 2 ? (q + 1) * (q + 2) / 2 : (q + 1) * (q + 2) * (q + 3) / 6;
+  const int KF = D == 2 ? q + 1 : (q + 1) * (q + 2) / 2;
+  ShapeVel sv;
+  memset(&sv, 0, sizeof(sv));
+  sv.kind = kind;
+  sv.body = body;
+  if (kind == 1) {
+    if (!mode_host) { set_error("eb_geometry_shape_table: the mode is required"); return EB_ERR_INVALID; }
+    for (int k = 0; k < 3; ++k) sv.k[k] = mode_host[k];
+    sv.theta = mode_host[3];
+  } else if (kind != 0 || body < 0 || body >= g->n_body) {
+    set_error("eb_geometry_shape_table: kind 0 (radius of a body) or 1 (level-set mode)");
+    return EB_ERR_INVALID;
+  }
+  if (which == EB_TABLE_FACE_MOM && (dir < 0 || dir >= D)) { set_error("eb_geometry_shape_table: dir"); return EB_ERR_INVALID; }
+  int64_t nb = 0;
+  switch (which) {
+    case EB_TABLE_VOL_MOM: case EB_TABLE_EB_MOM: nb = (int64_t)d.n_cut * KS * 8; break;
+    case EB_TABLE_EB_NMOM: nb = (int64_t)d.n_cut * D * KS * 8; break;
+    case EB_TABLE_FACE_MOM: nb = (int64_t)d.n_cutface[dir] * KF * 8; break;
+    default: set_error("eb_geometry_shape_table: volume, EB, normal EB or face moments"); return EB_ERR_INVALID;
+  }
+  *bytes = nb;
+  if (!dst_host) return EB_OK;
+  if (cap_bytes < nb) { set_error("eb_geometry_shape_table: destination too small"); return EB_ERR_INVALID; }
+  const int64_t nc = std::max<int64_t>(1, d.n_cut);
+  std::vector<void*> tmp;
+  auto get = [&](int64_t n) -> double* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)n * 8) != cudaSuccess) return nullptr;
+    tmp.push_back(p);
+    return (double*)p;
+  };
+  double* dv = get(nc * KS);
+  double* de = get(nc * KS);
+  double* dn = get(nc * D * KS);
+  double* df[3] = {nullptr, nullptr, nullptr};
+  bool ok = dv && de && dn;
+  for (int k = 0; k < D && ok; ++k) ok = (df[k] = get(std::max<int64_t>(1, d.n_cutface[k]) * KF)) != nullptr;
+  cudaError_t e = ok ? geometry_shape_derivative(g, sv, dv, de, dn, df, 0) : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess && nb > 0) {
+    const double* src = which == EB_TABLE_VOL_MOM ? dv : (which == EB_TABLE_EB_MOM ? de : (which == EB_TABLE_EB_NMOM ? dn : df[dir]));
+    e = cudaMemcpy(dst_host, src, (size_t)nb, cudaMemcpyDeviceToHost);
+  }
+  for (void* p : tmp) cudaFree(p);
+  if (e != cudaSuccess) { set_error(std::string("eb_geometry_shape_table: ") + cudaGetErrorString(e)); return e == cudaErrorMemoryAllocation ? EB_ERR_OOM : EB_ERR_CUDA; }
   return EB_OK;
 }

@@ -17,9 +17,17 @@ struct eb_geometry;
 
 namespace eb {
 
-// d/dr of a device geometry's moment tables for the radius of circle `body` (eb_geom.cu)
-cudaError_t geometry_radius_derivative(const eb_geometry* g, int body, double* dvol, double* deb, double* debn,
-                                       double* const* dface, cudaStream_t s);
+// A normal velocity of the embedded boundary, along N = (x - c)/r (out of each body), for the moment
+// tables' shape derivatives (eb_geom.cu): kind 0 the radius of body `body` (unit speed on its boundary);
+// kind 1 the amplitude a of the level-set mode a sin(2 pi k . x + theta) added to the distance function
+// of every body, at a = 0 (speed -sin(...) outside the bodies, +sin(...) inside one).
+struct ShapeVel {
+  int kind, body;
+  double k[3], theta;
+};
+// the tables' derivatives for sv, laid out like the tables (eb_geom.cu)
+cudaError_t geometry_shape_derivative(const eb_geometry* g, const ShapeVel& sv, double* dvol, double* deb,
+                                      double* debn, double* const* dface, cudaStream_t s);
 int geometry_bodies(const eb_geometry* g);
 int64_t geometry_cutfaces(const eb_geometry* g, int d);
 bool geometry_matches(const eb_geometry* g, int dim, const int* n, int n_cut);
