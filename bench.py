@@ -65,7 +65,8 @@ def parse():
     p.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 GPU solve timed once")
     p.add_argument("--out", default=None)
     p.add_argument("--batch", type=int, default=256, help="geometries of --mode batch")
-    p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch", "sweep", "adjoint"],
+    p.add_argument("--batch-dim", type=int, default=2, choices=[2, 3], help="dimension of --mode batch")
+    p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch", "sweep", "adjoint", "peak"],
                    help="build: one stencil build and exit; apply: build plus 3 FP32 applies (profiling cases); "
                         "sweep: the 2-D convergence sweep (five circles, 128^2..1024^2, Q = 2 and 4)")
     p.add_argument("--sweep-n", default="128,256,512,1024", help="grids of --mode sweep")
@@ -327,6 +328,14 @@ def main():
     if args.mode == "adjoint":
         run_adjoint(args, P, torch)
         return
+    if args.mode == "peak":
+        rates = {str(b): P.eb_fp64_fma_rate(blocks_per_sm=b, iters=1 << 16) for b in (2, 4, 8, 16)}
+        print(json.dumps({"mode": "peak", "fp64_fma_tflops": rates, "sm_count": sms, "sm_max_mhz": sm_max,
+                          "derived_fp64_tflops": fp64_peak_tflops(sm_max, sms)}))
+        return
+    if args.mode in ("build", "apply"):
+        run_operator(args, P, torch)
+        return
     if g is None:
         g, man, rho_h, Phi_h, geb_h, gw_h, t_geom = make_problem(args.n)
     # the same moment tables generated on the device (eb_geometry_spheres), timed once: the host generator's
@@ -346,18 +355,6 @@ def main():
     g_wall = torch.tensor(gw_h, device=dev)
     volmask = torch.tensor((g.flag > 0).astype(np.float64), device=dev)
     stream = torch.cuda.current_stream()
-    if args.mode != "step":
-        st = P.eb_build_stencils(dg, order=args.order)
-        if args.mode == "apply":
-            import eb_inputs as E
-            x = torch.tensor(E.seeded_field(3, g.ncell), dtype=torch.float32, device=dev)
-            y = torch.empty_like(x)
-            for _ in range(3):
-                P.eb_apply(st, x, y, kappa_weighted=True)
-        torch.cuda.synchronize()
-        print(json.dumps({"mode": args.mode, "n": args.n, "build_info": st.info}))
-        return
-
     tol = args.tol
 
     def solve_timed(st, tol_, mixed, time_applies=False):
@@ -525,6 +522,24 @@ def main():
             json.dump(line, open(args.out, "w"), indent=1)
 
 
+def run_operator(args, P, torch):
+    """--mode build / apply (profiling runs): the benchmark geometry (the unit cube minus the sphere
+    r = 0.35 at 0.5 + delta, delta ~ U[-h/2, h/2)^3 from SplitMix64(2)) with its moment tables generated on
+    the device, one stencil build, and (apply) three FP32 applies to phi ~ U[-1, 1] (seed 3)."""
+    import eb_inputs as E
+    h = 1.0 / args.n
+    c = 0.5 + E.uniform(2, 3, -0.5 * h, 0.5 * h)
+    G = P.eb_geometry_spheres(args.n, [tuple(c)], [0.35], moment_degree=4)
+    st = P.eb_build_stencils(G, order=args.order)
+    if args.mode == "apply":
+        x = torch.tensor(E.seeded_field(3, st.ncell), dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            P.eb_apply(st, x, y, kappa_weighted=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": args.mode, "n": args.n, "build_info": st.info}))
+
+
 def run_sweep(args, P, torch):
     """The 2-D convergence sweep: the unit square minus the circle r = 0.3 at (0.51, 0.49) and four seeded
     circles (radii U[0.05, 0.15], clearance 0.04, SplitMix64(1)), phi = sin(2 pi x) cos(3 pi y) with its
@@ -611,19 +626,28 @@ def run_adjoint(args, P, torch):
 
 
 def run_batch(args, P, torch):
-    """Many-instance batch: --batch seeded 2-D geometries (the unit square minus a circle, centre
-    0.5 + U[-0.1, 0.1)^2, radius U[0.2, 0.3), grid sizes 2^k with k ~ U{5..9}, i.e. 32^2..512^2, all from
-    SplitMix64(11)), built with one least-squares launch against one build per geometry.  Reports LS
-    systems per second for both (each system a face's weighted LS solve)."""
+    """Many-instance batch.  2-D (--batch-dim 2): --batch seeded geometries, the unit square minus a
+    circle (centre 0.5 + U[-0.1, 0.1)^2, radius U[0.2, 0.3), grid sizes 2^k with k ~ U{5..9}, i.e.
+    32^2..512^2); 3-D (--batch-dim 3): the unit cube minus a sphere (centre 0.5 + U[-0.05, 0.05)^3,
+    radius U[0.25, 0.35), grids 64^3, 96^3 or 128^3); all from SplitMix64(11).  Build: one least-squares
+    launch for the batch against one build per geometry (LS systems per second).  Solve: kappa L phi =
+    kappa with homogeneous Dirichlet data to a relative residual of 1e-12, the batched refined solve
+    (one graph launch) against one eb_solve per geometry (systems solved per second)."""
     import eb_inputs as E
     from eb_inputs.rng import SplitMix64
     rng = SplitMix64(11)
     gs = []
     for i in range(args.batch):
-        k = 5 + int(rng.next_u64() % 5)
-        cx, cy = 0.4 + 0.2 * rng.next_double(), 0.4 + 0.2 * rng.next_double()
-        r = 0.2 + 0.1 * rng.next_double()
-        gs.append(E.circle_config(2 ** k, center=(cx, cy), r=r))
+        if args.batch_dim == 2:
+            k = 5 + int(rng.next_u64() % 5)
+            cx, cy = 0.4 + 0.2 * rng.next_double(), 0.4 + 0.2 * rng.next_double()
+            r = 0.2 + 0.1 * rng.next_double()
+            gs.append(E.circle_config(2 ** k, center=(cx, cy), r=r))
+        else:
+            N = (64, 96, 128)[int(rng.next_u64() % 3)]
+            c = [0.45 + 0.1 * rng.next_double() for _ in range(3)]
+            r = 0.25 + 0.1 * rng.next_double()
+            gs.append(E.Geometry(3, N, np.array([c]), np.array([r]), False, 4, name=f"sphere-{N}"))
     dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
     torch.cuda.synchronize()
 
@@ -654,11 +678,52 @@ def run_batch(args, P, torch):
         tb.append(time.perf_counter() - t0)
         del out
     ms, mb = float(np.median(ts)), float(np.median(tb))
+    # the solves, on one batch of stencils
+    sts = P.eb_build_stencils_batch(dgs, order=args.order)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    rho = [torch.ones(g.ncell, **f64) for g in gs]
+    geb = [torch.zeros(max(len(g.cut_cells), 1), **f64) for g in gs]
+    gw = [torch.zeros(max(len(P.eb_wall_faces(st)), 1), **f64) for st in sts]
+    phis = [torch.zeros(g.ncell, **f64) for g in gs]
+    t0 = time.perf_counter()
+    bs = P.BatchSolver(sts)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    tss, tbs, its_s, its_b = [], [], 0, 0
+    for step in range(max(1, args.warmup) + args.steps):
+        for x in phis:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf_s = [P.eb_solve(st, r_, e_, w_, x, tol=1e-12) for st, r_, e_, w_, x in zip(sts, rho, geb, gw, phis)]
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        ref = [x.clone() for x in phis]
+        for x in phis:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf_b = bs.solve(rho, geb, gw, phis, tol=1e-12)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
+        if step >= max(1, args.warmup):
+            tss.append(t_seq)
+            tbs.append(t_bat)
+            its_s = sum(i["iterations"] for i in inf_s)
+            its_b = sum(i["iterations"] for i in inf_b)
+    dev = max(float((x - y).abs().max() / y.abs().max()) for x, y in zip(phis, ref))
+    mss, mbs = float(np.median(tss)), float(np.median(tbs))
     sizes = [g.N for g in gs]
-    print(json.dumps({"mode": "batch", "metric": "LS systems/s (many-instance batch, 2-D)", "unit": "systems/s",
-                      "geometries": len(gs), "grid_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
+    print(json.dumps({"mode": "batch", "dim": args.batch_dim, "metric": "LS systems/s (many-instance batch)",
+                      "unit": "systems/s", "geometries": len(gs),
+                      "grid_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
                       "systems_per_pass": systems, "batch_value": systems / mb, "batch_seconds": mb,
                       "sequential_value": systems / ms, "sequential_seconds": ms, "speedup": ms / mb,
+                      "solve": {"batch_seconds": mbs, "sequential_seconds": mss, "speedup": mss / mbs,
+                                "batch_systems_per_s": len(gs) / mbs, "sequential_systems_per_s": len(gs) / mss,
+                                "graph_setup_seconds": t_setup, "iterations_batch": its_b,
+                                "iterations_sequential": its_s, "max_rel_diff_vs_sequential": dev,
+                                "tol": 1e-12},
                       "steps": args.steps, "order": args.order, "data": "synthetic"}))
 
 

@@ -191,6 +191,34 @@ typedef struct eb_solve_info {
 eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
                    const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream);
 
+/* Batched solve: the mixed-precision refinement of eb_solve (Sec. 2.3 system,
+ * solved as eb_solve does) for n independent stencil sets at once, as one
+ * CUDA graph launch per call.  Per system, a graph loop (conditional WHILE
+ * node) runs the refinement sweeps -- FP64 residual with the FP64 operator,
+ * an inner FP32 BiCGStab as a nested loop, the FP64 correction -- and
+ * one-thread kernels set the loop conditions on the device from the
+ * device-resident scalars: no host synchronisation inside the solve, the
+ * systems' loops side by side.  Every loop stops at its iteration cap.
+ *
+ * eb_batch_solver_create: st[n] (host array of handles, which must outlive
+ * the solver and are not used concurrently by other solves); opts as for
+ * eb_solve (mixed must be 1; check_every is ignored); sets up each system's
+ * preconditioner, its vectors (about 72 bytes per cell) and the graph.
+ * eb_batch_solve: host arrays of device pointers rho[n], g_eb[n], g_wall[n]
+ * (the arrays may be NULL when no system has EB or wall faces), phi[n]
+ * (in: initial guess, out: solution, FP64); tol as for eb_solve;
+ * infos[n] (may be NULL) as for eb_solve without the apply timings.
+ * Returns EB_ERR_NOT_CONVERGED naming the first system that did not
+ * converge (its phi holds the last iterate; the others are solved).
+ * Synchronises the stream once, at the end. */
+typedef struct eb_batch_solver eb_batch_solver;
+eb_status eb_batch_solver_create(const eb_stencils* const* st, int32_t n, const eb_solve_opts* opts,
+                                 eb_batch_solver** out, eb_stream_t stream);
+eb_status eb_batch_solve(eb_batch_solver* b, const double* const* rho, const double* const* g_eb,
+                         const double* const* g_wall, double tol, double* const* phi, eb_solve_info* infos,
+                         eb_stream_t stream);
+void eb_batch_solver_destroy(eb_batch_solver* b);
+
 /* Error norms of Sec. 3.3 over the volumes: L_inf, L1 = sum |e||V| / sum|V|,
  * L2 = (sum e^2 |V| / sum |V|)^(1/2).  err: [ncell] FP64 device; out_host[3]. */
 eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, eb_stream_t stream);
@@ -335,6 +363,12 @@ void eb_stencils_destroy(eb_stencils* st);
 const char* eb_status_string(eb_status s);
 const char* eb_last_error_message(void);
 int32_t eb_abi_version(void);
+
+/* Measured FP64 FMA throughput of the device (the FP64 roofline's
+ * denominator): blocks_per_sm x SM-count blocks of 256 threads, each thread
+ * eight independent FMA chains of iters steps, timed with CUDA events after a
+ * warm-up launch; *tflops_host = 2 x FMAs / time in TFLOP/s.  Synchronous. */
+eb_status eb_fp64_fma_rate(int32_t blocks_per_sm, int64_t iters, double* tflops_host, eb_stream_t stream);
 
 /* Cumulative number of CUDA kernels this library has launched in the
  * process (all threads); differences around a region count its launches. */

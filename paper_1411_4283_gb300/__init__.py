@@ -120,6 +120,10 @@ def load():
         "eb_geometry_table": (i32, [_vp, i32, i32, _vp, i64, P(i64)]),
         "eb_geometry_shape_table": (i32, [_vp, i32, i32, P(dbl), i32, i32, P(dbl), i64, P(i64)]),
         "eb_adjoint_radii": (i32, [_vp, _vp, _vp, P(dbl), P(dbl), _vp]),
+        "eb_batch_solver_create": (i32, [P(_vp), i32, P(EbSolveOpts), P(_vp), _vp]),
+        "eb_batch_solve": (i32, [_vp, P(_vp), P(_vp), P(_vp), dbl, P(_vp), P(EbSolveInfo), _vp]),
+        "eb_batch_solver_destroy": (None, [_vp]),
+        "eb_fp64_fma_rate": (i32, [i32, i64, P(dbl), _vp]),
         "eb_adjoint_shape": (i32, [_vp, _vp, _vp, i32, P(dbl), P(dbl), P(dbl), P(dbl), P(EbAdjointInfo), _vp]),
     }
     for name, (res, args) in sig.items():
@@ -424,6 +428,44 @@ def eb_solve(st: Stencils, rho, g_eb, g_wall, phi, tol=1e-12, mixed=True, inner_
     return d
 
 
+def eb_fp64_fma_rate(blocks_per_sm=8, iters=1 << 16, stream=None) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s (see eb.h)."""
+    out = ctypes.c_double()
+    _check(load().eb_fp64_fma_rate(int(blocks_per_sm), int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+class BatchSolver:
+    """The batched refined solve of several stencil sets (eb_batch_solver_*): one CUDA graph launch per
+    solve, the systems' refinement loops run on the device side by side (see eb.h)."""
+
+    def __init__(self, stencils, inner_tol=1e-5, max_inner=20000, max_outer=40, max_iters=400000, precond="mg",
+                 stream=None):
+        lib = load()
+        self.stencils = list(stencils)  # kept alive with the solver
+        o = EbSolveOpts(1, inner_tol, max_inner, max_outer, max_iters, 1, {"jacobi": 0, "mg": 1}[precond])
+        hs = (ctypes.c_void_p * len(self.stencils))(*[st.handle for st in self.stencils])
+        self.handle = ctypes.c_void_p()
+        _check(lib.eb_batch_solver_create(hs, len(self.stencils), ctypes.byref(o), ctypes.byref(self.handle),
+                                          _stream(stream)))
+
+    def solve(self, rho, g_eb, g_wall, phi, tol=1e-12, stream=None, allow_not_converged=False) -> list:
+        """rho, g_eb, g_wall, phi: lists of device FP64 tensors, one per system; phi in/out."""
+        n = len(self.stencils)
+        arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
+        infos = (EbSolveInfo * n)()
+        code = load().eb_batch_solve(self.handle, arr(rho), arr(g_eb), arr(g_wall), tol, arr(phi), infos,
+                                     _stream(stream))
+        if not (allow_not_converged and code == 4):
+            _check(code)
+        return [infos[k].as_dict() for k in range(n)]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.eb_batch_solver_destroy(self.handle)
+            self.handle = None
+
+
 def eb_norms(st: Stencils, err, stream=None) -> dict:
     out = (ctypes.c_double * 3)()
     _check(load().eb_norms(st.handle, _ptr(err), out, _stream(stream)))
@@ -476,5 +518,5 @@ def eb_kernel_launches() -> int:
     return int(load().eb_kernel_launches())
 
 
-__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "eb_geometry_spheres", "GpuGeometry", "eb_adjoint_radii", "eb_adjoint_shape", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
+__all__ = ["eb_kernel_launches", "eb_lsq_batch_noalloc", "eb_geometry_circles", "eb_geometry_spheres", "GpuGeometry", "eb_adjoint_radii", "eb_adjoint_shape", "BatchSolver", "eb_fp64_fma_rate", "load", "lib_path", "DeviceGeometry", "Stencils", "eb_build_stencils", "eb_apply", "eb_bc_rhs", "eb_solve",
            "eb_norms", "eb_stencil_query", "eb_wall_faces", "eb_last_error_faces", "EbError", "EB_F32", "EB_F64"]

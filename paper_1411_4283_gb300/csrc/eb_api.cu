@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1733,6 +1734,48 @@ eb_status eb_norms(const eb_stencils* st, const double* err, double* out_host, e
   return EB_OK;
 }
 
+// the stencils' multigrid preconditioner, set up at its first use
+static eb_status ensure_mg(const eb_stencils* st, cudaStream_t s) {
+  if (!st->mg) {
+    Multigrid* m = new Multigrid();
+    MgFineInput in;
+    in.dim = st->dm.dim;
+    for (int d = 0; d < 3; ++d) in.n[d] = st->dm.n[d];
+    in.h = st->dm.h;
+    in.flag = st->flag;
+    for (int d = 0; d < 3; ++d) {
+      int dd = d < st->dm.dim ? d : 0;
+      in.ff[d] = st->face_flag[dd];
+      in.cf[d] = st->cutface_of[dd];
+      in.fm[d] = st->face_mom[dd];
+    }
+    in.KFS = st->dm.KFS;
+    in.dinv_high = st->dinv64;
+    in.rows64 = st->rows64;
+    in.rows32 = st->rows32;
+    in.n_rows = st->n_rows;
+    in.nfoot = st->nfoot;
+    in.center = st->foot_center;
+    in.irr_cell = st->irr_cell;
+    in.irr_row = st->irr_row;
+    in.n_irr = st->n_irr;
+    in.kind = st->cell_kind;
+    in.tmpl64 = st->tmpl64;
+    in.tmpl32 = st->tmpl32;
+    in.foot_off = st->foot_off;
+    in.R = st->dm.R;
+    in.box = st->dm.nbr_box;
+    cudaError_t me = mg_setup(in, m, s);
+    if (me != cudaSuccess) {
+      mg_free(m);
+      delete m;
+      return cuda_status(me, "multigrid setup");
+    }
+    const_cast<eb_stencils*>(st)->mg = m;
+  }
+  return EB_OK;
+}
+
 eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb, const double* g_wall, double tol,
                    const eb_solve_opts* opts, double* phi, eb_solve_info* info, eb_stream_t stream) {
   if (!st || !rho || !phi) { set_error("null argument"); return EB_ERR_INVALID; }
@@ -1762,43 +1805,7 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
   eb_status ret = EB_OK;
   const Multigrid* mg = nullptr;
   if (o.precond == 1) {
-    if (!st->mg) {
-      Multigrid* m = new Multigrid();
-      MgFineInput in;
-      in.dim = st->dm.dim;
-      for (int d = 0; d < 3; ++d) in.n[d] = st->dm.n[d];
-      in.h = st->dm.h;
-      in.flag = st->flag;
-      for (int d = 0; d < 3; ++d) {
-        int dd = d < st->dm.dim ? d : 0;
-        in.ff[d] = st->face_flag[dd];
-        in.cf[d] = st->cutface_of[dd];
-        in.fm[d] = st->face_mom[dd];
-      }
-      in.KFS = st->dm.KFS;
-      in.dinv_high = st->dinv64;
-      in.rows64 = st->rows64;
-      in.rows32 = st->rows32;
-      in.n_rows = st->n_rows;
-      in.nfoot = st->nfoot;
-      in.center = st->foot_center;
-      in.irr_cell = st->irr_cell;
-      in.irr_row = st->irr_row;
-      in.n_irr = st->n_irr;
-      in.kind = st->cell_kind;
-      in.tmpl64 = st->tmpl64;
-      in.tmpl32 = st->tmpl32;
-      in.foot_off = st->foot_off;
-      in.R = st->dm.R;
-      in.box = st->dm.nbr_box;
-      cudaError_t me = mg_setup(in, m, s);
-      if (me != cudaSuccess) {
-        mg_free(m);
-        delete m;
-        return cuda_status(me, "multigrid setup");
-      }
-      const_cast<eb_stencils*>(st)->mg = m;
-    }
+    EB_TRY(ensure_mg(st, s));
     mg = st->mg;
     inf->precond_blocks = mg->nblk;
   }
@@ -1884,6 +1891,173 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
   return ret;
 }
 
+}  // extern "C"
+
+struct eb_batch_solver {
+  std::vector<const eb_stencils*> st;
+  eb_solve_opts o;
+  std::vector<BatchSys> sys;
+  BatchCtl* ctl = nullptr;  // device [n]
+  std::vector<void*> mem;   // device arrays
+  // copies of each system's apply plan for the two captured loop bodies, each with its own side
+  // stream and events (a stream joins one capture at a time)
+  std::deque<ApplyPlan> plans;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+void eb_batch_solver_destroy(eb_batch_solver* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (ApplyPlan& pl : b->plans) {
+    if (pl.fork) cudaEventDestroy(pl.fork);
+    if (pl.join) cudaEventDestroy(pl.join);
+    if (pl.side) cudaStreamDestroy(pl.side);
+  }
+  for (void* p : b->mem) cudaFree(p);
+  delete b;
+}
+
+eb_status eb_batch_solver_create(const eb_stencils* const* st, int32_t n, const eb_solve_opts* opts,
+                                 eb_batch_solver** out, eb_stream_t stream) {
+  if (!st || !out || n < 1) { set_error("eb_batch_solver_create: null argument or empty batch"); return EB_ERR_INVALID; }
+  *out = nullptr;
+  g_err.clear();
+  eb_solve_opts o = {1, 1e-5, 20000, 30, 200000, 1, 1};
+  if (opts) o = *opts;
+  if (!o.mixed) { set_error("eb_batch_solver_create: the batched solve is the mixed-precision refinement"); return EB_ERR_INVALID; }
+  if (o.max_inner < 1 || o.max_outer < 1 || o.max_iters < 1 || !(o.inner_tol > 0.0)) {
+    set_error("eb_batch_solver_create: iteration caps must be positive and inner_tol > 0");
+    return EB_ERR_INVALID;
+  }
+  for (int32_t k = 0; k < n; ++k)
+    if (!st[k]) { set_error("eb_batch_solver_create: null stencils"); return EB_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  eb_batch_solver* b = new eb_batch_solver();
+  b->o = o;
+  b->st.assign(st, st + n);
+  auto fail = [&](eb_status r) {
+    eb_batch_solver_destroy(b);
+    return r;
+  };
+  auto get = [&](void** p, size_t bytes) -> eb_status {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return cuda_status(e, "batched solve allocation");
+    b->mem.push_back(*p);
+    return EB_OK;
+  };
+  eb_status r;
+  if ((r = get((void**)&b->ctl, sizeof(BatchCtl) * n)) != EB_OK) return fail(r);
+  b->sys.resize(n);
+  for (int32_t k = 0; k < n; ++k) {
+    const eb_stencils* S = st[k];
+    if (o.precond == 1 && (r = ensure_mg(S, s)) != EB_OK) return fail(r);
+    BatchSys& y = b->sys[k];
+    memset(&y, 0, sizeof(y));
+    y.n = S->dm.ncell;
+    y.A64 = apply_args<double>(S, 1);
+    y.A32 = apply_args<float>(S, 1);
+    if (S->plan) {
+      for (int c = 0; c < 2; ++c) {
+        b->plans.push_back(*S->plan);
+        ApplyPlan& pl = b->plans.back();
+        pl.side = nullptr;
+        pl.fork = pl.join = nullptr;
+        cudaError_t e = S->plan->side ? cudaStreamCreateWithFlags(&pl.side, cudaStreamNonBlocking) : cudaSuccess;
+        if (e == cudaSuccess && S->plan->side) e = cudaEventCreateWithFlags(&pl.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && S->plan->side) e = cudaEventCreateWithFlags(&pl.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(cuda_status(e, "batched solve streams"));
+        (c == 0 ? y.A64.plan : y.A32.plan) = &pl;
+      }
+    }
+    y.mg = o.precond == 1 ? S->mg : nullptr;
+    y.dinv32 = S->dinv32;
+    const size_t n8 = (size_t)y.n * 8, n4 = (size_t)y.n * 4;
+    void* p;
+    if ((r = get(&p, 4 * n8)) != EB_OK) return fail(r);
+    y.rhs = (double*)p;
+    y.phi = y.rhs + y.n;
+    y.y64 = y.phi + y.n;
+    y.r64 = y.y64 + y.n;
+    if ((r = get(&p, 10 * n4)) != EB_OK) return fail(r);
+    y.w32 = (float*)p;
+    y.b32 = y.w32 + 8 * y.n;
+    y.x32 = y.b32 + y.n;
+    if ((r = get(&p, (SC_N + 2) * 8)) != EB_OK) return fail(r);
+    y.sc = (double*)p;
+    y.ctl = b->ctl + k;
+  }
+  EB_CUDA(cudaStreamSynchronize(s));
+  cudaError_t e = batch_graph(b->sys, &b->graph, &b->exec, s);
+  if (e != cudaSuccess) return fail(cuda_status(e, "batched solve graph"));
+  *out = b;
+  return EB_OK;
+}
+
+eb_status eb_batch_solve(eb_batch_solver* b, const double* const* rho, const double* const* g_eb,
+                         const double* const* g_wall, double tol, double* const* phi, eb_solve_info* infos,
+                         eb_stream_t stream) {
+  if (!b || !rho || !phi) { set_error("eb_batch_solve: null argument"); return EB_ERR_INVALID; }
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t n = (int32_t)b->sys.size();
+  std::vector<BatchCtl> h(n);
+  for (int32_t k = 0; k < n; ++k) {
+    const eb_stencils* S = b->st[k];
+    BatchSys& y = b->sys[k];
+    if (!rho[k] || !phi[k]) { set_error("eb_batch_solve: null rho or phi"); return EB_ERR_INVALID; }
+    EB_TRY(eb_bc_rhs(S, g_eb ? g_eb[k] : nullptr, g_wall ? g_wall[k] : nullptr, y.y64, 1, stream));
+    EB_CUDA(compute_rhs(y.n, S->flag, S->kappa, rho[k], y.y64, y.rhs, s));
+    EB_CUDA(cudaMemcpyAsync(y.phi, phi[k], (size_t)y.n * 8, cudaMemcpyDeviceToDevice, s));
+    BatchCtl& c = h[k];
+    memset(&c, 0, sizeof(c));
+    c.tol = tol;
+    c.inner_tol = b->o.inner_tol;
+    c.max_outer = b->o.max_outer;
+    c.max_inner = b->o.max_inner;
+    c.max_iters = b->o.max_iters;
+  }
+  // the control blocks up to the loop handles, which the graph owns
+  for (int32_t k = 0; k < n; ++k)
+    EB_CUDA(cudaMemcpyAsync(b->ctl + k, &h[k], offsetof(BatchCtl, ho), cudaMemcpyHostToDevice, s));
+  for (int32_t k = 0; k < n; ++k) EB_CUDA(batch_dots(b->sys[k].n, b->sys[k].rhs, &b->ctl[k].bnorm2, s));
+  EB_CUDA(cudaGraphLaunch(b->exec, s));
+  for (int32_t k = 0; k < n; ++k)
+    EB_CUDA(cudaMemcpyAsync(phi[k], b->sys[k].phi, (size_t)b->sys[k].n * 8, cudaMemcpyDeviceToDevice, s));
+  EB_CUDA(cudaMemcpyAsync(h.data(), b->ctl, sizeof(BatchCtl) * n, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  eb_status ret = EB_OK;
+  for (int32_t k = 0; k < n; ++k) {
+    const BatchCtl& c = h[k];
+    eb::count_launches((long long)c.runs * b->sys[k].k_sweep + (long long)c.total * b->sys[k].k_iter);
+    if (infos) {
+      eb_solve_info& f = infos[k];
+      memset(&f, 0, sizeof(f));
+      f.iterations = c.total;
+      f.sweeps = c.sweeps;
+      f.rel_residual = c.rel_residual;
+      f.n_history = std::min(c.n_hist, 64);
+      for (int i = 0; i < f.n_history; ++i) f.history[i] = c.hist[i];
+      f.precond_blocks = b->sys[k].mg ? b->sys[k].mg->nblk : 0;
+    }
+    if (c.status != 1 && ret == EB_OK) {
+      ret = EB_ERR_NOT_CONVERGED;
+      set_error("eb_batch_solve: system " + std::to_string(k) +
+                (c.status == 3 ? " broke down (non-finite residual)" : " did not reach the tolerance within the caps"));
+    }
+    const eb_stencils* S = b->st[k];
+    if (S->plan && S->plan->err) {
+      int32_t fl = 0;
+      EB_CUDA(cudaMemcpy(&fl, S->plan->err, 4, cudaMemcpyDeviceToHost));
+      if (fl) { set_error("a bounded device wait gave up in the operator apply"); return EB_ERR_TIMEOUT; }
+    }
+  }
+  return ret;
+}
+
 eb_status eb_wall_faces(const eb_stencils* st, int64_t* ids_host, int64_t cap, int64_t* n) {
   if (!st || !n) { set_error("null argument"); return EB_ERR_INVALID; }
   *n = st->n_wall;
@@ -1954,6 +2128,50 @@ eb_status eb_stencil_query(const eb_stencils* st, int64_t face, int32_t* n, int6
 }
 
 }  // extern "C"
+
+// ================================================================= FP64 FMA throughput probe
+
+namespace eb {
+// eight independent FMA chains per thread; the sum keeps them live
+__global__ void k_dfma_probe(int64_t iters, double seed, double* sink) {
+  double a[8];
+  for (int k = 0; k < 8; ++k) a[k] = seed + threadIdx.x + k;
+  const double m = 0.9999999, c = 1e-9;
+  for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  double t = 0.0;
+  for (int k = 0; k < 8; ++k) t += a[k];
+  if (t == 1234.5678) *sink = t;
+}
+}  // namespace eb
+
+extern "C" eb_status eb_fp64_fma_rate(int32_t blocks_per_sm, int64_t iters, double* tflops_host, eb_stream_t stream) {
+  if (!tflops_host || blocks_per_sm < 1 || iters < 1) { set_error("eb_fp64_fma_rate: bad argument"); return EB_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  EB_CUDA(cudaGetDevice(&dev));
+  EB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double* sink;
+  EB_CUDA(cudaMallocAsync((void**)&sink, 8, s));
+  cudaEvent_t e0, e1;
+  EB_CUDA(cudaEventCreate(&e0));
+  EB_CUDA(cudaEventCreate(&e1));
+  const unsigned blocks = (unsigned)(nsm * blocks_per_sm);
+  k_dfma_probe<<<blocks, 256, 0, s>>>(iters / 8 + 1, 1.0, sink);  // warm-up
+  EB_CUDA(cudaEventRecord(e0, s));
+  k_dfma_probe<<<blocks, 256, 0, s>>>(iters, 1.0, sink);
+  EB_CUDA(cudaEventRecord(e1, s));
+  eb::count_launches(2);
+  EB_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  EB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  EB_CUDA(cudaFreeAsync(sink, s));
+  *tflops_host = 2.0 * 8.0 * (double)iters * blocks * 256.0 / (ms * 1e-3) / 1e12;
+  return EB_OK;
+}
 
 // ================================================================= adjoint with respect to the radii
 

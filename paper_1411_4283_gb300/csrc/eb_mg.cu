@@ -762,7 +762,10 @@ cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
   MgLevel& L = mg.lev[0];
   const int k = sizeof(T) == 4 ? 0 : 1;
   cudaError_t e;
-  if (!mg.exec[k]) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cst))) return e;
+  const bool capturing = cst == cudaStreamCaptureStatusActive;  // inside a graph being captured: the cycle's kernels
+  if (!capturing && !mg.exec[k]) {
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return e;
     long long before = eb::launches_so_far();
@@ -780,8 +783,12 @@ cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
     if (e) return e;
   }
   if ((e = cudaMemcpyAsync(vbuf<T>(L, 0), r, L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s))) return e;
-  if ((e = cudaGraphLaunch(mg.exec[k], s))) return e;
-  eb::count_launches(mg.nodes[k]);
+  if (capturing) {
+    if ((e = vcycle<T>(mg, 0, s))) return e;
+  } else {
+    if ((e = cudaGraphLaunch(mg.exec[k], s))) return e;
+    eb::count_launches(mg.nodes[k]);
+  }
   if ((e = cudaMemcpyAsync(z, vbuf<T>(L, 1), L.ncell * sizeof(T), cudaMemcpyDeviceToDevice, s))) return e;
   if (mg.nblk > 0) {
     RowSrc a = row_src(mg);

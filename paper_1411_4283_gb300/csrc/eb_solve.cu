@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <vector>
 
 #include "eb_apply.cuh"
@@ -241,8 +243,6 @@ static cudaError_t timed_apply(const ApplyArgs<T>& A, cudaStream_t s) {
 // (a thread handles at most a few dozen elements), the block and grid sums in FP64.  FP64
 // arithmetic is slow on this GPU, so FP32 vectors keep their per-element work in FP32.
 
-// Device-resident BiCGStab scalars (FP64): slots of the running dot products
-enum { SC_RHO0 = 0, SC_RHO1 = 1, SC_RV = 2, SC_TS = 3, SC_TT = 4, SC_RR = 5, SC_BB = 6, SC_N = 8 };
 
 __device__ __forceinline__ void block_accumulate(double v, double* dst, double* sh) {
   v = block_sum(v, sh);
@@ -251,9 +251,14 @@ __device__ __forceinline__ void block_accumulate(double v, double* dst, double* 
 
 // p = r + beta (p - omega v), beta = (rho_i / rho_{i-1}) (alpha / omega); phat = dinv p.
 // Also clears the slot of (rhat, v) for this iteration.
+// itp (batched solve): the iteration count on the device; q and first follow from it
 template <typename T>
 __global__ void k_bs_p(int64_t n, const T* r, const T* v, T* p, T* ph, const T* dinv, double* sc, int q, int first,
-                       const double* ao) {
+                       const double* ao, const int32_t* itp) {
+  if (itp) {
+    q = *itp & 1;
+    first = *itp == 0;
+  }
   double beta = 0.0, omega = 0.0;
   if (!first) {
     double rho = sc[q], rho_old = sc[1 - q];
@@ -280,7 +285,9 @@ __global__ void k_bs_dot_rv(int64_t n, const T* rh, const T* v, double* sc) {
 
 // alpha = rho_i / (rhat, v); s = r - alpha v; shat = dinv s.  Clears the slots filled later this iteration.
 template <typename T>
-__global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T* dinv, double* sc, int q, double* ao) {
+__global__ void k_bs_s(int64_t n, const T* r, const T* v, T* s, T* shv, const T* dinv, double* sc, int q, double* ao,
+                       const int32_t* itp) {
+  if (itp) q = *itp & 1;
   double rv = sc[SC_RV];
   double alpha = rv != 0.0 ? sc[q] / rv : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -315,8 +322,9 @@ __global__ void k_bs_dot_ts(int64_t n, const T* t, const T* s, double* sc) {
 // omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t; rho_{i+1} = (rhat, r); (r, r)
 template <typename T>
 __global__ void k_bs_x(int64_t n, T* x, const T* ph, const T* shv, T* r, const T* s, const T* t, const T* rh,
-                       double* sc, int q, double* ao) {
+                       double* sc, int q, double* ao, const int32_t* itp) {
   __shared__ double sh[32];
+  if (itp) q = *itp & 1;
   double alpha = ao[0];
   double omega = sc[SC_TT] > 0.0 ? sc[SC_TS] / sc[SC_TT] : 0.0;
   T a = 0, b = 0;
@@ -386,19 +394,19 @@ cudaError_t bicgstab(const ApplyArgs<T>& A0, const T* b, T* x, const T* dinv, T*
   if (*relres <= tol) { *iters = 0; return cudaSuccess; }
   for (it = 1; it <= maxit; ++it) {
     int q = (it - 1) & 1;
-    k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, mg ? nullptr : dinv, sc, q, it == 1, ao); eb::count_launch();
+    k_bs_p<T><<<G, VB, 0, s>>>(n, r, v, p, ph, mg ? nullptr : dinv, sc, q, it == 1, ao, nullptr); eb::count_launch();
     if (mg && (e = mg_precond<T>(*mg, p, ph, s))) return e;  // phat = V-cycle(p) instead of Jacobi
     A.phi = ph;
     A.y = v;
     if ((e = timed_apply<T>(A, s))) return e;
     k_bs_dot_rv<T><<<G, VB, 0, s>>>(n, rh, v, sc); eb::count_launch();
-    k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, mg ? nullptr : dinv, sc, q, ao); eb::count_launch();
+    k_bs_s<T><<<G, VB, 0, s>>>(n, r, v, sv, shv, mg ? nullptr : dinv, sc, q, ao, nullptr); eb::count_launch();
     if (mg && (e = mg_precond<T>(*mg, sv, shv, s))) return e;
     A.phi = shv;
     A.y = t;
     if ((e = timed_apply<T>(A, s))) return e;
     k_bs_dot_ts<T><<<G, VB, 0, s>>>(n, t, sv, sc); eb::count_launch();
-    k_bs_x<T><<<G, VB, 0, s>>>(n, x, ph, shv, r, sv, t, rh, sc, q, ao); eb::count_launch();
+    k_bs_x<T><<<G, VB, 0, s>>>(n, x, ph, shv, r, sv, t, rh, sc, q, ao, nullptr); eb::count_launch();
     if ((e = cudaMemcpyAsync(h, sc, SC_N * sizeof(double), cudaMemcpyDeviceToHost, s))) return e;
     if ((e = cudaStreamSynchronize(s))) return e;
     *relres = sqrt(h[SC_RR]) / bn;
@@ -455,6 +463,225 @@ cudaError_t norm2_64(int64_t n, const double* a, double* dscr, double* out, cuda
   cudaError_t e = dots<double>(n, a, a, nullptr, nullptr, nullptr, nullptr, dscr, h, 1, s);
   *out = sqrt(h[0]);
   return e;
+}
+
+
+// ----------------------------------------------------------------- batched refined solve
+//
+// Several independent systems (one per geometry) go through the refinement of eb_solve in one CUDA
+// graph: per system a conditional WHILE node runs the refinement sweeps (the FP64 residual with the
+// FP64 operator, the inner FP32 BiCGStab as a nested WHILE node, phi += its correction); one-thread
+// control kernels set the loop conditions on the device from the device-resident scalars, so the
+// systems' loops run side by side in one graph launch with no host synchronisation.  Every loop ends
+// at its iteration cap: the control kernels count the iterations and clear the condition there.
+
+cudaError_t batch_dots(int64_t n, const double* a, double* out, cudaStream_t s) {
+  k_dots<double><<<grid_for(n), VB, 0, s>>>(n, a, a, nullptr, nullptr, nullptr, nullptr, out); eb::count_launch();
+  return cudaGetLastError();
+}
+
+// after the FP64 residual of a sweep: stop (converged, caps, non-finite) or start an inner solve
+__global__ void k_bt_outer(BatchCtl* c) {
+  const double bn = c->bnorm2 > 0.0 ? sqrt(c->bnorm2) : 1.0;
+  c->rn = sqrt(c->rn2);
+  const double rel = c->rn / bn;
+  c->runs += 1;
+  c->rel_residual = rel;
+  if (c->n_hist < 64) c->hist[c->n_hist++] = rel;
+  int go = 0;
+  if (c->status == 3) go = 0;  // the last inner solve broke down: phi is unchanged, stop
+  else if (rel <= c->tol) c->status = 1;
+  else if (!isfinite(rel)) c->status = 3;
+  else if (c->sweeps >= c->max_outer || c->total >= c->max_iters) c->status = 2;
+  else go = 1;
+  c->active = go;
+  if (go) {
+    c->sweeps += 1;
+    c->it = 0;
+    c->scale = 1.0 / c->rn;
+  }
+  cudaGraphSetConditional(c->ho, go);
+  cudaGraphSetConditional(c->hi, go);
+}
+
+// b32 = r64 / ||r64||, x32 = 0, r32 = 0 (A x for the zero guess)
+__global__ void k_bt_prep(int64_t n, const BatchCtl* c, const double* r64, float* b32, float* x32, float* r32) {
+  if (!c->active) return;
+  const double sc = c->scale;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    b32[i] = (float)(sc * r64[i]);
+    x32[i] = 0.0f;
+    r32[i] = 0.0f;
+  }
+}
+
+// the inner solve's initial residual: skip the loop when it already meets inner_tol
+__global__ void k_bt_inner0(BatchCtl* c, const double* sc) {
+  if (!c->active) return;
+  const double bn = sc[SC_BB] > 0.0 ? sqrt(sc[SC_BB]) : 1.0;
+  const double rel = sqrt(sc[SC_RHO0]) / bn;
+  c->inner_relres = rel;
+  if (!(rel > c->inner_tol)) cudaGraphSetConditional(c->hi, 0);
+}
+
+// after an inner iteration: the recurrence residual, breakdown and the caps decide whether to go on
+__global__ void k_bt_inner(BatchCtl* c, const double* sc) {
+  const int q = c->it & 1;
+  const double bn = sc[SC_BB] > 0.0 ? sqrt(sc[SC_BB]) : 1.0;
+  const double rr = sqrt(sc[SC_RR]) / bn;
+  c->it += 1;
+  c->total += 1;
+  c->inner_relres = rr;
+  int more = rr > c->inner_tol;
+  if (sc[1 - q] == 0.0 || sc[SC_TT] == 0.0 || sc[SC_RV] == 0.0) more = 0;  // breakdown
+  if (c->it >= c->max_inner || c->total >= c->max_iters) more = 0;
+  if (!isfinite(rr)) {  // no usable correction: phi stays unchanged and the next sweep's control stops
+    c->status = 3;
+    c->active = 0;
+    more = 0;
+  }
+  cudaGraphSetConditional(c->hi, more);
+}
+
+// phi += ||r|| x32
+__global__ void k_bt_corr(int64_t n, const BatchCtl* c, double* phi, const float* x32) {
+  if (!c->active) return;
+  const double sc = c->rn;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] += sc * (double)x32[i];
+}
+
+namespace {
+
+// a WHILE node on the stream's capture, after its current dependencies; returns its body graph
+cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp))) return e;
+  *body = cp.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// one inner BiCGStab iteration of system y (the loop of bicgstab with the parity from the device)
+cudaError_t capture_iteration(const BatchSys& y, cudaStream_t s) {
+  const int64_t n = y.n;
+  float* w = y.w32;
+  float *r = w, *rh = w + n, *p = w + 2 * n, *v = w + 3 * n, *ph = w + 4 * n, *sv = w + 5 * n, *shv = w + 6 * n,
+        *t = w + 7 * n;
+  double* sc = y.sc;
+  double* ao = y.sc + SC_N;
+  const int32_t* itp = &y.ctl->it;
+  const float* dinv = y.mg ? nullptr : y.dinv32;
+  const unsigned G = grid_for(n);
+  cudaError_t e;
+  ApplyArgs<float> A = y.A32;
+  k_bs_p<float><<<G, VB, 0, s>>>(n, r, v, p, ph, dinv, sc, 0, 0, ao, itp); eb::count_launch();
+  if (y.mg && (e = mg_precond<float>(*y.mg, p, ph, s))) return e;
+  A.phi = ph;
+  A.y = v;
+  if ((e = launch_apply<float>(A, s))) return e;
+  k_bs_dot_rv<float><<<G, VB, 0, s>>>(n, rh, v, sc); eb::count_launch();
+  k_bs_s<float><<<G, VB, 0, s>>>(n, r, v, sv, shv, dinv, sc, 0, ao, itp); eb::count_launch();
+  if (y.mg && (e = mg_precond<float>(*y.mg, sv, shv, s))) return e;
+  A.phi = shv;
+  A.y = t;
+  if ((e = launch_apply<float>(A, s))) return e;
+  k_bs_dot_ts<float><<<G, VB, 0, s>>>(n, t, sv, sc); eb::count_launch();
+  k_bs_x<float><<<G, VB, 0, s>>>(n, y.x32, ph, shv, r, sv, t, rh, sc, 0, ao, itp); eb::count_launch();
+  k_bt_inner<<<1, 1, 0, s>>>(y.ctl, sc); eb::count_launch();
+  return cudaGetLastError();
+}
+
+// one refinement sweep of system y: FP64 residual, control, inner solve (nested loop), correction
+cudaError_t capture_sweep(BatchSys& y, cudaStream_t s, cudaStream_t s2) {
+  const int64_t n = y.n;
+  const unsigned G = grid_for(n);
+  cudaError_t e;
+  const long long c0 = eb::launches_so_far();
+  ApplyArgs<double> A = y.A64;
+  A.phi = y.phi;
+  A.y = y.y64;
+  if ((e = launch_apply<double>(A, s))) return e;
+  k_resid64<<<G, VB, 0, s>>>(n, y.rhs, y.y64, y.r64); eb::count_launch();
+  if ((e = cudaMemsetAsync(&y.ctl->rn2, 0, sizeof(double), s))) return e;
+  if ((e = batch_dots(n, y.r64, &y.ctl->rn2, s))) return e;
+  k_bt_outer<<<1, 1, 0, s>>>(y.ctl); eb::count_launch();
+  float* r32 = y.w32;
+  k_bt_prep<<<G, VB, 0, s>>>(n, y.ctl, y.r64, y.b32, y.x32, r32); eb::count_launch();
+  if ((e = cudaMemsetAsync(y.sc, 0, (SC_N + 2) * sizeof(double), s))) return e;
+  float* w = y.w32;
+  k_bs_init<float><<<G, VB, 0, s>>>(n, y.b32, w, w + n, w + 2 * n, w + 3 * n, y.sc); eb::count_launch();
+  k_bt_inner0<<<1, 1, 0, s>>>(y.ctl, y.sc); eb::count_launch();
+  cudaGraph_t ib = nullptr;
+  if ((e = add_while(s, y.ctl_hi_host, &ib))) return e;
+  const long long c1 = eb::launches_so_far();
+  if ((e = cudaStreamBeginCaptureToGraph(s2, ib, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) return e;
+  cudaError_t ce = capture_iteration(y, s2);
+  cudaGraph_t done = nullptr;
+  e = cudaStreamEndCapture(s2, &done);
+  if (ce) return ce;
+  if (e) return e;
+  const long long c2 = eb::launches_so_far();
+  k_bt_corr<<<G, VB, 0, s>>>(n, y.ctl, y.phi, y.x32); eb::count_launch();
+  y.k_iter = c2 - c1;
+  y.k_sweep = (eb::launches_so_far() - c0) - y.k_iter;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t batch_graph(std::vector<BatchSys>& sys, cudaGraph_t* graph, cudaGraphExec_t* exec, cudaStream_t s) {
+  *graph = nullptr;
+  *exec = nullptr;
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (!e) e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+  cudaGraph_t top = nullptr;
+  if (!e) e = cudaGraphCreate(&top, 0);
+  const long long before = eb::launches_so_far();
+  for (size_t k = 0; k < sys.size() && !e; ++k) {
+    BatchSys& y = sys[k];
+    cudaGraphConditionalHandle ho, hi;
+    if ((e = cudaGraphConditionalHandleCreate(&ho, top, 1, cudaGraphCondAssignDefault))) break;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = ho;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &cp))) break;
+    cudaGraph_t ob = cp.conditional.phGraph_out[0];
+    if ((e = cudaGraphConditionalHandleCreate(&hi, ob, 0, 0))) break;
+    y.ctl_hi_host = hi;
+    if ((e = cudaMemcpyAsync(&y.ctl->ho, &ho, sizeof(ho), cudaMemcpyHostToDevice, s))) break;
+    if ((e = cudaMemcpyAsync(&y.ctl->hi, &hi, sizeof(hi), cudaMemcpyHostToDevice, s))) break;
+    if ((e = cudaStreamSynchronize(s))) break;
+    if ((e = cudaStreamBeginCaptureToGraph(cs, ob, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+    cudaError_t ce = capture_sweep(y, cs, cs2);
+    cudaGraph_t done = nullptr;
+    e = cudaStreamEndCapture(cs, &done);
+    if (ce) e = ce;
+  }
+  eb::uncount_launches(eb::launches_so_far() - before);  // capture issued no work
+  if (!e) e = cudaGraphInstantiate(exec, top, 0);
+  if (cs) cudaStreamDestroy(cs);
+  if (cs2) cudaStreamDestroy(cs2);
+  if (e) {
+    if (top) cudaGraphDestroy(top);
+    *exec = nullptr;
+    return e;
+  }
+  *graph = top;
+  return cudaSuccess;
 }
 
 }  // namespace eb
