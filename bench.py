@@ -329,9 +329,16 @@ def main():
         run_adjoint(args, P, torch)
         return
     if args.mode == "peak":
-        rates = {str(b): P.eb_fp64_fma_rate(blocks_per_sm=b, iters=1 << 16) for b in (2, 4, 8, 16)}
+        # the FP64 FMA probe, long enough for the clock sampler to see it (clocks recorded alongside)
+        P.eb_fp64_fma_rate(blocks_per_sm=8, iters=1 << 16)
+        ck = Clocks(os.path.join(os.environ.get("EB_CLOCKS_DIR", tempfile.gettempdir()), "clocks_peak.csv"))
+        ck.start()
+        time.sleep(0.5)
+        rates = {str(b): P.eb_fp64_fma_rate(blocks_per_sm=b, iters=1 << 18) for b in (2, 4, 8, 16)}
+        clocks = ck.stop()
         print(json.dumps({"mode": "peak", "fp64_fma_tflops": rates, "sm_count": sms, "sm_max_mhz": sm_max,
-                          "derived_fp64_tflops": fp64_peak_tflops(sm_max, sms)}))
+                          "derived_fp64_tflops": fp64_peak_tflops(sm_max, sms), "clocks": clocks,
+                          "derived_at_median_clock_tflops": fp64_peak_tflops(clocks["sm_mhz"] or sm_max, sms)}))
         return
     if args.mode in ("build", "apply"):
         run_operator(args, P, torch)
@@ -618,7 +625,7 @@ def run_adjoint(args, P, torch):
     print(json.dumps({
         "mode": "adjoint", "workload": f"unit cube minus eight seeded spheres at {N}^3, Q = 4, gradient of "
         "J = 1/2 sum |V| phi^2 with respect to 8 radii and 16 + 1 level-set mode amplitudes",
-        "data": "synthetic", "N": N, "n_cut": int(G.n_cut), "unique_systems": st.info["n_unique"],
+        "data": "synthetic", "N": N, "n_cut": int(G.n_cut), "unique_systems": st.info["n_unique_faces"],
         "geometry_ms": ev[0].elapsed_time(ev[1]), "build_ms": ev[1].elapsed_time(ev[2]),
         "solve_ms": ev[2].elapsed_time(ev[3]), "solve_iterations": sinfo["iterations"],
         "adjoint_s": t_adj, "adjoint": ainfo, "J": J, "dJ_dr": list(dr), "dJ_da": list(da[:-1]),
@@ -631,7 +638,7 @@ def run_batch(args, P, torch):
     32^2..512^2); 3-D (--batch-dim 3): the unit cube minus a sphere (centre 0.5 + U[-0.05, 0.05)^3,
     radius U[0.25, 0.35), grids 64^3, 96^3 or 128^3); all from SplitMix64(11).  Build: one least-squares
     launch for the batch against one build per geometry (LS systems per second).  Solve: kappa L phi =
-    kappa with homogeneous Dirichlet data to a relative residual of 1e-12, the batched refined solve
+    kappa with homogeneous Dirichlet data to a relative residual of 1e-10, the batched refined solve
     (one graph launch) against one eb_solve per geometry (systems solved per second)."""
     import eb_inputs as E
     from eb_inputs.rng import SplitMix64
@@ -685,17 +692,21 @@ def run_batch(args, P, torch):
     geb = [torch.zeros(max(len(g.cut_cells), 1), **f64) for g in gs]
     gw = [torch.zeros(max(len(P.eb_wall_faces(st)), 1), **f64) for st in sts]
     phis = [torch.zeros(g.ncell, **f64) for g in gs]
+    # kappa L phi = kappa with zero boundary data reaches a relative residual floor near 1e-12 at 512^2
+    # (FP64 rounding of the residual), so the batch solves to 1e-10
+    tol = 1e-10
     t0 = time.perf_counter()
     bs = P.BatchSolver(sts)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    tss, tbs, its_s, its_b = [], [], 0, 0
+    tss, tbs, its_s, its_b, conv_s, conv_b = [], [], 0, 0, 0, 0
     for step in range(max(1, args.warmup) + args.steps):
         for x in phis:
             x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        inf_s = [P.eb_solve(st, r_, e_, w_, x, tol=1e-12) for st, r_, e_, w_, x in zip(sts, rho, geb, gw, phis)]
+        inf_s = [P.eb_solve(st, r_, e_, w_, x, tol=tol, allow_not_converged=True)
+                 for st, r_, e_, w_, x in zip(sts, rho, geb, gw, phis)]
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
         ref = [x.clone() for x in phis]
@@ -703,7 +714,7 @@ def run_batch(args, P, torch):
             x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        inf_b = bs.solve(rho, geb, gw, phis, tol=1e-12)
+        inf_b = bs.solve(rho, geb, gw, phis, tol=tol, allow_not_converged=True)
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t0
         if step >= max(1, args.warmup):
@@ -711,6 +722,8 @@ def run_batch(args, P, torch):
             tbs.append(t_bat)
             its_s = sum(i["iterations"] for i in inf_s)
             its_b = sum(i["iterations"] for i in inf_b)
+            conv_s = sum(i["status"] == "EB_OK" for i in inf_s)
+            conv_b = sum(i["rel_residual"] <= tol for i in inf_b)
     dev = max(float((x - y).abs().max() / y.abs().max()) for x, y in zip(phis, ref))
     mss, mbs = float(np.median(tss)), float(np.median(tbs))
     sizes = [g.N for g in gs]
@@ -723,7 +736,7 @@ def run_batch(args, P, torch):
                                 "batch_systems_per_s": len(gs) / mbs, "sequential_systems_per_s": len(gs) / mss,
                                 "graph_setup_seconds": t_setup, "iterations_batch": its_b,
                                 "iterations_sequential": its_s, "max_rel_diff_vs_sequential": dev,
-                                "tol": 1e-12},
+                                "converged_batch": conv_b, "converged_sequential": conv_s, "tol": tol},
                       "steps": args.steps, "order": args.order, "data": "synthetic"}))
 
 

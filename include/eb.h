@@ -101,7 +101,13 @@ typedef struct eb_params {
   int32_t weighted;      /* 1: W_ii as in Sec. 2.4; 0: W = I (unstable control) */
   double w_threshold;    /* 0.5 */
   double w_power;        /* 5 */
+  int32_t ls_precision;  /* EB_LS_MIXED (default): each least-squares system is factorised in FP32
+                            and solved by FP64 corrected semi-normal iterations preconditioned by that
+                            factor, a system the FP32 factor cannot carry going to the FP64 path;
+                            EB_LS_FP64: FP64 Householder factorisation for every system.  Both give
+                            the FP64 minimum-norm stencil to rounding (Sec. 2.2.1). */
 } eb_params;
+enum { EB_LS_MIXED = 0, EB_LS_FP64 = 1 };
 
 typedef struct eb_stencils eb_stencils; /* opaque, library-owned */
 
@@ -113,8 +119,11 @@ typedef struct eb_build_info {
   int32_t max_rows;         /* largest LS system (rows) */
   int64_t n_irregular_rows; /* cells with their own operator row */
   int32_t n_row_classes;    /* shared operator rows (wall classes and template) */
-  int64_t lsq_flops;        /* algorithmic FP64 flops of the LS solves */
+  int64_t lsq_flops;        /* FP64 flops of the LS solves by Householder QR + corrected semi-normal
+                               equations (the reference count of the method, whichever path ran) */
   double ms_classify, ms_gather, ms_lsq, ms_assemble; /* device time per phase */
+  int64_t n_ls_fp64;        /* systems solved by the FP64 factorisation (all of them with
+                               EB_LS_FP64; with EB_LS_MIXED those the FP32 factor could not carry) */
 } eb_build_info;
 
 /* Build all flux stencils and the operator (Sec. 2.2-2.4).

@@ -40,7 +40,8 @@ class EbGeom(ctypes.Structure):
 
 class EbParams(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("path_radius", ctypes.c_int32), ("nbr_metric", ctypes.c_int32),
-                ("weighted", ctypes.c_int32), ("w_threshold", ctypes.c_double), ("w_power", ctypes.c_double)]
+                ("weighted", ctypes.c_int32), ("w_threshold", ctypes.c_double), ("w_power", ctypes.c_double),
+                ("ls_precision", ctypes.c_int32)]
 
 
 class EbBuildInfo(ctypes.Structure):
@@ -48,7 +49,7 @@ class EbBuildInfo(ctypes.Structure):
                 ("n_class_faces", ctypes.c_int64), ("n_classes", ctypes.c_int32), ("max_rows", ctypes.c_int32),
                 ("n_irregular_rows", ctypes.c_int64), ("n_row_classes", ctypes.c_int32),
                 ("lsq_flops", ctypes.c_int64), ("ms_classify", ctypes.c_double), ("ms_gather", ctypes.c_double),
-                ("ms_lsq", ctypes.c_double), ("ms_assemble", ctypes.c_double)]
+                ("ms_lsq", ctypes.c_double), ("ms_assemble", ctypes.c_double), ("n_ls_fp64", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -363,11 +364,14 @@ class Stencils:
             self.handle = None
 
 
+LS_PRECISION = {"mixed": 0, "fp64": 1}
+
+
 def eb_build_stencils(geom: DeviceGeometry, order=4, path_radius=0, nbr_metric=EB_NBR_BOX, weighted=True,
-                      w_threshold=0.5, w_power=5.0, stream=None) -> Stencils:
+                      w_threshold=0.5, w_power=5.0, stream=None, ls_precision="mixed") -> Stencils:
     lib = load()
     g = geom.struct()
-    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power)
+    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power, LS_PRECISION[ls_precision])
     h = ctypes.c_void_p()
     info = EbBuildInfo()
     _check(lib.eb_build_stencils(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h), ctypes.byref(info),
@@ -376,12 +380,12 @@ def eb_build_stencils(geom: DeviceGeometry, order=4, path_radius=0, nbr_metric=E
 
 
 def eb_build_stencils_batch(geoms, order=4, path_radius=0, nbr_metric=EB_NBR_BOX, weighted=True,
-                            w_threshold=0.5, w_power=5.0, stream=None) -> list:
+                            w_threshold=0.5, w_power=5.0, stream=None, ls_precision="mixed") -> list:
     """Stencils of several geometries (same dimension) with one least-squares launch."""
     lib = load()
     n = len(geoms)
     gs = (EbGeom * n)(*[geom.struct() for geom in geoms])
-    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power)
+    p = EbParams(order, path_radius, nbr_metric, int(weighted), w_threshold, w_power, LS_PRECISION[ls_precision])
     hs = (ctypes.c_void_p * n)()
     infos = (EbBuildInfo * n)()
     _check(lib.eb_build_stencils_batch(gs, n, ctypes.byref(p), hs, infos, _stream(stream)))

@@ -27,7 +27,6 @@
 
 namespace eb {
 
-constexpr int LS_SMEM_PER_SYS = (int)sizeof(LsSysSmem);
 
 // ------------------------------------------------------------------ errors
 
@@ -551,7 +550,7 @@ const char* eb_status_string(eb_status s) {
 }
 
 const char* eb_last_error_message(void) { return g_err.c_str(); }
-int32_t eb_abi_version(void) { return 2; }
+int32_t eb_abi_version(void) { return 3; }
 int64_t eb_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 void eb_stencils_destroy(eb_stencils* st) {
@@ -920,8 +919,9 @@ static eb_status build_pre(BuildCtx& c) {
   c.tmp.s = s;
   st->build_stream = s;
   if (!g) { set_error("geometry descriptor is NULL"); return EB_ERR_INVALID; }
-  eb_params P = {4, 0, EB_NBR_BOX, 1, 0.5, 5.0};
+  eb_params P = {4, 0, EB_NBR_BOX, 1, 0.5, 5.0, EB_LS_MIXED};
   if (prm) P = *prm;
+  if (P.ls_precision != EB_LS_MIXED && P.ls_precision != EB_LS_FP64) { set_error("bad ls_precision"); return EB_ERR_INVALID; }
   if (g->dim != 2 && g->dim != 3) { set_error("dim must be 2 or 3"); return EB_ERR_INVALID; }
   if (P.order != 2 && P.order != 4) { set_error("order must be 2 or 4"); return EB_ERR_INVALID; }
   if (g->moment_degree < P.order) { set_error("moment tables shallower than the order"); return EB_ERR_INVALID; }
@@ -1199,19 +1199,26 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   base[n] = total;
   Tmp tmp;
   tmp.s = s;
-  size_t ls_smem = (size_t)LS_SYS * LS_SMEM_PER_SYS;
-  EB_CUDA(lsq_prepare(ls_smem));
-  int64_t nblocks = std::min<int64_t>(c0.nsm, (total + LS_SYS - 1) / LS_SYS);
-  if (nblocks < 1) nblocks = 1;
+  EB_CUDA(lsq_prepare());
+  const bool fp32 = c0.P.ls_precision == EB_LS_MIXED;
+  for (int i = 1; i < n; ++i)
+    if (cs[i]->P.ls_precision != c0.P.ls_precision) { set_error("a batch mixes LS precisions"); return EB_ERR_INVALID; }
+  auto blocks_for = [&](int64_t systems, int per_cta) {
+    return std::max<int64_t>(1, std::min<int64_t>(c0.nsm, (systems + per_cta - 1) / per_cta));
+  };
+  const int64_t nb_d = blocks_for(total, LS_SYS), nb_f = blocks_for(total, LS_SYS_F);
   double* scratch;
-  EB_TRY(tmp.get(&scratch, (size_t)nblocks * LS_SYS * MAXROWS * (MAXK + 2)));
-  int32_t *next, *lerr;
+  EB_TRY(tmp.get(&scratch, (size_t)std::max(nb_d * LS_SYS, fp32 ? nb_f * LS_SYS_F : 0) * LS_SCRATCH));
+  int32_t *next, *lerr, *nfb, *fblist = nullptr;
   EB_TRY(tmp.get(&next, 1));
   EB_TRY(tmp.get(&lerr, 1));
+  EB_TRY(tmp.get(&nfb, 1));
   EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
   EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
+  EB_CUDA(cudaMemsetAsync(nfb, 0, 4, s));
   LsArgs a0 = c0.la;
   a0.n_slots = total;
+  a0.slot_list = nullptr;
   a0.next = next;
   a0.err = lerr;
   a0.scratch = scratch;
@@ -1219,7 +1226,10 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   int64_t* dbase = nullptr;
   if (n > 1) {
     std::vector<LsArgs> hb(n);
-    for (int i = 0; i < n; ++i) hb[i] = cs[i]->la;
+    for (int i = 0; i < n; ++i) {
+      hb[i] = cs[i]->la;
+      hb[i].slot_list = nullptr;
+    }
     EB_TRY(tmp.get(&dbatch, n));
     EB_TRY(tmp.get(&dbase, n + 1));
     EB_CUDA(cudaMemcpyAsync(dbatch, hb.data(), n * sizeof(LsArgs), cudaMemcpyHostToDevice, s));
@@ -1227,8 +1237,29 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   }
   for (int i = 0; i < n; ++i) EB_CUDA(cudaEventRecord(cs[i]->ev[2], s));
   if (total > 0) {
-    EB_CUDA(lsq_launch((unsigned)nblocks, ls_smem, s, a0, c0.T, n > 1 ? dbatch : nullptr, dbase, n));
-    eb::count_launch();
+    if (fp32) {
+      // FP32 factorisation for every system, then the FP64 one for those it left (status 3)
+      EB_CUDA(lsq_launch(true, (unsigned)nb_f, s, a0, c0.T, n > 1 ? dbatch : nullptr, dbase, n));
+      eb::count_launch();
+      EB_TRY(tmp.get(&fblist, total));
+      for (int i = 0; i < n; ++i) {
+        EB_CUDA(lsq_fallback_list(cs[i]->status, cs[i]->n_slots, base[i], fblist, nfb, s));
+        eb::count_launch();
+      }
+      int32_t hn = 0;
+      EB_CUDA(cudaMemcpyAsync(&hn, nfb, 4, cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      if (hn > 0) {
+        EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
+        a0.slot_list = fblist;
+        a0.n_slots = hn;
+        EB_CUDA(lsq_launch(false, (unsigned)blocks_for(hn, LS_SYS), s, a0, c0.T, n > 1 ? dbatch : nullptr, dbase, n));
+        eb::count_launch();
+      }
+    } else {
+      EB_CUDA(lsq_launch(false, (unsigned)nb_d, s, a0, c0.T, n > 1 ? dbatch : nullptr, dbase, n));
+      eb::count_launch();
+    }
   }
   for (int i = 0; i < n; ++i) EB_CUDA(cudaEventRecord(cs[i]->ev[3], s));
   int32_t h = 0;
@@ -1258,10 +1289,13 @@ static eb_status build_post(BuildCtx& c) {
     EB_CUDA(cudaMemcpyAsync(hs.data(), status, n_slots * 4, cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
     int unbuilt = 0, nbad = 0;
+    int64_t nfp64 = 0;
     for (int64_t i = 0; i < n_slots; ++i) {
       if (hs[i] == 1) ++nbad;
       if (hs[i] == 2) unbuilt = 1;  // a row flagged by the row builder
+      if (hs[i] == 4) ++nfp64;      // left by the FP32 factorisation, solved by the FP64 one
     }
+    info->n_ls_fp64 = c.P.ls_precision == EB_LS_FP64 ? n_slots : nfp64;
     if (unbuilt) { set_error("an LS row could not be built"); return EB_ERR_INVALID; }
     if (nbad) {
       // every face whose system failed: a class slot stands for all the faces of its class, so the
@@ -2274,7 +2308,20 @@ eb_status adjoint_shape(const eb_geometry* g, const eb_stencils* st, const doubl
   Events ev;
   EB_CUDA(ev.create(4));
   EB_CUDA(cudaEventRecord(ev.e[0], s));
-  EB_CUDA(bicgstab<double>(AT, rhs, lam, st->dinv64, work, n, 1e-12, 20000, dscr, &it, &rr, s, nullptr));
+  if (st->mg) {
+    // the forward solve's multigrid, its block solves transposed; Jacobi if that does not converge
+    Multigrid* mg = st->mg;
+    mg->transpose = 1;
+    const cudaError_t e = bicgstab<double>(AT, rhs, lam, st->dinv64, work, n, 1e-12, 2000, dscr, &it, &rr, s, mg);
+    mg->transpose = 0;
+    EB_CUDA(e);
+  }
+  if (!st->mg || !(rr <= 1e-10)) {
+    EB_CUDA(cudaMemsetAsync(lam, 0, n * 8, s));
+    int it2 = 0;
+    EB_CUDA(bicgstab<double>(AT, rhs, lam, st->dinv64, work, n, 1e-12, 20000, dscr, &it2, &rr, s, nullptr));
+    it += it2;
+  }
   EB_CUDA(cudaEventRecord(ev.e[1], s));
   if (info) {
     info->iterations = it;

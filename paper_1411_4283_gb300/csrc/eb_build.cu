@@ -547,7 +547,8 @@ __device__ void row_finish(const Tables& T, double* row) {
   for (int i = 0; i < T.K; ++i) row[i] *= sc;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
@@ -557,15 +558,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 // lane of each group; *col is the column number c (or -1).  The accumulators start from the first
 // partials (no additions of zero: the FP64 pipe is the kernel's bound, and an add costs it as much
 // as an FMA).
-template <int G, int STR>
-__device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int lane, int* col) {
+template <int G, int STR, typename T>
+__device__ __forceinline__ T colsum_g(const T* P, int c0, int mm, int lane, int* col) {
   constexpr int L = 32 / G;
   const int cl = lane / G, part = lane % G;
-  double s = 0.0;
+  T s = 0;
   if (cl < mm) {
-    const double* p = P + (part * L) * KST + c0 + STR * cl;
+    const T* p = P + (part * L) * KST + c0 + STR * cl;
     if constexpr (L >= 4) {
-      double a0 = p[0], a1 = p[KST], a2 = p[2 * KST], a3 = p[3 * KST];
+      T a0 = p[0], a1 = p[KST], a2 = p[2 * KST], a3 = p[3 * KST];
 #pragma unroll
       for (int l = 4; l < L; l += 4) {
         a0 += p[l * KST];
@@ -586,8 +587,8 @@ __device__ __forceinline__ double colsum_g(const double* P, int c0, int mm, int 
   return s;
 }
 
-template <int STR>
-__device__ __forceinline__ double column_sums(const double* P, int c0, int mm, int lane, int* col) {
+template <int STR, typename T>
+__device__ __forceinline__ T column_sums(const T* P, int c0, int mm, int lane, int* col) {
   if (mm > 16) return colsum_g<1, STR>(P, c0, mm, lane, col);
   if (mm > 8) return colsum_g<2, STR>(P, c0, mm, lane, col);
   if (mm > 4) return colsum_g<4, STR>(P, c0, mm, lane, col);
@@ -596,7 +597,16 @@ __device__ __forceinline__ double column_sums(const double* P, int c0, int mm, i
   return colsum_g<32, STR>(P, c0, mm, lane, col);
 }
 
+// sign and zero tests on the bit patterns (integer pipe)
+__device__ __forceinline__ bool bits_nonzero(double v) { return __double_as_longlong(v) != 0; }
+__device__ __forceinline__ bool bits_nonzero(float v) { return __float_as_int(v) != 0; }
+__device__ __forceinline__ bool bits_positive(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool bits_positive(float v) { return __float_as_int(v) > 0; }
+
 constexpr uint32_t PAIR_WAIT_LIMIT = 1000000u;
+constexpr int LS_MAX_CORR = 6;             // corrections of the FP32-factorisation path
+constexpr double LS_CORR_TOL = 1e-12;      // converged: the last correction moved t by at most this (2-norm, relative)
+constexpr float LS_F32_MIN_DIAG = 2e-5f;   // FP32 factor with min |R_kk| below this times the largest: FP64 path
 
 // Barrier of the two warps of one system: every lane arrives on the system's mbarrier (64 arrivals
 // complete a phase; arrive releases, the wait acquires), then waits for the phase.  The wait is
@@ -631,22 +641,33 @@ __device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& pha
 // column k+1 (the next vector, updated by its owner and read by the others after a group barrier)
 // and its scalars (posted by the owner with a sequence flag and read at the start of the next step).
 //
+// QT = double: the FP64 factorisation, the rank test |R_kk| <= 1e-12 max |R_jj| and one correction of
+// the semi-normal equations (t = B z, z = R^-1 R^-T F; t += B R^-1 R^-T (F - B^T t)).
+// QT = float: the rows are built in FP64 (kept for the corrections) and factorised in FP32; the FP32
+// factor preconditions FP64 corrections of the semi-normal equations, repeated until a correction moves
+// t by at most LS_CORR_TOL (B R^-1 has singular values within 1 +- cond(B) eps_32 of one, so each
+// correction gains that factor; the corrections stop at the same rounding floor as the FP64 path).  A
+// system whose FP32 factor is too ill-conditioned for that, or whose corrections do not settle within
+// LS_MAX_CORR, gets status 3 and is solved again by the FP64 kernel (which also makes the rank test).
+//
 // BATCH: the systems of several geometries (same dimension and order) in one launch; the work counter,
 // the total system count, the scratch and the error word come from a0, each system's geometry data
 // from batch[g] with g found from the prefix sums of the systems per geometry (slot_base).
-template <bool BATCH>
-__global__ void __launch_bounds__(LS_WARPS * 32, 1)
+template <bool BATCH, typename QT>
+__global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
     k_lsq(const __grid_constant__ LsArgs a0, const __grid_constant__ Tables T, const LsArgs* __restrict__ batch,
           const int64_t* __restrict__ slot_base, int n_geom) {
+  constexpr bool F32 = sizeof(QT) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sys = warp / LS_NW, h = warp % LS_NW;
-  LsSysSmem& S = reinterpret_cast<LsSysSmem*>(smem_raw)[sys];
+  LsSysSmem<QT>& S = reinterpret_cast<LsSysSmem<QT>*>(smem_raw)[sys];
   const int K = T.K;
-  const int gs = blockIdx.x * LS_SYS + sys;
-  double* scr = a0.scratch + (int64_t)gs * MAXROWS * (MAXK + 2);  // column-major: scr[k * MAXROWS + i]
+  const int gs = blockIdx.x * ls_sys<QT>() + sys;
+  double* scr = a0.scratch + (int64_t)gs * LS_SCRATCH;  // column-major: scr[k * MAXROWS + i]
   double* scr_w = scr + (int64_t)MAXROWS * MAXK;
   double* scr_t = scr_w + MAXROWS;
+  double* stage = scr_t + MAXROWS;  // FP64 rows of the chunk (FP32 factorisation), row stride KST
   double* F = S.vec;
   double* y = S.vec + MAXK;
   double* z = S.vec + 2 * MAXK;
@@ -667,6 +688,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
     PAIR_SYNC();
     int s = S.slot;
     if (s >= a0.n_slots) break;
+    if (a0.slot_list) s = a0.slot_list[s];
     int g = 0;
     if constexpr (BATCH) {  // the geometry of system s: last g with slot_base[g] <= s
       int lo = 0, hi = n_geom - 1;
@@ -699,21 +721,27 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       x0s[dface] = -0.5;
     }
     int bad = 0;
-    for (int i = lane + 32 * h; i < K * K; i += 32 * LS_NW) S.R[i] = 0.0;
+    for (int i = lane + 32 * h; i < K * K; i += 32 * LS_NW) S.R[i] = (QT)0;
     // ---- row-streamed Householder QR of B = W A: R accumulates the triangular factor
     for (int c0 = 0; c0 < n; c0 += CH) {
       // rows of the chunk (warp h builds the row slots r with r % LS_NW == h): table rows directly,
-      // shifted rows queued (one ballot mask per row slot) and shifted with every lane busy
+      // shifted rows queued (one ballot mask per row slot) and shifted with every lane busy.  FP64
+      // factorisation: built in the chunk buffer; FP32: built in the FP64 staging rows, then rounded
+      // into the chunk buffer
       constexpr int NSLOT = (RPL + LS_NW - 1) / LS_NW;
       unsigned pend[NSLOT];
       int npend = 0;
+      auto row_at = [&](int li) -> double* {
+        if constexpr (F32) return stage + li * KST;
+        else return reinterpret_cast<double*>(S.C) + li * KST;
+      };
 #pragma unroll
       for (int rr = 0; rr < NSLOT; ++rr) {
         const int r = h + LS_NW * rr;
         pend[rr] = 0u;
         if (r >= RPL) continue;
         const int li = lane + 32 * r, i = c0 + li;
-        double* dst = S.C + li * KST;
+        double* dst = row_at(li);
         int pd = 0;
         if (i < n) {
           scr_w[i] = row_prepare(a, T, a.row_desc[p0 + i], base, x0s, dst, &bad, &pd);
@@ -735,7 +763,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
           unsigned mk = pend[rr];
           for (int t = 0; t < q; ++t) mk &= mk - 1;  // drop the q lowest set bits
           const int l = __ffs(mk) - 1;
-          row_finish(T, S.C + (l + 32 * (h + LS_NW * rr)) * KST);
+          row_finish(T, row_at(l + 32 * (h + LS_NW * rr)));
         }
       }
       __syncwarp();
@@ -744,9 +772,15 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
         const int r = h + LS_NW * rr;
         if (r >= RPL) continue;
         const int li = lane + 32 * r, i = c0 + li;
+        const double* src = row_at(li);
         if (i < n) {
-          const double* src = S.C + li * KST;
-          for (int k = 0; k < K; ++k) scr[(int64_t)k * MAXROWS + i] = src[k];
+          for (int k = 0; k < K; ++k) {
+            const double v = src[k];
+            scr[(int64_t)k * MAXROWS + i] = v;
+            if constexpr (F32) S.C[li * KST + k] = (QT)v;
+          }
+        } else if constexpr (F32) {
+          for (int k = 0; k < K; ++k) S.C[li * KST + k] = (QT)0;
         }
       }
       PAIR_SYNC();  // the chunk's rows are complete
@@ -755,37 +789,36 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       // Householder steps k = 0..K-1 on [R; C].  The update of step k and the partial dot products of
       // step k+1 share one pass: column k+1 is updated first by its owner (it is step k+1's Householder
       // vector), then each warp loads, updates, stores and dots its own later columns.
-      double ck[RPL];
+      QT ck[RPL];
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) ck[r] = r < nr ? S.C[(lane + 32 * r) * KST] : 0.0;
-      double* Pl = S.P + lane * KST;
+      for (int r = 0; r < RPL; ++r) ck[r] = r < nr ? S.C[(lane + 32 * r) * KST] : (QT)0;
+      QT* Pl = S.P + lane * KST;
       {  // partial dots of column 0 with the own columns j >= 1
-        const double* Cl = S.C + lane * KST;
+        const QT* Cl = S.C + lane * KST;
         for (int j = 1 + (h + LS_NW - 1) % LS_NW; j < K; j += LS_NW) {
-          double p0 = 0.0;
+          QT pp = 0;
 #pragma unroll
           for (int r = 0; r < RPL; ++r)
-            if (r < nr) p0 = fma(ck[r], Cl[32 * r * KST + j], p0);
-          Pl[j] = p0;
+            if (r < nr) pp = fma(ck[r], Cl[32 * r * KST + j], pp);
+          Pl[j] = pp;
         }
       }
       // Householder scalars of step k from its vector (chunk part c, R part alpha = R_kk)
-      auto hscalars = [&](const double* c, int k, double* out) {
-        double ss = c[0] * c[0];
+      auto hscalars = [&](const QT* c, int k, QT* out) {
+        QT ss = c[0] * c[0];
 #pragma unroll
         for (int r = 1; r < RPL; ++r) ss = fma(c[r], c[r], ss);
         ss = warp_sum(ss);
-        // sign and zero tests on the bit patterns (integer pipe; ss >= +0): a zero chunk column needs
-        // no reflection
-        const bool refl = __double_as_longlong(ss) != 0;
-        const double alpha = S.R[k * K + k];
-        const double sigma = refl ? sqrt(fma(alpha, alpha, ss)) : 0.0;
-        out[0] = __double_as_longlong(alpha) > 0 ? -sigma : sigma;  // beta
-        out[1] = alpha - out[0];                       // v0
-        out[2] = refl ? -1.0 / (out[0] * out[1]) : 0.0;  // gamma
-        out[3] = refl ? 1.0 : 0.0;
+        // a zero chunk column needs no reflection
+        const bool refl = bits_nonzero(ss);
+        const QT alpha = S.R[k * K + k];
+        const QT sigma = refl ? sqrt(fma(alpha, alpha, ss)) : (QT)0;
+        out[0] = bits_positive(alpha) ? -sigma : sigma;  // beta
+        out[1] = alpha - out[0];                          // v0
+        out[2] = refl ? (QT)-1 / (out[0] * out[1]) : (QT)0;  // gamma
+        out[3] = refl ? (QT)1 : (QT)0;
       };
-      double hk[4], hnext[4] = {0.0, 0.0, 0.0, 0.0};
+      QT hk[4], hnext[4] = {0, 0, 0, 0};
       hscalars(ck, 0, hk);  // step 0: both warps (the vector is column 0)
       for (int k = 0; k < K; ++k, ++stepno) {
         if (k > 0 && h != k % LS_NW) {
@@ -806,33 +839,33 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
 #pragma unroll
           for (int q = 0; q < 4; ++q) hk[q] = hnext[q];  // this warp computed them in step k-1
         }
-        const double beta = hk[0], v0 = hk[1], gamma = hk[2];
-        const bool refl = __double_as_longlong(hk[3]) != 0;  // 1.0 or 0.0
+        const QT beta = hk[0], v0 = hk[1], gamma = hk[2];
+        const bool refl = bits_nonzero(hk[3]);  // 1 or 0
         __syncwarp();  // P holds the partial dots of column k with the own later columns
         const int jf = k + 1 + (h + LS_NW - (k + 1) % LS_NW) % LS_NW;  // first own column after k
         const int mown = jf < K ? (K - 1 - jf) / LS_NW + 1 : 0;
         for (int c1 = 0; c1 < mown; c1 += 32) {
           const int mm = mown - c1 < 32 ? mown - c1 : 32;
           int col;
-          const double sum = column_sums<LS_NW>(S.P, jf + LS_NW * c1, mm, lane, &col);
+          const QT sum = column_sums<LS_NW>(S.P, jf + LS_NW * c1, mm, lane, &col);
           if (col >= 0) {
             const int j = jf + LS_NW * (c1 + col);
-            const double rkj = S.R[k * K + j];
-            const double t = gamma * fma(v0, rkj, sum);
+            const QT rkj = S.R[k * K + j];
+            const QT t = gamma * fma(v0, rkj, sum);
             if (refl) S.R[k * K + j] = fma(-t, v0, rkj);
-            tau[j] = t;
+            tau[j] = (double)t;
           }
         }
         __syncwarp();
         if (k + 1 < K) {
           const int owner = (k + 1) % LS_NW;
-          double ck1[RPL];
+          QT ck1[RPL];
           if (h == owner) {  // column k+1: update, keep as the next Householder vector
-            const double t1 = tau[k + 1];
+            const QT t1 = (QT)tau[k + 1];
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
-              double* c = S.C + (lane + 32 * r) * KST + k + 1;
-              ck1[r] = 0.0;
+              QT* c = S.C + (lane + 32 * r) * KST + k + 1;
+              ck1[r] = 0;
               if (r < nr) {
                 ck1[r] = fma(-t1, ck[r], *c);
                 *c = ck1[r];
@@ -842,10 +875,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
           PAIR_SYNC();
           if (h != owner) {
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) ck1[r] = r < nr ? S.C[(lane + 32 * r) * KST + k + 1] : 0.0;
+            for (int r = 0; r < RPL; ++r) ck1[r] = r < nr ? S.C[(lane + 32 * r) * KST + k + 1] : (QT)0;
           } else {
             // step k+1's scalars, off the other warp's path: it picks them up at the start of step k+1
-            double hn[4];
+            QT hn[4];
             hscalars(ck1, k + 1, hn);  // R_{k+1,k+1} is not touched by step k
             if (lane == 0) {
 #pragma unroll
@@ -860,42 +893,42 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
           constexpr int W = LS_NW;
           int j = k + 2 + (h + W - (k + 2) % W) % W;
           for (; j + 3 * W < K; j += 4 * W) {
-            const double t0 = tau[j], tt1 = tau[j + W], t2 = tau[j + 2 * W], t3 = tau[j + 3 * W];
-            double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+            const QT t0 = (QT)tau[j], tt1 = (QT)tau[j + W], t2 = (QT)tau[j + 2 * W], t3 = (QT)tau[j + 3 * W];
+            QT q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               if (r < nr) {
-                double* c = S.C + (lane + 32 * r) * KST + j;
-                const double a0 = fma(-t0, ck[r], c[0]), a1 = fma(-tt1, ck[r], c[W]);
-                const double a2 = fma(-t2, ck[r], c[2 * W]), a3 = fma(-t3, ck[r], c[3 * W]);
-                c[0] = a0;
-                c[W] = a1;
-                c[2 * W] = a2;
-                c[3 * W] = a3;
-                p0 = fma(ck1[r], a0, p0);
-                p1 = fma(ck1[r], a1, p1);
-                p2 = fma(ck1[r], a2, p2);
-                p3 = fma(ck1[r], a3, p3);
+                QT* c = S.C + (lane + 32 * r) * KST + j;
+                const QT e0 = fma(-t0, ck[r], c[0]), e1 = fma(-tt1, ck[r], c[W]);
+                const QT e2 = fma(-t2, ck[r], c[2 * W]), e3 = fma(-t3, ck[r], c[3 * W]);
+                c[0] = e0;
+                c[W] = e1;
+                c[2 * W] = e2;
+                c[3 * W] = e3;
+                q0 = fma(ck1[r], e0, q0);
+                q1 = fma(ck1[r], e1, q1);
+                q2 = fma(ck1[r], e2, q2);
+                q3 = fma(ck1[r], e3, q3);
               }
             }
-            Pl[j] = p0;
-            Pl[j + W] = p1;
-            Pl[j + 2 * W] = p2;
-            Pl[j + 3 * W] = p3;
+            Pl[j] = q0;
+            Pl[j + W] = q1;
+            Pl[j + 2 * W] = q2;
+            Pl[j + 3 * W] = q3;
           }
           for (; j < K; j += W) {
-            const double t0 = tau[j];
-            double p0 = 0.0;
+            const QT t0 = (QT)tau[j];
+            QT q0 = 0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               if (r < nr) {
-                double* c = S.C + (lane + 32 * r) * KST + j;
-                const double a0 = fma(-t0, ck[r], c[0]);
-                c[0] = a0;
-                p0 = fma(ck1[r], a0, p0);
+                QT* c = S.C + (lane + 32 * r) * KST + j;
+                const QT e0 = fma(-t0, ck[r], c[0]);
+                c[0] = e0;
+                q0 = fma(ck1[r], e0, q0);
               }
             }
-            Pl[j] = p0;
+            Pl[j] = q0;
           }
 #pragma unroll
           for (int r = 0; r < RPL; ++r) ck[r] = ck1[r];
@@ -905,7 +938,8 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       }
       PAIR_SYNC();  // both warps are done with the chunk and with R
     }
-    // ---- rank check (|R_kk| <= 1e-12 max |R_jj| counts as rank deficient)
+    // ---- rank check (FP64: |R_kk| <= 1e-12 max |R_jj| counts as rank deficient; FP32: a factor that
+    // ill-conditioned leaves the system to the FP64 kernel)
     const int anyb = __any_sync(0xffffffffu, bad);
     if (lane == 0) S.bad[h] = anyb;
     PAIR_SYNC();
@@ -916,25 +950,26 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
     }
     double dmax = 0.0, dmin = INFINITY;
     for (int k = 0; k < K; ++k) {
-      double v = fabs(S.R[k * K + k]);
+      double v = fabs((double)S.R[k * K + k]);
       dmax = fmax(dmax, v);
       dmin = fmin(dmin, v);
     }
-    if (!bad && !(dmin > 1e-12 * dmax)) bad = 1;
+    if (!bad && !(dmin > (F32 ? (double)LS_F32_MIN_DIAG : 1e-12) * dmax)) bad = F32 ? 3 : 1;
     if (bad) {
       if (h == 0 && lane == 0) a.status[s] = bad;
-      for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) a.row_val[p0 + i] = 0.0;
+      if (bad != 3)
+        for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) a.row_val[p0 + i] = 0.0;
       PAIR_SYNC();
       continue;
     }
-    // ---- z = R^-1 R^-T rhs (two triangular solves, lanes own columns), by warp 0
+    // ---- z = R^-1 R^-T rhs (two triangular solves, lanes own columns), by warp 0, in FP64
     auto solve_rtr = [&](const double* rhs, double* outz) {
       for (int j = lane; j < K; j += 32) y[j] = rhs[j];
       __syncwarp();
       for (int k = 0; k < K; ++k) {  // R^T y = rhs (forward)
         double yk = y[k] * rinv[k];
         __syncwarp();
-        for (int j = k + 1 + lane; j < K; j += 32) y[j] = fma(-S.R[k * K + j], yk, y[j]);
+        for (int j = k + 1 + lane; j < K; j += 32) y[j] = fma(-(double)S.R[k * K + j], yk, y[j]);
         if (lane == 0) y[k] = yk;
         __syncwarp();
       }
@@ -943,13 +978,13 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       for (int k = K - 1; k >= 0; --k) {  // R z = y (backward)
         double zk = outz[k] * rinv[k];
         __syncwarp();
-        for (int j = lane; j < k; j += 32) outz[j] = fma(-S.R[j * K + k], zk, outz[j]);
+        for (int j = lane; j < k; j += 32) outz[j] = fma(-(double)S.R[j * K + k], zk, outz[j]);
         if (lane == 0) outz[k] = zk;
         __syncwarp();
       }
     };
     if (h == 0) {
-      for (int k = lane; k < K; k += 32) rinv[k] = 1.0 / S.R[k * K + k];
+      for (int k = lane; k < K; k += 32) rinv[k] = 1.0 / (double)S.R[k * K + k];
       // ---- F_hat (Sec. 2.2.1): grid face: p_d m_f^{p-e_d}; EB face: sum_d p_d m_{d,f}^{p-e_d}
       for (int i = lane; i < K; i += 32) {
         double f = 0.0;
@@ -974,42 +1009,98 @@ __global__ void __launch_bounds__(LS_WARPS * 32, 1)
       solve_rtr(F, z);
     }
     PAIR_SYNC();
-    // ---- corrected semi-normal equations: t1 = B z, r = F - B^T t1, t = t1 + B R^-1 R^-T r
-    // (rows split between the warps; warps h > 0 accumulate B^T t1 in the free chunk buffer)
-    double* Pw = h == 0 ? S.P : S.C + (h - 1) * 32 * KST;
-    for (int k = 0; k < K; ++k) Pw[lane * KST + k] = 0.0;
+    // ---- corrected semi-normal equations: t = B z, then corrections t += B R^-1 R^-T (F - B^T t).
+    // FP64 factorisation: one correction, B^T t from per-lane partials over the rows (warps h > 0 in the
+    // free chunk buffer) and column sums.  FP32: lanes own columns and each warp sums half of the rows
+    // (the chunk buffer is too small for the partials in FP64)
     for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
       double t1 = 0.0;
       for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
       scr_t[i] = t1;
-      for (int k = 0; k < K; ++k) Pw[lane * KST + k] = fma(scr[(int64_t)k * MAXROWS + i], t1, Pw[lane * KST + k]);
     }
-    __syncwarp();
-    for (int c1 = 0; c1 < K; c1 += 32) {
-      int mm = K - c1 < 32 ? K - c1 : 32;
-      int col;
-      double sum = column_sums<1>(Pw, c1, mm, lane, &col);
-      if (col >= 0) S.xch[h * MAXK + c1 + col] = sum;
-    }
-    PAIR_SYNC();
-    double* z2 = S.C + CH * KST - 2 * MAXK;  // the chunk buffer's tail is free after the exchange
-    if (h == 0) {
-      for (int c = lane; c < K; c += 32) {
-        double sx = 0.0;
-        for (int q = 0; q < LS_NW; ++q) sx += S.xch[q * MAXK + c];
-        tau[c] = F[c] - sx;
+    double* z2 = reinterpret_cast<double*>(S.C) + (CH * KST * sizeof(QT)) / 8 - 2 * MAXK;  // the chunk buffer's tail
+    bool settled = false;
+    for (int corr = 0; corr < (F32 ? LS_MAX_CORR : 1) && !settled; ++corr) {
+      if constexpr (F32) {
+        PAIR_SYNC();  // t is complete
+        const int i0 = h * ((n + 1) >> 1), i1 = h ? n : (n + 1) >> 1;
+        double s0 = 0.0, s1 = 0.0;
+        const double* c0p = scr + (int64_t)lane * MAXROWS;
+        const double* c1p = scr + (int64_t)(lane + 32) * MAXROWS;
+        for (int i = i0; i < i1; ++i) {
+          const double t1 = scr_t[i];
+          if (lane < K) s0 = fma(c0p[i], t1, s0);
+          if (lane + 32 < K) s1 = fma(c1p[i], t1, s1);
+        }
+        if (lane < K) S.xch[h * MAXK + lane] = s0;
+        if (lane + 32 < K) S.xch[h * MAXK + lane + 32] = s1;
+      } else {
+        double* Pw = h == 0 ? reinterpret_cast<double*>(S.P) : reinterpret_cast<double*>(S.C) + (h - 1) * 32 * KST;
+        for (int k = 0; k < K; ++k) Pw[lane * KST + k] = 0.0;
+        for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
+          const double t1 = scr_t[i];
+          for (int k = 0; k < K; ++k) Pw[lane * KST + k] = fma(scr[(int64_t)k * MAXROWS + i], t1, Pw[lane * KST + k]);
+        }
+        __syncwarp();
+        for (int c1 = 0; c1 < K; c1 += 32) {
+          int mm = K - c1 < 32 ? K - c1 : 32;
+          int col;
+          double sum = column_sums<1>(Pw, c1, mm, lane, &col);
+          if (col >= 0) S.xch[h * MAXK + c1 + col] = sum;
+        }
       }
-      __syncwarp();
-      solve_rtr(tau, z2);
+      PAIR_SYNC();
+      if (h == 0) {
+        for (int c = lane; c < K; c += 32) {
+          double sx = 0.0;
+          for (int q = 0; q < LS_NW; ++q) sx += S.xch[q * MAXK + c];
+          tau[c] = F[c] - sx;
+        }
+        __syncwarp();
+        solve_rtr(tau, z2);
+      }
+      PAIR_SYNC();
+      if constexpr (F32) {
+        double dd = 0.0, tt = 0.0;  // the correction's and the result's squared norms (this warp's rows)
+        for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
+          double dt = 0.0;
+          for (int k = 0; k < K; ++k) dt = fma(scr[(int64_t)k * MAXROWS + i], z2[k], dt);
+          const double t = scr_t[i] + dt;
+          scr_t[i] = t;
+          dd = fma(dt, dt, dd);
+          tt = fma(t, t, tt);
+        }
+        dd = warp_sum(dd);
+        tt = warp_sum(tt);
+        __syncwarp();
+        if (lane == 0) {
+          S.xch[h * MAXK] = dd;
+          S.xch[h * MAXK + 1] = tt;
+        }
+        PAIR_SYNC();
+        double sd = 0.0, st = 0.0;
+        for (int q = 0; q < LS_NW; ++q) {
+          sd += S.xch[q * MAXK];
+          st += S.xch[q * MAXK + 1];
+        }
+        settled = sd <= LS_CORR_TOL * LS_CORR_TOL * st;
+      } else {
+        for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
+          double t = scr_t[i];
+          for (int k = 0; k < K; ++k) t = fma(scr[(int64_t)k * MAXROWS + i], z2[k], t);
+          scr_t[i] = t;
+        }
+        settled = true;
+      }
     }
-    PAIR_SYNC();
-    for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
-      double t = scr_t[i];
-      for (int k = 0; k < K; ++k) t = fma(scr[(int64_t)k * MAXROWS + i], z2[k], t);
-      a.row_val[p0 + i] = scr_w[i] * t;  // s_hat = W t
+    if (!settled) {  // FP32 factor: the corrections did not settle; the FP64 kernel takes the system
+      if (h == 0 && lane == 0) a.status[s] = 3;
+      PAIR_SYNC();
+      continue;
     }
-    if (h == 0 && lane == 0) a.status[s] = 0;
-    PAIR_SYNC();
+    for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) a.row_val[p0 + i] = scr_w[i] * scr_t[i];  // s_hat = W t
+    if (h == 0 && lane == 0) a.status[s] = a0.slot_list ? 4 : 0;  // 4: solved by the FP64 pass after the FP32 one
+    PAIR_SYNC();  // xch and the chunk buffer are free for the next system
   }
 }
 
@@ -1152,10 +1243,17 @@ __global__ void k_assemble_b(AsmArgs a, const int32_t* __restrict__ cells, int64
 
 namespace eb {
 
-cudaError_t lsq_prepare(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_lsq<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_lsq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+size_t lsq_smem(bool fp32) {
+  return fp32 ? (size_t)LS_SYS_F * sizeof(LsSysSmem<float>) : (size_t)LS_SYS * sizeof(LsSysSmem<double>);
+}
+
+cudaError_t lsq_prepare() {
+  const int sd = (int)lsq_smem(false), sf = (int)lsq_smem(true);
+  cudaError_t e = cudaFuncSetAttribute(k_lsq<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lsq<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lsq<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lsq<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+  return e;
 }
 
 // ============================================================ 4c. adjoint of the stencil solves
@@ -1487,10 +1585,32 @@ cudaError_t stencil_adjoint_launch(unsigned blocks, cudaStream_t s, const LsArgs
   return cudaGetLastError();
 }
 
-cudaError_t lsq_launch(unsigned blocks, size_t smem, cudaStream_t s, const LsArgs& a0, const Tables& T,
+cudaError_t lsq_launch(bool fp32, unsigned blocks, cudaStream_t s, const LsArgs& a0, const Tables& T,
                        const LsArgs* batch, const int64_t* slot_base, int n_geom) {
-  if (batch) k_lsq<true><<<blocks, LS_WARPS * 32, smem, s>>>(a0, T, batch, slot_base, n_geom);
-  else k_lsq<false><<<blocks, LS_WARPS * 32, smem, s>>>(a0, T, nullptr, nullptr, 1);
+  const size_t smem = lsq_smem(fp32);
+  if (fp32) {
+    constexpr unsigned nt = LS_SYS_F * LS_NW * 32;
+    if (batch) k_lsq<true, float><<<blocks, nt, smem, s>>>(a0, T, batch, slot_base, n_geom);
+    else k_lsq<false, float><<<blocks, nt, smem, s>>>(a0, T, nullptr, nullptr, 1);
+  } else {
+    constexpr unsigned nt = LS_SYS * LS_NW * 32;
+    if (batch) k_lsq<true, double><<<blocks, nt, smem, s>>>(a0, T, batch, slot_base, n_geom);
+    else k_lsq<false, double><<<blocks, nt, smem, s>>>(a0, T, nullptr, nullptr, 1);
+  }
+  return cudaGetLastError();
+}
+
+// the systems with status 3 (global numbers: + base) appended to list[*count]
+__global__ void k_ls_fallback(const int32_t* __restrict__ status, int64_t n, int64_t base, int32_t* list,
+                              int32_t* count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && status[i] == 3) list[atomicAdd(count, 1)] = (int32_t)(base + i);
+}
+
+cudaError_t lsq_fallback_list(const int32_t* status, int64_t n, int64_t base, int32_t* list, int32_t* count,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ls_fallback<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(status, n, base, list, count);
   return cudaGetLastError();
 }
 

@@ -27,34 +27,50 @@ struct GatherArgs {
   int32_t* too_many;         // capacity flag
 };
 
-// LS kernel shape (compile-time; EB_LS_SYS / EB_LS_RPL override it for tuning builds)
+// LS kernel shape (compile-time; EB_LS_SYS / EB_LS_SYS_F / EB_LS_RPL override it for tuning builds)
 #ifndef EB_LS_SYS
 #define EB_LS_SYS 4
+#endif
+#ifndef EB_LS_SYS_F
+#define EB_LS_SYS_F 6
 #endif
 #ifndef EB_LS_RPL
 #define EB_LS_RPL 4
 #endif
-constexpr int LS_SYS = EB_LS_SYS;      // systems in flight per CTA (shared memory bound)
+constexpr int LS_SYS = EB_LS_SYS;      // systems in flight per CTA, FP64 factorisation (shared memory bound)
+constexpr int LS_SYS_F = EB_LS_SYS_F;  // systems in flight per CTA, FP32 factorisation
 constexpr int LS_NW = 2;               // warps per system (each owns the columns j with j % LS_NW == its rank)
-constexpr int LS_WARPS = LS_NW * LS_SYS;
 constexpr int RPL = EB_LS_RPL;  // rows per lane per chunk
 constexpr int CH = 32 * RPL;  // rows per chunk
-constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 64-bit access)
+constexpr int KST = MAXK;     // row stride in shared memory (odd: conflict-free 32- and 64-bit access)
+template <typename QT>
+__host__ __device__ constexpr int ls_sys() {
+  return sizeof(QT) == 8 ? LS_SYS : LS_SYS_F;
+}
 
+// Per-system shared memory; QT is the precision of the factorisation (the corrected semi-normal
+// equations run in FP64 either way)
+template <typename QT>
 struct __align__(16) LsSysSmem {
-  double R[MAXK * MAXK];     // triangular factor, row-major
-  double C[CH * KST];        // current chunk of weighted rows
-  double P[32 * KST];        // partial dot products, column j in P[lane][j] (each column owned by one warp)
+  QT R[MAXK * MAXK + 1];     // triangular factor, row-major (one pad entry keeps C 8-byte aligned)
+  QT C[CH * KST];            // current chunk of weighted rows
+  QT P[32 * KST];            // partial dot products, column j in P[lane][j] (each column owned by one warp)
   double vec[5 * MAXK];      // F, y, z, tau, 1/R_kk
   double xch[LS_NW * MAXK];  // the warps' partial sums (corrected semi-normal equations)
-  double hs[2][4];           // Householder scalars (beta, v0, gamma, reflect) of step k in hs[k % 2]
+  QT hs[2][4];               // Householder scalars (beta, v0, gamma, reflect) of step k in hs[k % 2]
   unsigned long long bar;    // barrier of the system's warps (mbarrier, 32 * LS_NW arrivals per phase)
   int32_t slot;              // system being solved
   int32_t bad[LS_NW];        // per-warp row flags
   int32_t hs_seq[2];         // step number whose scalars hs[k % 2] holds (posted after the values)
+  int32_t done;              // corrections converged (FP32 factorisation)
 };
-static_assert(sizeof(LsSysSmem) % 16 == 0, "per-system blocks stay 16-byte aligned");
-static_assert(LS_SYS * sizeof(LsSysSmem) <= 232448, "the systems of a CTA fit in 227 KB of shared memory");
+static_assert(sizeof(LsSysSmem<double>) % 16 == 0 && sizeof(LsSysSmem<float>) % 16 == 0,
+              "per-system blocks stay 16-byte aligned");
+static_assert(LS_SYS * sizeof(LsSysSmem<double>) <= 232448 && LS_SYS_F * sizeof(LsSysSmem<float>) <= 232448,
+              "the systems of a CTA fit in 227 KB of shared memory");
+// per-system global scratch (doubles): the rows column-major (MAXROWS x MAXK), the weights and t
+// (MAXROWS each), and the FP64 row staging of the FP32 factorisation (CH x KST)
+constexpr int64_t LS_SCRATCH = (int64_t)MAXROWS * (MAXK + 2) + (int64_t)CH * KST;
 
 // offsets in units of h/2 span [-11, 11] on each axis (volume, EB and wall rows)
 constexpr int TAB_S = 23;
@@ -77,9 +93,10 @@ struct LsArgs {
   const uint32_t* row_desc;
   double* row_val;
   int64_t n_slots;
+  const int32_t* slot_list;  // [n_slots] systems to solve (null: 0 .. n_slots-1)
   int32_t* next;       // work counter
-  int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row
-  double* scratch;     // per system slot: MAXROWS * (K + 2) doubles, column-major rows
+  int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row, 3 left to the FP64 path
+  double* scratch;     // per system in flight: LS_SCRATCH doubles
   int32_t* err;        // set when a bounded wait between the two warps of a system gives up
   const double* ftab;  // [TAB_N][MAXK] weighted rows of full cells, by offset
   const double* wtab;  // [TAB_N] weights, by offset
@@ -137,9 +154,14 @@ cudaError_t stencil_adjoint_launch(unsigned blocks, cudaStream_t s, const LsArgs
                                    const AdjArgs& g);
 // k_lsq launchers (eb_build.cu): shared-memory attribute, then one launch over the systems of one
 // geometry (batch == null) or of several (batch[g] per geometry, slot_base prefix sums of their systems)
-cudaError_t lsq_prepare(size_t smem);
-cudaError_t lsq_launch(unsigned blocks, size_t smem, cudaStream_t s, const LsArgs& a0, const Tables& T,
+// fp32: the FP32-factorisation kernel (systems it cannot finish get status 3), else the FP64 one
+cudaError_t lsq_prepare();
+size_t lsq_smem(bool fp32);
+cudaError_t lsq_launch(bool fp32, unsigned blocks, cudaStream_t s, const LsArgs& a0, const Tables& T,
                        const LsArgs* batch, const int64_t* slot_base, int n_geom);
+// the systems with status 3 (global numbers: + base) appended to list[*count]
+cudaError_t lsq_fallback_list(const int32_t* status, int64_t n, int64_t base, int32_t* list, int32_t* count,
+                              cudaStream_t s);
 __global__ void k_full_rows(Dims dm, const Tables* T, double* ftab, double* wtab);
 __global__ void k_assemble_rows(AsmArgs a, const int32_t* rep_cell, int64_t nrep, int64_t row0, int32_t* err);
 __global__ void k_assemble_b(AsmArgs a, const int32_t* cells, int64_t ncells, int64_t* cnt, const int64_t* bptr,

@@ -727,6 +727,22 @@ __device__ __forceinline__ void mon3(int i, int* p) {
   p[2] = i;
 }
 
+// mon3's exponents packed p0 | p1 << 4 | p2 << 8, for loops unrolled over a compile-time count (the
+// accumulators of such loops stay in registers)
+__host__ __device__ constexpr int mon3_packed(int i) {
+  int q = 0;
+  while (i >= (q + 1) * (q + 2) / 2) {
+    i -= (q + 1) * (q + 2) / 2;
+    ++q;
+  }
+  int a = 0;
+  while (i > a) {
+    i -= a + 1;
+    ++a;
+  }
+  return (q - a) | ((a - i) << 4) | (i << 8);
+}
+
 __device__ __forceinline__ void sort_small(double* v, int n) {
   for (int i = 1; i < n; ++i)
     for (int j = i; j > 0 && v[j] < v[j - 1]; --j) {
@@ -942,9 +958,10 @@ __device__ void sphere_patch_quad(double cx, double cy, double cz, double R, con
 // one table of a cut cell's EB patch integrals (thread per cell and table): t = 0 int xi^p dA, t = 1..3
 // int xi^p n_(t-1) dA, t = 4 int xi^(p+e_d) n_d dA (the patch part of the volume moments, d the cell's
 // divergence direction); divided by h^2
-__global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double h, const int32_t* __restrict__ cells, int64_t n,
-                               const int32_t* __restrict__ cbody, int q, int K, double* eb, double* ebn,
-                               double* volp) {
+template <int Q>
+__global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double h, const int32_t* __restrict__ cells,
+                               int64_t n, const int32_t* __restrict__ cbody, double* eb, double* ebn, double* volp) {
+  constexpr int K = (Q + 1) * (Q + 2) * (Q + 3) / 6;
   const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tt >= 5 * n) return;
   const int64_t t = tt / 5;
@@ -958,14 +975,9 @@ __global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double 
   // divergence-theorem direction (table 4): the smallest component of the centre offset, the direction
   // most tangent to the patch (see k_sphere_vol)
   const int dd = (fabs(cx) <= fabs(cy) && fabs(cx) <= fabs(cz)) ? 0 : (fabs(cy) <= fabs(cz) ? 1 : 2);
-  double acc[35];
-  int pk[35];  // exponents of monomial k, packed p0 | p1 << 4 | p2 << 8
-  for (int k = 0; k < K; ++k) {
-    int p[3];
-    mon3(k, p);
-    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
-    acc[k] = 0.0;
-  }
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
   sphere_patch_quad(cx, cy, cz, R, gl, glt,
                     [&](double x, double y, double z, double ex, double ey, double ez, double w) {
                       double f = w;
@@ -975,18 +987,23 @@ __global__ void k_sphere_patch(Spheres B, GlRule gl, GlRuleT glt, int N, double 
                       } else if (table == 4) {
                         f *= sgn * (dd == 0 ? ex : (dd == 1 ? ey : ez)) / R;
                       }
-                      double xp[GEO_MAXQ + 2], yp[GEO_MAXQ + 2], zp[GEO_MAXQ + 2];
+                      double xp[Q + 2], yp[Q + 2], zp[Q + 2];
                       xp[0] = yp[0] = zp[0] = 1.0;
-                      for (int k = 1; k <= q + 1; ++k) {
+#pragma unroll
+                      for (int k = 1; k <= Q + 1; ++k) {
                         xp[k] = xp[k - 1] * x;
                         yp[k] = yp[k - 1] * y;
                         zp[k] = zp[k - 1] * z;
                       }
                       const int ex4 = table == 4 && dd == 0, ey4 = table == 4 && dd == 1, ez4 = table == 4 && dd == 2;
-                      for (int k = 0; k < K; ++k)
-                        acc[k] += f * xp[(pk[k] & 15) + ex4] * yp[((pk[k] >> 4) & 15) + ey4] * zp[(pk[k] >> 8) + ez4];
+#pragma unroll
+                      for (int k = 0; k < K; ++k) {
+                        const int pk = mon3_packed(k);
+                        acc[k] += f * xp[(pk & 15) + ex4] * yp[((pk >> 4) & 15) + ey4] * zp[(pk >> 8) + ez4];
+                      }
                     });
   double* dst = table == 0 ? eb + t * K : (table == 4 ? volp + t * K : ebn + (t * 3 + table - 1) * K);
+#pragma unroll
   for (int k = 0; k < K; ++k) dst[k] = acc[k];
 }
 
@@ -1098,24 +1115,22 @@ __device__ void sphere_edge_quad(const double* cc, double R, const GlRule& gl, F
 }
 
 // one derivative table of a cut cell (thread per cell and table): t = 0 the volume moments, t = 1 the EB
-// moments, t = 2..4 the EB moments weighted by n_(t-2)
+// moments, t = 2..4 the EB moments weighted by n_(t-2); Q the moment degree (K = (Q+1)(Q+2)(Q+3)/6
+// monomials, unrolled)
+template <int Q>
 __global__ void k_sphere_cells_dv(Spheres B, GlRule gl, GlRuleT glt, int N, double h, ShapeVel sv,
                                   const int32_t* __restrict__ cells, int64_t n, const int32_t* __restrict__ cbody,
-                                  int q, int K, double* dvol, double* deb, double* debn) {
+                                  double* dvol, double* deb, double* debn) {
+  constexpr int K = (Q + 1) * (Q + 2) * (Q + 3) / 6;
   const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tt >= 5 * n) return;
   const int64_t t = tt / 5;
   const int table = (int)(tt % 5);
   const int c = cells[t];
   const int b = cbody[c];
-  double acc[35];
-  int pk[35];
-  for (int k = 0; k < K; ++k) {
-    int p[3];
-    mon3(k, p);
-    pk[k] = p[0] | (p[1] << 4) | (p[2] << 8);
-    acc[k] = 0.0;
-  }
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
   if (shape_moves(sv, b)) {
     const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
     const double* C = B.c[b];
@@ -1124,24 +1139,24 @@ __global__ void k_sphere_cells_dv(Spheres B, GlRule gl, GlRuleT glt, int N, doub
     const double sgn = B.inside ? 1.0 : -1.0;
     const int dn = table - 2;
     auto add = [&](double x, double y, double z, const double* Nv, double cf, double cg) {
-      double xp[GEO_MAXQ + 1], yp[GEO_MAXQ + 1], zp[GEO_MAXQ + 1];
+      double xp[Q + 1], yp[Q + 1], zp[Q + 1];
       xp[0] = yp[0] = zp[0] = 1.0;
-      for (int k = 1; k <= q; ++k) {
+#pragma unroll
+      for (int k = 1; k <= Q; ++k) {
         xp[k] = xp[k - 1] * x;
         yp[k] = yp[k - 1] * y;
         zp[k] = zp[k - 1] * z;
       }
+#pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int p0 = pk[k] & 15, p1 = (pk[k] >> 4) & 15, p2 = pk[k] >> 8;
+        const int pk = mon3_packed(k);
+        const int p0 = pk & 15, p1 = (pk >> 4) & 15, p2 = pk >> 8;
         double v = cf * xp[p0] * yp[p1] * zp[p2];
-        if (cg != 0.0) {
-          double gN = 0.0;  // grad_xi f . N
-          if (p0 > 0) gN += p0 * xp[p0 - 1] * yp[p1] * zp[p2] * Nv[0];
-          if (p1 > 0) gN += p1 * xp[p0] * yp[p1 - 1] * zp[p2] * Nv[1];
-          if (p2 > 0) gN += p2 * xp[p0] * yp[p1] * zp[p2 - 1] * Nv[2];
-          v += cg * gN;
-        }
-        acc[k] += v;
+        double gN = 0.0;  // grad_xi f . N
+        if (p0 > 0) gN += p0 * xp[p0 > 0 ? p0 - 1 : 0] * yp[p1] * zp[p2] * Nv[0];
+        if (p1 > 0) gN += p1 * xp[p0] * yp[p1 > 0 ? p1 - 1 : 0] * zp[p2] * Nv[1];
+        if (p2 > 0) gN += p2 * xp[p0] * yp[p1] * zp[p2 > 0 ? p2 - 1 : 0] * Nv[2];
+        acc[k] += fma(cg, gN, v);
       }
     };
     sphere_patch_quad(cx, cy, cz, R, gl, glt,
@@ -1170,9 +1185,11 @@ __global__ void k_sphere_cells_dv(Spheres B, GlRule gl, GlRuleT glt, int N, doub
         add(pos[0], pos[1], pos[2], ev, cf, 0.0);
       });
     }
+#pragma unroll
     for (int k = 0; k < K; ++k) acc[k] /= h;
   }
   double* dst = table == 0 ? dvol + t * K : (table == 1 ? deb + t * K : debn + (t * 3 + table - 2) * K);
+#pragma unroll
   for (int k = 0; k < K; ++k) dst[k] = acc[k];
 }
 
@@ -1286,10 +1303,16 @@ cudaError_t geometry_shape_derivative(const eb_geometry* g, const ShapeVel& sv, 
     for (int k = 0; k < 3; ++k) B.c[b][k] = g->centers[b][k];
     B.r[b] = g->radii[b];
   }
-  const int K = (q + 1) * (q + 2) * (q + 3) / 6;
   if (d.n_cut > 0) {
-    k_sphere_cells_dv<<<(unsigned)((5 * (int64_t)d.n_cut + 127) / 128), 128, 0, s>>>(
-        B, gl, glt, N, h, sv, d.cut_cell, d.n_cut, g->cell_body, q, K, dvol, deb, debn);
+    const unsigned nb = (unsigned)((5 * (int64_t)d.n_cut + 127) / 128);
+    const int64_t nc = d.n_cut;
+    switch (q) {
+      case 0: k_sphere_cells_dv<0><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 1: k_sphere_cells_dv<1><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 2: k_sphere_cells_dv<2><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 3: k_sphere_cells_dv<3><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      default: k_sphere_cells_dv<4><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+    }
     eb::count_launch();
   }
   for (int dir = 0; dir < 3; ++dir) {
@@ -1615,7 +1638,13 @@ extern "C" eb_status eb_geometry_spheres(int32_t N, int32_t n_body, const double
       GEO_TRY(A.temp(&ebn0, nc0 * 3 * K));
       GEO_TRY(A.temp(&volp, nc0 * K));
       if (nc0 > 0) {
-        k_sphere_patch<<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, q, K, eb0, ebn0, volp);
+        switch (q) {
+          case 0: k_sphere_patch<0><<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, eb0, ebn0, volp); break;
+          case 1: k_sphere_patch<1><<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, eb0, ebn0, volp); break;
+          case 2: k_sphere_patch<2><<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, eb0, ebn0, volp); break;
+          case 3: k_sphere_patch<3><<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, eb0, ebn0, volp); break;
+          default: k_sphere_patch<4><<<nb256(5 * nc0), 256, 0, s>>>(B, gl, glt, N, h, cut0, nc0, cbody, eb0, ebn0, volp); break;
+        }
         k_sphere_vol<<<nb256(nc0), 256, 0, s>>>(B, glt, N, h, cut0, nc0, cbody, q, K, volp, vol0);
         eb::count_launch();
         eb::count_launch();

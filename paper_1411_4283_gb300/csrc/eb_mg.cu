@@ -443,8 +443,10 @@ __global__ void k_blk_invert(int nblk, double* __restrict__ M, float* __restrict
 }
 
 // res_i = r_ci - (A z)_ci for the cells of every block; one warp per cell, the lanes splitting the
-// footprint (few cells, long rows: a thread per cell leaves the GPU idle behind 637 dependent loads)
-template <typename T>
+// footprint (few cells, long rows: a thread per cell leaves the GPU idle behind 637 dependent loads).
+// TR: the transposed operator, (A^T z)_c = sum_f A(c - off_f, f) z_(c - off_f) (the rows that reach c;
+// a linear offset that wraps across a grid line lands on a row whose entry there is zero)
+template <typename T, bool TR>
 __global__ void k_blk_res(RowSrc a, int nblk, const int32_t* __restrict__ cells, const T* __restrict__ r,
                           const T* __restrict__ z, T* __restrict__ res) {
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
@@ -462,18 +464,28 @@ __global__ void k_blk_res(RowSrc a, int nblk, const int32_t* __restrict__ cells,
   }
   T acc = (T)0;
   const int64_t hi = a.ncell - 1;
-  for (int f = lane; f < a.nfoot; f += 32) {
-    int64_t q = c + a.foot_off[f];
-    q = q < 0 ? 0 : (q > hi ? hi : q);  // out-of-domain entries have zero coefficients
-    acc = fma(coef_at<T>(a, row, f), z[q], acc);
+  if (TR) {
+    for (int f = lane; f < a.nfoot; f += 32) {
+      const int64_t q = c - a.foot_off[f];
+      if (q < 0 || q > hi) continue;
+      const int64_t rq = row_of_cell(a, q);
+      if (rq == -2) continue;
+      acc = fma(coef_at<T>(a, rq, f), z[q], acc);
+    }
+  } else {
+    for (int f = lane; f < a.nfoot; f += 32) {
+      int64_t q = c + a.foot_off[f];
+      q = q < 0 ? 0 : (q > hi ? hi : q);  // out-of-domain entries have zero coefficients
+      acc = fma(coef_at<T>(a, row, f), z[q], acc);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) res[t] = r[c] - acc;
 }
 
-// z_ci += sum_j inv(A_BB)_ij res_j (blocks may overlap: additive)
-template <typename T>
+// z_ci += sum_j inv(A_BB)_ij res_j (blocks may overlap: additive); TR: inv(A_BB^T) = inv(A_BB)^T
+template <typename T, bool TR>
 __global__ void k_blk_corr(int nblk, const int32_t* __restrict__ cells, const T* __restrict__ inv,
                            const T* __restrict__ res, T* z) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -481,10 +493,15 @@ __global__ void k_blk_corr(int nblk, const int32_t* __restrict__ cells, const T*
   const int32_t c = cells[t];
   if (c < 0) return;
   const int64_t b = t / BLK, i = t % BLK;
-  const T* m = inv + (b * BLK + i) * BLK;
   const T* rr = res + b * BLK;
   T d = (T)0;
-  for (int j = 0; j < BLK; ++j) d = fma(m[j], rr[j], d);
+  if (TR) {
+    const T* m = inv + b * BLK * BLK + i;
+    for (int j = 0; j < BLK; ++j) d = fma(m[j * BLK], rr[j], d);
+  } else {
+    const T* m = inv + (b * BLK + i) * BLK;
+    for (int j = 0; j < BLK; ++j) d = fma(m[j], rr[j], d);
+  }
   atomicAdd(z + c, d);
 }
 
@@ -796,8 +813,13 @@ cudaError_t mg_precond(const Multigrid& mgc, const T* r, T* z, cudaStream_t s) {
     const T* inv;
     if constexpr (sizeof(T) == 4) inv = mg.blk_inv32;
     else inv = mg.blk_inv64;
-    k_blk_res<T><<<nb256(nt * 32), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
-    k_blk_corr<T><<<nb256(nt), 256, 0, s>>>(mg.nblk, mg.blk_cells, inv, (const T*)mg.blk_res, z);
+    if (mg.transpose) {
+      k_blk_res<T, true><<<nb256(nt * 32), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
+      k_blk_corr<T, true><<<nb256(nt), 256, 0, s>>>(mg.nblk, mg.blk_cells, inv, (const T*)mg.blk_res, z);
+    } else {
+      k_blk_res<T, false><<<nb256(nt * 32), 256, 0, s>>>(a, mg.nblk, mg.blk_cells, r, z, (T*)mg.blk_res);
+      k_blk_corr<T, false><<<nb256(nt), 256, 0, s>>>(mg.nblk, mg.blk_cells, inv, (const T*)mg.blk_res, z);
+    }
     eb::count_launches(2);
   }
   return cudaGetLastError();

@@ -47,6 +47,9 @@ struct Multigrid {
   const int32_t* foot_off = nullptr;
   int16_t* foot_lut = nullptr;    // [(2R+3)^3] footprint index of an offset (-1 outside)
   int R = 0;
+  // 1: precondition the transposed operator (the adjoint solve): the V-cycle (on a symmetric
+  // approximation) as it is, the block solves with A_BB^T
+  int transpose = 0;
 };
 
 struct MgFineInput {

@@ -49,7 +49,7 @@ def test_status_strings(lib):
     assert lib.eb_status_string(0) == b"ok"
     assert b"rank" in lib.eb_status_string(2)
     lib.eb_abi_version.restype = ctypes.c_int32
-    assert lib.eb_abi_version() == 2
+    assert lib.eb_abi_version() == 3
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):

@@ -28,7 +28,7 @@ def circle32():
 
 def test_library_loaded():
     import paper_1411_4283_gb300 as P
-    assert P.load().eb_abi_version() == 2
+    assert P.load().eb_abi_version() == 3
 
 
 @pytest.mark.parametrize("Q", [4, 2])
