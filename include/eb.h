@@ -124,6 +124,10 @@ typedef struct eb_build_info {
   double ms_classify, ms_gather, ms_lsq, ms_assemble; /* device time per phase */
   int64_t n_ls_fp64;        /* systems solved by the FP64 factorisation (all of them with
                                EB_LS_FP64; with EB_LS_MIXED those the FP32 factor could not carry) */
+  double ls_fp64_flops;     /* FP64 flops the LS kernels executed (factorisations, semi-normal
+                               solves and corrections; row construction not counted) */
+  double ls_fp32_flops;     /* FP32 flops of the FP32 factorisations (EB_LS_MIXED).  For a batch
+                               both are the launch's totals shared out by the systems' counts. */
 } eb_build_info;
 
 /* Build all flux stencils and the operator (Sec. 2.2-2.4).

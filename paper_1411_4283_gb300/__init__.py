@@ -49,7 +49,8 @@ class EbBuildInfo(ctypes.Structure):
                 ("n_class_faces", ctypes.c_int64), ("n_classes", ctypes.c_int32), ("max_rows", ctypes.c_int32),
                 ("n_irregular_rows", ctypes.c_int64), ("n_row_classes", ctypes.c_int32),
                 ("lsq_flops", ctypes.c_int64), ("ms_classify", ctypes.c_double), ("ms_gather", ctypes.c_double),
-                ("ms_lsq", ctypes.c_double), ("ms_assemble", ctypes.c_double), ("n_ls_fp64", ctypes.c_int64)]
+                ("ms_lsq", ctypes.c_double), ("ms_assemble", ctypes.c_double), ("n_ls_fp64", ctypes.c_int64),
+                ("ls_fp64_flops", ctypes.c_double), ("ls_fp32_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -602,6 +602,7 @@ struct BuildCtx {
   double* invk = nullptr;
   LsArgs la;            // least-squares inputs (scratch, work counter and error word set per launch)
   int32_t* status = nullptr;
+  double ls_flops[2] = {0.0, 0.0};  // executed FP64 and FP32 flops of the LS launches
   eb_status rc = EB_OK;  // a phase's failure in a batch worker thread, with its message and faces
   std::string err;
   std::vector<int64_t> bad;
@@ -1210,9 +1211,12 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   double* scratch;
   EB_TRY(tmp.get(&scratch, (size_t)std::max(nb_d * LS_SYS, fp32 ? nb_f * LS_SYS_F : 0) * LS_SCRATCH));
   int32_t *next, *lerr, *nfb, *fblist = nullptr;
+  double* flops;
   EB_TRY(tmp.get(&next, 1));
   EB_TRY(tmp.get(&lerr, 1));
   EB_TRY(tmp.get(&nfb, 1));
+  EB_TRY(tmp.get(&flops, 2));
+  EB_CUDA(cudaMemsetAsync(flops, 0, 16, s));
   EB_CUDA(cudaMemsetAsync(next, 0, 4, s));
   EB_CUDA(cudaMemsetAsync(lerr, 0, 4, s));
   EB_CUDA(cudaMemsetAsync(nfb, 0, 4, s));
@@ -1222,6 +1226,7 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   a0.next = next;
   a0.err = lerr;
   a0.scratch = scratch;
+  a0.flops = flops;
   LsArgs* dbatch = nullptr;
   int64_t* dbase = nullptr;
   if (n > 1) {
@@ -1263,8 +1268,15 @@ static eb_status build_ls(BuildCtx* const* cs, int n, cudaStream_t s) {
   }
   for (int i = 0; i < n; ++i) EB_CUDA(cudaEventRecord(cs[i]->ev[3], s));
   int32_t h = 0;
+  double hf[2] = {0.0, 0.0};
   EB_CUDA(cudaMemcpyAsync(&h, lerr, 4, cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(hf, flops, 16, cudaMemcpyDeviceToHost, s));
   EB_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {  // a batch's totals shared out by the systems' counts
+    const double share = total > 0 ? (double)cs[i]->n_slots / (double)total : 0.0;
+    cs[i]->ls_flops[0] = hf[0] * share;
+    cs[i]->ls_flops[1] = hf[1] * share;
+  }
   if (h) { set_error("a bounded device wait gave up in the least-squares kernel"); return EB_ERR_TIMEOUT; }
   return EB_OK;
 }
@@ -1296,6 +1308,8 @@ static eb_status build_post(BuildCtx& c) {
       if (hs[i] == 4) ++nfp64;      // left by the FP32 factorisation, solved by the FP64 one
     }
     info->n_ls_fp64 = c.P.ls_precision == EB_LS_FP64 ? n_slots : nfp64;
+    info->ls_fp64_flops = c.ls_flops[0];
+    info->ls_fp32_flops = c.ls_flops[1];
     if (unbuilt) { set_error("an LS row could not be built"); return EB_ERR_INVALID; }
     if (nbad) {
       // every face whose system failed: a class slot stands for all the faces of its class, so the

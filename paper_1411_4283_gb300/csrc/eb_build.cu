@@ -604,8 +604,9 @@ __device__ __forceinline__ bool bits_positive(double v) { return __double_as_lon
 __device__ __forceinline__ bool bits_positive(float v) { return __float_as_int(v) > 0; }
 
 constexpr uint32_t PAIR_WAIT_LIMIT = 1000000u;
-constexpr int LS_MAX_CORR = 6;             // corrections of the FP32-factorisation path
-constexpr double LS_CORR_TOL = 1e-12;      // converged: the last correction moved t by at most this (2-norm, relative)
+constexpr int LS_MAX_CORR = 8;             // corrections of the FP32-factorisation path
+constexpr double LS_CORR_TOL = 1e-14;      // converged: the last correction moved t by at most this (2-norm, relative)
+constexpr double LS_CORR_FLOOR = 1e-11;    // ... or by at most this and less than half the one before (rounding floor)
 constexpr float LS_F32_MIN_DIAG = 2e-5f;   // FP32 factor with min |R_kk| below this times the largest: FP64 path
 
 // Barrier of the two warps of one system: every lane arrives on the system's mbarrier (64 arrivals
@@ -645,8 +646,9 @@ __device__ __forceinline__ bool pair_sync(unsigned long long* bar, uint32_t& pha
 // the semi-normal equations (t = B z, z = R^-1 R^-T F; t += B R^-1 R^-T (F - B^T t)).
 // QT = float: the rows are built in FP64 (kept for the corrections) and factorised in FP32; the FP32
 // factor preconditions FP64 corrections of the semi-normal equations, repeated until a correction moves
-// t by at most LS_CORR_TOL (B R^-1 has singular values within 1 +- cond(B) eps_32 of one, so each
-// correction gains that factor; the corrections stop at the same rounding floor as the FP64 path).  A
+// t by at most LS_CORR_TOL, or stops shrinking at the rounding floor (B R^-1 has singular values within
+// 1 +- cond(B) eps_32 of one, so each correction gains about that factor; the corrections end at the
+// same rounding floor as the FP64 path).  A
 // system whose FP32 factor is too ill-conditioned for that, or whose corrections do not settle within
 // LS_MAX_CORR, gets status 3 and is solved again by the FP64 kernel (which also makes the rank test).
 //
@@ -1020,7 +1022,10 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
     }
     double* z2 = reinterpret_cast<double*>(S.C) + (CH * KST * sizeof(QT)) / 8 - 2 * MAXK;  // the chunk buffer's tail
     bool settled = false;
+    double prev_sd = INFINITY;  // the previous correction's squared norm
+    int ncorr = 0;
     for (int corr = 0; corr < (F32 ? LS_MAX_CORR : 1) && !settled; ++corr) {
+      ++ncorr;
       if constexpr (F32) {
         PAIR_SYNC();  // t is complete
         const int i0 = h * ((n + 1) >> 1), i1 = h ? n : (n + 1) >> 1;
@@ -1083,7 +1088,9 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
           sd += S.xch[q * MAXK];
           st += S.xch[q * MAXK + 1];
         }
-        settled = sd <= LS_CORR_TOL * LS_CORR_TOL * st;
+        settled = sd <= LS_CORR_TOL * LS_CORR_TOL * st ||
+                  (sd <= LS_CORR_FLOOR * LS_CORR_FLOOR * st && sd > 0.25 * prev_sd);
+        prev_sd = sd;
       } else {
         for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
           double t = scr_t[i];
@@ -1092,6 +1099,13 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
         }
         settled = true;
       }
+    }
+    if (h == 0 && lane == 0 && a0.flops) {  // executed flops of this system (the row construction not counted)
+      const double nn = n, kk = K;
+      const double fact = 2.0 * nn * kk * kk - 2.0 / 3.0 * kk * kk * kk;  // Householder QR of n x K
+      const double semi = 2.0 * nn * kk + 2.0 * kk * kk + ncorr * (4.0 * nn * kk + 2.0 * kk * kk);
+      atomicAdd(a0.flops + 0, F32 ? semi : fact + semi);
+      if (F32) atomicAdd(a0.flops + 1, fact);
     }
     if (!settled) {  // FP32 factor: the corrections did not settle; the FP64 kernel takes the system
       if (h == 0 && lane == 0) a.status[s] = 3;

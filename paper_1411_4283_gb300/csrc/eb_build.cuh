@@ -98,6 +98,7 @@ struct LsArgs {
   int32_t* status;     // [n_slots]: 0 ok, 1 rank deficient, 2 unsupported row, 3 left to the FP64 path
   double* scratch;     // per system in flight: LS_SCRATCH doubles
   int32_t* err;        // set when a bounded wait between the two warps of a system gives up
+  double* flops;       // [2] executed flops, accumulated: FP64 (factorisation, corrections), FP32 (factorisation)
   const double* ftab;  // [TAB_N][MAXK] weighted rows of full cells, by offset
   const double* wtab;  // [TAB_N] weights, by offset
 };

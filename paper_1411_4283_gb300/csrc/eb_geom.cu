@@ -1082,115 +1082,221 @@ __global__ void k_geo_close_faces3(const uint8_t* __restrict__ cflag, int N, int
 // xi_d = e the circle has radius rho = (R^2 - (e - c_d)^2)^(1/2), N . n_p = sign(e) (e - c_d) / R is
 // constant along it, and V_e dl = -V (N . n_p) R dt in the arc angle t.
 
-// fn(pos, ev, wl) at the quadrature nodes of the patch's edges: pos the node, ev = pos - centre = R N,
-// wl = -(N . n_p) R dt (V wl = V_e dl / h)
-template <class Fn>
-__device__ void sphere_edge_quad(const double* cc, double R, const GlRule& gl, Fn&& fn) {
-  for (int dd = 0; dd < 3; ++dd) {
-    const int u = dd == 0 ? 1 : 0, v = dd == 2 ? 1 : 2;
-    for (int s = -1; s <= 1; s += 2) {
-      const double e = 0.5 * s, dn = e - cc[dd], r2 = R * R - dn * dn;
-      if (!(r2 > 0.0)) continue;
-      const double rho = sqrt(r2), en = s * dn / R;
-      double a0[4], a1[4];
-      const int narc = square_arcs(cc[u], cc[v], rho, a0, a1);
-      for (int a = 0; a < narc; ++a) {
-        const int npc = (int)ceil((a1[a] - a0[a]) / (0.25 * M_PI));
-        const double span = (a1[a] - a0[a]) / npc;
-        for (int pc = 0; pc < npc; ++pc) {
-          const double mm = a0[a] + (pc + 0.5) * span, hw = 0.5 * span;
-          for (int g = 0; g < GEO_GL; ++g) {
-            const double tt = mm + hw * gl.x[g];
-            double pos[3], ev[3];
-            pos[dd] = e;
-            pos[u] = cc[u] + rho * cos(tt);
-            pos[v] = cc[v] + rho * sin(tt);
-            for (int d = 0; d < 3; ++d) ev[d] = pos[d] - cc[d];
-            fn(pos, ev, -en * R * gl.w[g] * hw);
-          }
-        }
-      }
-    }
-  }
+// The derivative tables of the cut cells with one warp per cell: the lanes own the monomials (k = lane
+// and lane + 32), the quadrature nodes (the patch rule of sphere_patch_quad; 20-point Gauss-Legendre on
+// pieces of at most pi/4 of the edge arcs) are computed 32 at a time, one per lane with its speed and the speed's surface gradient, and broadcast to
+// the warp, which accumulates the five tables at once: each node's position, weight and sines serve
+// all tables and monomials.
+__device__ __forceinline__ double ipow_small(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
 }
 
-// one derivative table of a cut cell (thread per cell and table): t = 0 the volume moments, t = 1 the EB
-// moments, t = 2..4 the EB moments weighted by n_(t-2); Q the moment degree (K = (Q+1)(Q+2)(Q+3)/6
-// monomials, unrolled)
+// f = x^e0 y^e1 z^e2 and grad f . N for the exponents e
+__device__ __forceinline__ void mono_grad(const int* e, double x, double y, double z, double n0, double n1, double n2,
+                                          double* f, double* gN) {
+  const double px = e[0] > 0 ? ipow_small(x, e[0] - 1) : 0.0, py = e[1] > 0 ? ipow_small(y, e[1] - 1) : 0.0;
+  const double pz = e[2] > 0 ? ipow_small(z, e[2] - 1) : 0.0;
+  const double fx = e[0] > 0 ? px * x : 1.0, fy = e[1] > 0 ? py * y : 1.0, fz = e[2] > 0 ? pz * z : 1.0;
+  *f = fx * fy * fz;
+  double g = 0.0;
+  if (e[0] > 0) g = fma(e[0] * px * fy * fz, n0, g);
+  if (e[1] > 0) g = fma(e[1] * fx * py * fz, n1, g);
+  if (e[2] > 0) g = fma(e[2] * fx * fy * pz, n2, g);
+  *gN = g;
+}
+
 template <int Q>
-__global__ void k_sphere_cells_dv(Spheres B, GlRule gl, GlRuleT glt, int N, double h, ShapeVel sv,
-                                  const int32_t* __restrict__ cells, int64_t n, const int32_t* __restrict__ cbody,
-                                  double* dvol, double* deb, double* debn) {
+__global__ void __launch_bounds__(128) k_sphere_cells_dw(Spheres B, GlRule gl, GlRuleT glt, int N, double h,
+                                                         ShapeVel sv, const int32_t* __restrict__ cells, int64_t n,
+                                                         const int32_t* __restrict__ cbody, double* dvol,
+                                                         double* deb, double* debn) {
   constexpr int K = (Q + 1) * (Q + 2) * (Q + 3) / 6;
-  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tt >= 5 * n) return;
-  const int64_t t = tt / 5;
-  const int table = (int)(tt % 5);
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;
   const int c = cells[t];
   const int b = cbody[c];
-  double acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const bool own1 = lane + 32 < K;
+  int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
+  if (lane < K) {
+    const int pk = mon3_packed(lane);
+    e0[0] = pk & 15;
+    e0[1] = (pk >> 4) & 15;
+    e0[2] = pk >> 8;
+  }
+  if (own1) {
+    const int pk = mon3_packed(lane + 32);
+    e1[0] = pk & 15;
+    e1[1] = (pk >> 4) & 15;
+    e1[2] = pk >> 8;
+  }
+  double a0[5] = {0, 0, 0, 0, 0}, a1[5] = {0, 0, 0, 0, 0};
   if (shape_moves(sv, b)) {
     const int ix = c % N, iy = (c / N) % N, iz = c / (N * N);
     const double* C = B.c[b];
     const double cx = (C[0] - (ix + 0.5) * h) / h, cy = (C[1] - (iy + 0.5) * h) / h;
     const double cz = (C[2] - (iz + 0.5) * h) / h, R = B.r[b] / h;
-    const double sgn = B.inside ? 1.0 : -1.0;
-    const int dn = table - 2;
-    auto add = [&](double x, double y, double z, const double* Nv, double cf, double cg) {
-      double xp[Q + 1], yp[Q + 1], zp[Q + 1];
-      xp[0] = yp[0] = zp[0] = 1.0;
-#pragma unroll
-      for (int k = 1; k <= Q; ++k) {
-        xp[k] = xp[k - 1] * x;
-        yp[k] = yp[k - 1] * y;
-        zp[k] = zp[k - 1] * z;
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int pk = mon3_packed(k);
-        const int p0 = pk & 15, p1 = (pk >> 4) & 15, p2 = pk >> 8;
-        double v = cf * xp[p0] * yp[p1] * zp[p2];
-        double gN = 0.0;  // grad_xi f . N
-        if (p0 > 0) gN += p0 * xp[p0 > 0 ? p0 - 1 : 0] * yp[p1] * zp[p2] * Nv[0];
-        if (p1 > 0) gN += p1 * xp[p0] * yp[p1 > 0 ? p1 - 1 : 0] * zp[p2] * Nv[1];
-        if (p2 > 0) gN += p2 * xp[p0] * yp[p1] * zp[p2 > 0 ? p2 - 1 : 0] * Nv[2];
-        acc[k] += fma(cg, gN, v);
-      }
+    const double sgn = B.inside ? 1.0 : -1.0, c2 = 2.0 / R;
+    // patch node (broadcast): position, normal, w V, w grad_G V (h-scaled)
+    auto patch_node = [&](double x, double y, double z, double n0, double n1, double n2, double wv, double g0,
+                          double g1, double g2, const int* e, double* a) {
+      double f, gN;
+      mono_grad(e, x, y, z, n0, n1, n2, &f, &gN);
+      const double u = wv * fma(c2, f, gN);
+      a[0] = fma(sgn * wv, f, a[0]);
+      a[1] += u;
+      a[2] = fma(sgn, fma(u, n0, -g0 * f), a[2]);
+      a[3] = fma(sgn, fma(u, n1, -g1 * f), a[3]);
+      a[4] = fma(sgn, fma(u, n2, -g2 * f), a[4]);
     };
-    sphere_patch_quad(cx, cy, cz, R, gl, glt,
-                      [&](double x, double y, double z, double ex, double ey, double ez, double w) {
-                        const double Nv[3] = {ex / R, ey / R, ez / R};
-                        const double X[3] = {C[0] + h * ex, C[1] + h * ey, C[2] + h * ez};
-                        double gv[3];
-                        const double V = shape_speed(sv, B.inside, b, X, 3, gv);
-                        if (table == 0) {
-                          add(x, y, z, Nv, sgn * w * V, 0.0);
-                        } else if (table == 1) {
-                          add(x, y, z, Nv, w * V * 2.0 / R, w * V);
-                        } else {
-                          const double gn = gv[0] * Nv[0] + gv[1] * Nv[1] + gv[2] * Nv[2];
-                          const double gG = h * (gv[dn] - gn * Nv[dn]);
-                          add(x, y, z, Nv, sgn * w * (V * 2.0 / R * Nv[dn] - gG), sgn * w * V * Nv[dn]);
-                        }
-                      });
-    if (table >= 1) {
-      const double cc[3] = {cx, cy, cz};
-      sphere_edge_quad(cc, R, gl, [&](const double* pos, const double* ev, double wl) {
-        const double X[3] = {C[0] + h * ev[0], C[1] + h * ev[1], C[2] + h * ev[2]};
-        double gv[3];
-        double cf = shape_speed(sv, B.inside, b, X, 3, gv) * wl;
-        if (table >= 2) cf *= sgn * ev[dn] / R;
-        add(pos[0], pos[1], pos[2], ev, cf, 0.0);
-      });
+    // the patch: theta panels as in sphere_patch_quad, the phi nodes of each arc 32 at a time
+    const double zl = fmax(-0.5, cz - R), zh = fmin(0.5, cz + R);
+    double br[20];
+    int nb = 0;
+    br[nb++] = zl;
+    br[nb++] = zh;
+    for (int e = -1; e <= 1; e += 2) {
+      const double dd[2] = {(0.5 * e - cx) * (0.5 * e - cx), (0.5 * e - cy) * (0.5 * e - cy)};
+      for (int j = 0; j < 2; ++j) {
+        const double qq = R * R - dd[j];
+        if (qq > 0.0)
+          for (int sg = -1; sg <= 1; sg += 2) {
+            const double zz = cz + sg * sqrt(qq);
+            if (zz > zl && zz < zh) br[nb++] = zz;
+          }
+      }
+      for (int e2 = -1; e2 <= 1; e2 += 2) {
+        const double qq = R * R - (0.5 * e - cx) * (0.5 * e - cx) - (0.5 * e2 - cy) * (0.5 * e2 - cy);
+        if (qq > 0.0)
+          for (int sg = -1; sg <= 1; sg += 2) {
+            const double zz = cz + sg * sqrt(qq);
+            if (zz > zl && zz < zh) br[nb++] = zz;
+          }
+      }
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] /= h;
+    for (int i = 0; i < nb; ++i) br[i] = acos(fmin(1.0, fmax(-1.0, (br[i] - cz) / R)));
+    sort_small(br, nb);
+    for (int pnl = 0; pnl + 1 < nb; ++pnl) {
+      if (br[pnl + 1] <= br[pnl]) continue;
+      for (int gz = 0; gz < GEO_GLT; ++gz) {
+        double th, wth;
+        sin2_node(glt, gz, br[pnl], br[pnl + 1], &th, &wth);
+        const double z = cz + R * cos(th), rho = R * sin(th);
+        const double wz = wth * rho;
+        if (rho <= 0.0) continue;
+        double aa0[4], aa1[4];
+        const int narc = square_arcs(cx, cy, rho, aa0, aa1);
+        for (int a = 0; a < narc; ++a) {
+          const int npc = (int)ceil((aa1[a] - aa0[a]) / (0.25 * M_PI));
+          const double span = (aa1[a] - aa0[a]) / npc, hw = 0.5 * span;
+          const int M = npc * GEO_GL;
+          for (int base = 0; base < M; base += 32) {
+            const int j = base + lane;
+            double x = 0, y = 0, n0 = 0, n1 = 0, n2 = 0, wv = 0, g0 = 0, g1 = 0, g2 = 0;
+            if (j < M) {
+              const int pc = j / GEO_GL, g = j % GEO_GL;
+              const double ph = aa0[a] + (pc + 0.5) * span + hw * gl.x[g];
+              const double w = wz * gl.w[g] * hw * R;
+              const double cp = cos(ph), sp = sin(ph);
+              const double ex = rho * cp, ey = rho * sp, ez = z - cz;
+              x = cx + ex;
+              y = cy + ey;
+              n0 = ex / R;
+              n1 = ey / R;
+              n2 = ez / R;
+              const double X[3] = {C[0] + h * ex, C[1] + h * ey, C[2] + h * ez};
+              double gv[3];
+              const double V = shape_speed(sv, B.inside, b, X, 3, gv);
+              const double gn = gv[0] * n0 + gv[1] * n1 + gv[2] * n2;
+              wv = w * V;
+              g0 = w * h * (gv[0] - gn * n0);
+              g1 = w * h * (gv[1] - gn * n1);
+              g2 = w * h * (gv[2] - gn * n2);
+            }
+            const int cnt = min(32, M - base);
+            for (int q = 0; q < cnt; ++q) {
+              const double qx = __shfl_sync(0xffffffffu, x, q), qy = __shfl_sync(0xffffffffu, y, q);
+              const double q0 = __shfl_sync(0xffffffffu, n0, q), q1 = __shfl_sync(0xffffffffu, n1, q);
+              const double q2 = __shfl_sync(0xffffffffu, n2, q), qw = __shfl_sync(0xffffffffu, wv, q);
+              const double r0 = __shfl_sync(0xffffffffu, g0, q), r1 = __shfl_sync(0xffffffffu, g1, q);
+              const double r2 = __shfl_sync(0xffffffffu, g2, q);
+              patch_node(qx, qy, z, q0, q1, q2, qw, r0, r1, r2, e0, a0);
+              if (own1) patch_node(qx, qy, z, q0, q1, q2, qw, r0, r1, r2, e1, a1);
+            }
+          }
+        }
+      }
+    }
+    // the edges: the arcs of the circles on the cell's face planes inside the faces; V_e dl / h = V wl,
+    // wl = -(N . n_p) R dt
+    const double cc[3] = {cx, cy, cz};
+    for (int dd = 0; dd < 3; ++dd) {
+      const int u = dd == 0 ? 1 : 0, v = dd == 2 ? 1 : 2;
+      for (int s = -1; s <= 1; s += 2) {
+        const double e = 0.5 * s, dn = e - cc[dd], r2 = R * R - dn * dn;
+        if (!(r2 > 0.0)) continue;
+        const double rho = sqrt(r2), en = s * dn / R;
+        double aa0[4], aa1[4];
+        const int narc = square_arcs(cc[u], cc[v], rho, aa0, aa1);
+        for (int a = 0; a < narc; ++a) {
+          const int npc = (int)ceil((aa1[a] - aa0[a]) / (0.25 * M_PI));
+          const double span = (aa1[a] - aa0[a]) / npc, hw = 0.5 * span;
+          const int M = npc * GEO_GL;
+          for (int base = 0; base < M; base += 32) {
+            const int j = base + lane;
+            double p[3] = {0, 0, 0}, nv[3] = {0, 0, 0}, we = 0;
+            if (j < M) {
+              const int pc = j / GEO_GL, g = j % GEO_GL;
+              const double tt = aa0[a] + (pc + 0.5) * span + hw * gl.x[g];
+              p[dd] = e;
+              p[u] = cc[u] + rho * cos(tt);
+              p[v] = cc[v] + rho * sin(tt);
+              for (int k = 0; k < 3; ++k) nv[k] = (p[k] - cc[k]) / R;
+              const double X[3] = {C[0] + h * R * nv[0], C[1] + h * R * nv[1], C[2] + h * R * nv[2]};
+              double gv[3];
+              we = shape_speed(sv, B.inside, b, X, 3, gv) * (-en * R * gl.w[g] * hw);
+            }
+            const int cnt = min(32, M - base);
+            for (int q = 0; q < cnt; ++q) {
+              const double px = __shfl_sync(0xffffffffu, p[0], q), py = __shfl_sync(0xffffffffu, p[1], q);
+              const double pz = __shfl_sync(0xffffffffu, p[2], q), q0 = __shfl_sync(0xffffffffu, nv[0], q);
+              const double q1 = __shfl_sync(0xffffffffu, nv[1], q), q2 = __shfl_sync(0xffffffffu, nv[2], q);
+              const double qw = __shfl_sync(0xffffffffu, we, q);
+              double f, gN;
+              mono_grad(e0, px, py, pz, q0, q1, q2, &f, &gN);
+              a0[1] = fma(qw, f, a0[1]);
+              a0[2] = fma(sgn * qw * q0, f, a0[2]);
+              a0[3] = fma(sgn * qw * q1, f, a0[3]);
+              a0[4] = fma(sgn * qw * q2, f, a0[4]);
+              if (own1) {
+                mono_grad(e1, px, py, pz, q0, q1, q2, &f, &gN);
+                a1[1] = fma(qw, f, a1[1]);
+                a1[2] = fma(sgn * qw * q0, f, a1[2]);
+                a1[3] = fma(sgn * qw * q1, f, a1[3]);
+                a1[4] = fma(sgn * qw * q2, f, a1[4]);
+              }
+            }
+          }
+        }
+      }
+    }
+    for (int k = 0; k < 5; ++k) {
+      a0[k] /= h;
+      a1[k] /= h;
+    }
   }
-  double* dst = table == 0 ? dvol + t * K : (table == 1 ? deb + t * K : debn + (t * 3 + table - 2) * K);
-#pragma unroll
-  for (int k = 0; k < K; ++k) dst[k] = acc[k];
+  if (lane < K) {
+    dvol[t * K + lane] = a0[0];
+    deb[t * K + lane] = a0[1];
+    for (int d = 0; d < 3; ++d) debn[(t * 3 + d) * K + lane] = a0[2 + d];
+  }
+  if (own1) {
+    dvol[t * K + lane + 32] = a1[0];
+    deb[t * K + lane + 32] = a1[1];
+    for (int d = 0; d < 3; ++d) debn[(t * 3 + d) * K + lane + 32] = a1[2 + d];
+  }
 }
 
 // derivative of the tangential moments of the cut faces normal to dir (thread per face)
@@ -1304,14 +1410,14 @@ cudaError_t geometry_shape_derivative(const eb_geometry* g, const ShapeVel& sv, 
     B.r[b] = g->radii[b];
   }
   if (d.n_cut > 0) {
-    const unsigned nb = (unsigned)((5 * (int64_t)d.n_cut + 127) / 128);
+    const unsigned nb = (unsigned)((32 * (int64_t)d.n_cut + 127) / 128);  // a warp per cut cell
     const int64_t nc = d.n_cut;
     switch (q) {
-      case 0: k_sphere_cells_dv<0><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
-      case 1: k_sphere_cells_dv<1><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
-      case 2: k_sphere_cells_dv<2><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
-      case 3: k_sphere_cells_dv<3><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
-      default: k_sphere_cells_dv<4><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 0: k_sphere_cells_dw<0><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 1: k_sphere_cells_dw<1><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 2: k_sphere_cells_dw<2><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      case 3: k_sphere_cells_dw<3><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
+      default: k_sphere_cells_dw<4><<<nb, 128, 0, s>>>(B, gl, glt, N, h, sv, d.cut_cell, nc, g->cell_body, dvol, deb, debn); break;
     }
     eb::count_launch();
   }

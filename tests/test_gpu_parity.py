@@ -153,7 +153,10 @@ def _row_sample_cells(g, order, rng):
 @pytest.mark.parametrize("order", [4, 2])
 def test_apply_3d_sampled_rows(order):
     """Operator rows at sampled cells: (L phi)_v assembled by the oracle from the cell's own face
-    stencils, against the GPU apply of the whole field (FP64 at 1e-12, FP32 at 1e-5 of the row scale)."""
+    stencils, against the GPU apply of the whole field.  FP64: 1e-12 of sum_f max|s_f| sum|phi_cols| / h^2
+    (the stencils of both sides are exact to rounding, about cond(WA) eps = 1e-14 .. 3e-13 of each face's
+    largest coefficient against a 40-digit reference, the oracle's SVD included; the row value itself
+    can cancel to a few thousandths of those terms).  FP32: 1e-5 of the field's row scale."""
     import torch
     import paper_1411_4283_gb300 as P
     g = E.sphere_box_config(20)
@@ -169,12 +172,15 @@ def test_apply_3d_sampled_rows(order):
     scale = np.abs(yg).max()
     for c in _row_sample_cells(g, order, np.random.default_rng(4)):
         acc = 0.0
+        bound = 0.0
         for fid, sg in o.cell_flux_faces(c):
             cols, s = o.stencil(fid)
             vm = cols >= 0
             acc += sg * float(s[vm] @ phi[cols[vm]])
+            bound += np.abs(s).max() * np.abs(phi[cols[vm]]).sum()
         acc /= g.h ** 2
-        assert abs(yg[c] - acc) <= 1e-12 * max(abs(acc), scale * 1e-3), (c, yg[c], acc)
+        bound /= g.h ** 2
+        assert abs(yg[c] - acc) <= 1e-12 * bound, (c, yg[c], acc, bound)
         assert abs(yg32[c] - acc) <= 1e-5 * scale, (c, yg32[c], acc)
 
 
