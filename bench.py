@@ -31,8 +31,9 @@ import tempfile
 import time
 
 # The oracle is single-threaded: one BLAS thread per process, set before numpy loads its BLAS (the
-# CPU baseline runs one oracle process per host core; more threads would oversubscribe them)
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+# CPU baseline runs one oracle process per host core; more threads would oversubscribe them).  OpenMP
+# is left alone: the host input generator (eb_inputs, OpenMP) uses every core before the pool starts.
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import numpy as np
@@ -41,10 +42,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cut-face LS stencils/s; EB Laplacian apply GB/s (% HBM); solve s at fixed error"
-# DRAM bytes (read + write) of one k_lsq launch per LS system solved, from an ncu capture of the
-# 48^3 sphere build: 823.3 MB read + 7363.4 MB written for 90,123 systems.  The writes are the
-# per-warp row scratch (each system's rows, kept for the corrected semi-normal step) leaving L2.
-LSQ_DRAM_BYTES_PER_SYSTEM = (823.290368e6 + 7363.410e6) / 90123
+# DRAM bytes (read + write) of the least-squares launch per LS system solved, from an ncu capture of
+# the 48^3 sphere build (the mixed path, k_lsq<false, float>): 9.848 GB read + 16.650 GB written for
+# 90,123 systems.  The traffic is the per-system scratch (FP64 rows staged, then read by every
+# correction) of the ~900 systems in flight, which exceeds L2.
+LSQ_DRAM_BYTES_PER_SYSTEM = (9.848110e9 + 16.649961e9) / 90123
 
 
 def parse():
@@ -458,8 +460,8 @@ def main():
                 "executed_fp64_tflops": ex64, "executed_fp64_frac": ex64 / fp64_pk,
                 "executed_fp32_tflops": ex32, "executed_fp32_frac": ex32 / fp32_pk,
                 "systems_fp64_factorised": int(bi["n_ls_fp64"]),
-                "traffic_note": "bytes per launch, scaled from an ncu capture at 48^3 by systems solved (FP64 "
-                                "factorisation; the mixed path's traffic not captured)",
+                "traffic_note": "bytes per launch, scaled from an ncu capture of the mixed path at 48^3 by "
+                                "systems solved",
                 "peak_kind": f"derived: {sms} SMs (read from the device) x 2 DFMA/clk x 2 flop x max SM clock; "
                              f"the FP64 FMA probe (bench.py --mode peak) measures 1.058 TFLOP/s",
                 "share_of_step": lsq_share}
