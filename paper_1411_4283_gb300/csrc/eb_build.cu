@@ -597,35 +597,6 @@ __device__ __forceinline__ T column_sums(const T* P, int c0, int mm, int lane, i
   return colsum_g<32, STR>(P, c0, mm, lane, col);
 }
 
-// sum_k B[k * MAXROWS + i] v[k] with four independent accumulators (the loads of a row's K entries
-// overlap instead of waiting on one FMA chain)
-__device__ __forceinline__ double row_dot4(const double* __restrict__ B, int i, const double* v, int K) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int k = 0;
-  for (; k + 3 < K; k += 4) {
-    a0 = fma(B[(int64_t)k * MAXROWS + i], v[k], a0);
-    a1 = fma(B[(int64_t)(k + 1) * MAXROWS + i], v[k + 1], a1);
-    a2 = fma(B[(int64_t)(k + 2) * MAXROWS + i], v[k + 2], a2);
-    a3 = fma(B[(int64_t)(k + 3) * MAXROWS + i], v[k + 3], a3);
-  }
-  for (; k < K; ++k) a0 = fma(B[(int64_t)k * MAXROWS + i], v[k], a0);
-  return (a0 + a1) + (a2 + a3);
-}
-
-// sum_{i0 <= i < i1} c[i] t[i] with four independent accumulators
-__device__ __forceinline__ double col_dot4(const double* __restrict__ c, const double* __restrict__ t, int i0, int i1) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int i = i0;
-  for (; i + 3 < i1; i += 4) {
-    a0 = fma(c[i], t[i], a0);
-    a1 = fma(c[i + 1], t[i + 1], a1);
-    a2 = fma(c[i + 2], t[i + 2], a2);
-    a3 = fma(c[i + 3], t[i + 3], a3);
-  }
-  for (; i < i1; ++i) a0 = fma(c[i], t[i], a0);
-  return (a0 + a1) + (a2 + a3);
-}
-
 // sign and zero tests on the bit patterns (integer pipe)
 __device__ __forceinline__ bool bits_nonzero(double v) { return __double_as_longlong(v) != 0; }
 __device__ __forceinline__ bool bits_nonzero(float v) { return __float_as_int(v) != 0; }
@@ -1046,11 +1017,7 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
     // (the chunk buffer is too small for the partials in FP64)
     for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
       double t1 = 0.0;
-      if constexpr (F32) {
-        t1 = row_dot4(scr, i, z, K);
-      } else {
-        for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
-      }
+      for (int k = 0; k < K; ++k) t1 = fma(scr[(int64_t)k * MAXROWS + i], z[k], t1);
       scr_t[i] = t1;
     }
     double* z2 = reinterpret_cast<double*>(S.C) + (CH * KST * sizeof(QT)) / 8 - 2 * MAXK;  // the chunk buffer's tail
@@ -1062,8 +1029,16 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
       if constexpr (F32) {
         PAIR_SYNC();  // t is complete
         const int i0 = h * ((n + 1) >> 1), i1 = h ? n : (n + 1) >> 1;
-        if (lane < K) S.xch[h * MAXK + lane] = col_dot4(scr + (int64_t)lane * MAXROWS, scr_t, i0, i1);
-        if (lane + 32 < K) S.xch[h * MAXK + lane + 32] = col_dot4(scr + (int64_t)(lane + 32) * MAXROWS, scr_t, i0, i1);
+        double s0 = 0.0, s1 = 0.0;
+        const double* c0p = scr + (int64_t)lane * MAXROWS;
+        const double* c1p = scr + (int64_t)(lane + 32) * MAXROWS;
+        for (int i = i0; i < i1; ++i) {
+          const double t1 = scr_t[i];
+          if (lane < K) s0 = fma(c0p[i], t1, s0);
+          if (lane + 32 < K) s1 = fma(c1p[i], t1, s1);
+        }
+        if (lane < K) S.xch[h * MAXK + lane] = s0;
+        if (lane + 32 < K) S.xch[h * MAXK + lane + 32] = s1;
       } else {
         double* Pw = h == 0 ? reinterpret_cast<double*>(S.P) : reinterpret_cast<double*>(S.C) + (h - 1) * 32 * KST;
         for (int k = 0; k < K; ++k) Pw[lane * KST + k] = 0.0;
@@ -1093,7 +1068,8 @@ __global__ void __launch_bounds__(ls_sys<QT>() * LS_NW * 32, 1)
       if constexpr (F32) {
         double dd = 0.0, tt = 0.0;  // the correction's and the result's squared norms (this warp's rows)
         for (int i = lane + 32 * h; i < n; i += 32 * LS_NW) {
-          const double dt = row_dot4(scr, i, z2, K);
+          double dt = 0.0;
+          for (int k = 0; k < K; ++k) dt = fma(scr[(int64_t)k * MAXROWS + i], z2[k], dt);
           const double t = scr_t[i] + dt;
           scr_t[i] = t;
           dd = fma(dt, dt, dd);

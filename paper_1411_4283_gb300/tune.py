@@ -1,13 +1,14 @@
 """Autotuner of the compile-time kernel shapes, run on the target GPU.
 
 The least-squares kernel's shape is fixed at compile time: how many systems one CTA keeps in
-flight (EB_LS_SYS; their shared-memory blocks must fit in 227 KB) and how many rows each lane holds
-per chunk (EB_LS_RPL; larger chunks amortise the per-step Householder scalars and column sums over
-more rows but leave fewer warps per SM to hide the serial parts).  Each candidate is compiled into
-its own copy of the library (a candidate whose blocks do not fit fails its compile-time check and
-is skipped), timed in a fresh process that builds the stencils of the 3-D sphere workload and reads
-the least-squares launch's device time, and the fastest is written to tuned_gb300.json, from which
-build.py takes the default flags.
+flight (EB_LS_SYS_F for the FP32-factorisation kernel, the default path; EB_LS_SYS for the FP64
+one; their shared-memory blocks must fit in 227 KB) and how many rows each lane holds per chunk
+(EB_LS_RPL, shared by both; larger chunks amortise the per-step Householder scalars and column sums
+over more rows but leave fewer warps per SM to hide the serial parts).  Each candidate is compiled
+into its own copy of the library (a candidate whose blocks do not fit fails its compile-time check
+and is skipped), timed in a fresh process that builds the stencils of the 3-D sphere workload and
+reads the least-squares launches' device time, and the fastest is written to tuned_gb300.json, from
+which build.py takes the default flags.
 
     python -m paper_1411_4283_gb300.tune --n 128 --reps 2
 """
@@ -24,16 +25,23 @@ from . import build as _build
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-CANDIDATES = [(4, 4), (3, 5), (3, 6), (2, 8), (4, 3), (2, 6)]
+# candidate shapes: the defines of each (FP32 systems per CTA, rows per lane, FP64 systems per CTA)
+CANDIDATES = [
+    {"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
+    {"EB_LS_SYS_F": 5, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
+    {"EB_LS_SYS_F": 4, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
+    {"EB_LS_SYS_F": 4, "EB_LS_RPL": 6, "EB_LS_SYS": 3},
+    {"EB_LS_SYS_F": 3, "EB_LS_RPL": 8, "EB_LS_SYS": 2},
+]
 
 
-def flags_of(shape) -> list:
-    return [f"-DEB_LS_SYS={shape[0]}", f"-DEB_LS_RPL={shape[1]}"]
+def flags_of(shape: dict) -> list:
+    return [f"-D{k}={int(v)}" for k, v in sorted(shape.items())]
 
 
-def build_variant(shape) -> str | None:
+def build_variant(shape: dict) -> str | None:
     """Library path of the candidate, or None when it does not compile (shared memory)."""
-    out = os.path.join(HERE, "_lib", "tune", f"sys{shape[0]}_rpl{shape[1]}")
+    out = os.path.join(HERE, "_lib", "tune", "_".join(f"{k[6:].lower()}{v}" for k, v in sorted(shape.items())))
     try:
         return _build.build(force=True, out_dir=out, flags=flags_of(shape))
     except RuntimeError:
@@ -75,17 +83,17 @@ def tune(n: int = 128, reps: int = 2, candidates=CANDIDATES, build_fn=build_vari
     for shape in candidates:
         lib = build_fn(shape)
         if lib is None:
-            results.append({"EB_LS_SYS": shape[0], "EB_LS_RPL": shape[1], "ms_lsq": None,
-                            "note": "does not fit in shared memory"})
+            results.append({**shape, "ms_lsq": None, "note": "does not fit in shared memory"})
             continue
-        results.append({"EB_LS_SYS": shape[0], "EB_LS_RPL": shape[1], "ms_lsq": measure_fn(lib, n, reps)})
+        results.append({**shape, "ms_lsq": measure_fn(lib, n, reps)})
     timed = [r for r in results if r["ms_lsq"] is not None]
     if not timed:
         raise RuntimeError("no candidate compiled")
     best = min(timed, key=lambda r: r["ms_lsq"])
-    rec = {"workload": f"3-D unit cube minus sphere r=0.35 (seed 2), {n}^3, Q=4: least-squares launch (ms)",
+    rec = {"workload": f"3-D unit cube minus sphere r=0.35 (seed 2), {n}^3, Q=4: least-squares launches (ms), "
+                       "the default (mixed-precision) path",
            "date": time.strftime("%Y-%m-%d"), "results": results,
-           "best": {"EB_LS_SYS": best["EB_LS_SYS"], "EB_LS_RPL": best["EB_LS_RPL"]}}
+           "best": {k: v for k, v in best.items() if k.startswith("EB_")}}
     with open(out, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")

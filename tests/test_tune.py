@@ -9,26 +9,38 @@ from paper_1411_4283_gb300 import tune as T
 
 
 def test_tune_picks_fastest_and_skips_infeasible(tmp_path):
-    times = {(4, 4): 850.0, (3, 5): 905.0, (2, 8): 1156.0}
+    key = lambda s: (s["EB_LS_SYS_F"], s["EB_LS_RPL"])
+    times = {(6, 4): 420.0, (5, 4): 450.0, (3, 8): 700.0}
+    cands = [{"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4}, {"EB_LS_SYS_F": 5, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
+             {"EB_LS_SYS_F": 9, "EB_LS_RPL": 8, "EB_LS_SYS": 4}, {"EB_LS_SYS_F": 3, "EB_LS_RPL": 8, "EB_LS_SYS": 2}]
+    libs = {}
+
+    def build_fn(s):
+        if key(s) == (9, 8):
+            return None
+        libs[f"lib{len(libs)}"] = key(s)
+        return f"lib{len(libs) - 1}"
     out = tmp_path / "tuned.json"
-    rec = T.tune(n=16, reps=1, candidates=[(4, 4), (3, 5), (5, 8), (2, 8)],
-                 build_fn=lambda s: None if s == (5, 8) else f"lib{s[0]}{s[1]}",
-                 measure_fn=lambda lib, n, reps: times[(int(lib[3]), int(lib[4]))], out=str(out))
-    assert rec["best"] == {"EB_LS_SYS": 4, "EB_LS_RPL": 4}
+    rec = T.tune(n=16, reps=1, candidates=cands, build_fn=build_fn,
+                 measure_fn=lambda lib, n, reps: times[libs[lib]], out=str(out))
+    assert rec["best"] == {"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4}
     skipped = [r for r in rec["results"] if r["ms_lsq"] is None]
-    assert [(r["EB_LS_SYS"], r["EB_LS_RPL"]) for r in skipped] == [(5, 8)]
+    assert [key(r) for r in skipped] == [(9, 8)]
     assert json.loads(out.read_text()) == rec
-    assert B.tuned_flags(str(out)) == ["-DEB_LS_RPL=4", "-DEB_LS_SYS=4"]
+    assert B.tuned_flags(str(out)) == ["-DEB_LS_RPL=4", "-DEB_LS_SYS=4", "-DEB_LS_SYS_F=6"]
+    assert T.flags_of(cands[3]) == ["-DEB_LS_RPL=8", "-DEB_LS_SYS=2", "-DEB_LS_SYS_F=3"]
 
 
 def test_tune_fails_when_nothing_compiles(tmp_path):
     with pytest.raises(RuntimeError):
-        T.tune(candidates=[(9, 9)], build_fn=lambda s: None, measure_fn=None, out=str(tmp_path / "t.json"))
+        T.tune(candidates=[{"EB_LS_SYS_F": 9, "EB_LS_RPL": 9}], build_fn=lambda s: None, measure_fn=None,
+               out=str(tmp_path / "t.json"))
 
 
 def test_committed_record_is_consistent():
     rec = json.load(open(B.TUNED))
     timed = [r for r in rec["results"] if r["ms_lsq"] is not None]
     best = min(timed, key=lambda r: r["ms_lsq"])
-    assert rec["best"] == {"EB_LS_SYS": best["EB_LS_SYS"], "EB_LS_RPL": best["EB_LS_RPL"]}
-    assert B.tuned_flags() == [f"-DEB_LS_RPL={best['EB_LS_RPL']}", f"-DEB_LS_SYS={best['EB_LS_SYS']}"]
+    want = {k: v for k, v in best.items() if k.startswith("EB_")}
+    assert rec["best"] == want
+    assert B.tuned_flags() == [f"-D{k}={int(v)}" for k, v in sorted(want.items())]
