@@ -27,6 +27,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 # candidate shapes: the defines of each (FP32 systems per CTA, rows per lane, FP64 systems per CTA)
 CANDIDATES = [
+    {"EB_LS_SYS_F": 7, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 5, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 4, "EB_LS_RPL": 4, "EB_LS_SYS": 4},

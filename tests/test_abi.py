@@ -64,6 +64,20 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert P._LIB.eb_build_stencils_batch(None, 0, None, hs, None, None) == 1
     assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 15, 300, None, None, None) == 8
     assert P._LIB.eb_lsq_batch_noalloc(None, None, None, None, 1, 40, 10, None, None, None) == 1
+    # batched solve: empty batch, null handles; FP64 probe and the adjoint entry points: null arguments
+    sv = ctypes.c_void_p()
+    assert P._LIB.eb_batch_solver_create(None, 0, None, ctypes.byref(sv), None) == 1
+    assert P._LIB.eb_batch_solver_create((ctypes.c_void_p * 1)(None), 1, None, ctypes.byref(sv), None) == 1
+    assert P._LIB.eb_batch_solve(None, None, None, None, 1e-12, None, None, None) == 1
+    assert P._LIB.eb_fp64_fma_rate(0, 1, None, None) == 1
+    J = ctypes.c_double()
+    assert P._LIB.eb_adjoint_shape(None, None, None, 0, None, ctypes.byref(J), None, None, None, None) == 1
+    assert P._LIB.eb_adjoint_radii(None, None, None, ctypes.byref(J), None, None) == 1
+    nb = ctypes.c_int64()
+    assert P._LIB.eb_geometry_shape_table(None, 0, 0, None, 2, 0, None, 0, ctypes.byref(nb)) == 1
+    opts = P.EbSolveOpts(0, 1e-5, 100, 10, 1000, 1, 1)  # mixed = 0: the batch is the refinement only
+    assert P._LIB.eb_batch_solver_create((ctypes.c_void_p * 1)(1), 1, ctypes.byref(opts), ctypes.byref(sv),
+                                         None) == 1
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
