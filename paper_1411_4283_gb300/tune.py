@@ -7,8 +7,9 @@ one; their shared-memory blocks must fit in 227 KB) and how many rows each lane 
 over more rows but leave fewer warps per SM to hide the serial parts).  Each candidate is compiled
 into its own copy of the library (a candidate whose blocks do not fit fails its compile-time check
 and is skipped), timed in a fresh process that builds the stencils of the 3-D sphere workload and
-reads the least-squares launches' device time, and the fastest is written to tuned_gb300.json, from
-which build.py takes the default flags.
+reads the least-squares launches' device time, and the fastest (the built-in default unless another
+candidate beats it by more than MARGIN) is written to tuned_gb300.json, from which build.py takes the
+default flags.
 
     python -m paper_1411_4283_gb300.tune --n 128 --reps 2
 """
@@ -27,13 +28,29 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 # candidate shapes: the defines of each (FP32 systems per CTA, rows per lane, FP64 systems per CTA)
 CANDIDATES = [
+    {"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4},  # the built-in default: kept unless beaten by MARGIN
     {"EB_LS_SYS_F": 7, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
-    {"EB_LS_SYS_F": 6, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 5, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 4, "EB_LS_RPL": 4, "EB_LS_SYS": 4},
     {"EB_LS_SYS_F": 4, "EB_LS_RPL": 6, "EB_LS_SYS": 3},
     {"EB_LS_SYS_F": 3, "EB_LS_RPL": 8, "EB_LS_SYS": 2},
 ]
+
+
+MARGIN = 0.02  # a candidate replaces the first (the built-in default) only when faster by more than this
+
+
+def pick_best(results: list, margin: float = MARGIN) -> dict:
+    """The fastest timed result, or the first one when the fastest beats it by less than margin
+    (run-to-run noise of the timing)."""
+    timed = [r for r in results if r["ms_lsq"] is not None]
+    if not timed:
+        raise RuntimeError("no candidate compiled")
+    best = min(timed, key=lambda r: r["ms_lsq"])
+    first = results[0]
+    if first["ms_lsq"] is not None and best["ms_lsq"] > (1.0 - margin) * first["ms_lsq"]:
+        best = first
+    return {k: v for k, v in best.items() if k.startswith("EB_")}
 
 
 def flags_of(shape: dict) -> list:
@@ -87,14 +104,10 @@ def tune(n: int = 128, reps: int = 2, candidates=CANDIDATES, build_fn=build_vari
             results.append({**shape, "ms_lsq": None, "note": "does not fit in shared memory"})
             continue
         results.append({**shape, "ms_lsq": measure_fn(lib, n, reps)})
-    timed = [r for r in results if r["ms_lsq"] is not None]
-    if not timed:
-        raise RuntimeError("no candidate compiled")
-    best = min(timed, key=lambda r: r["ms_lsq"])
     rec = {"workload": f"3-D unit cube minus sphere r=0.35 (seed 2), {n}^3, Q=4: least-squares launches (ms), "
                        "the default (mixed-precision) path",
-           "date": time.strftime("%Y-%m-%d"), "results": results,
-           "best": {k: v for k, v in best.items() if k.startswith("EB_")}}
+           "date": time.strftime("%Y-%m-%d"), "results": results, "margin": MARGIN,
+           "best": pick_best(results)}
     with open(out, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")

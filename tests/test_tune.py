@@ -39,8 +39,13 @@ def test_tune_fails_when_nothing_compiles(tmp_path):
 
 def test_committed_record_is_consistent():
     rec = json.load(open(B.TUNED))
-    timed = [r for r in rec["results"] if r["ms_lsq"] is not None]
-    best = min(timed, key=lambda r: r["ms_lsq"])
-    want = {k: v for k, v in best.items() if k.startswith("EB_")}
+    want = T.pick_best(rec["results"], rec.get("margin", T.MARGIN))
     assert rec["best"] == want
     assert B.tuned_flags() == [f"-D{k}={int(v)}" for k, v in sorted(want.items())]
+
+
+def test_default_kept_within_margin():
+    res = [{"EB_LS_SYS_F": 6, "ms_lsq": 429.0}, {"EB_LS_SYS_F": 7, "ms_lsq": 425.7}, {"EB_LS_SYS_F": 5, "ms_lsq": None}]
+    assert T.pick_best(res, 0.02) == {"EB_LS_SYS_F": 6}
+    res[1]["ms_lsq"] = 400.0
+    assert T.pick_best(res, 0.02) == {"EB_LS_SYS_F": 7}
