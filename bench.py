@@ -29,6 +29,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import types
 
 # The oracle is single-threaded: one BLAS thread per process, set before numpy loads its BLAS (the
 # CPU baseline runs one oracle process per host core; more threads would oversubscribe them).  OpenMP
@@ -668,8 +669,12 @@ def run_batch(args, P, torch):
             N = (64, 96, 128)[int(rng.next_u64() % 3)]
             c = [0.45 + 0.1 * rng.next_double() for _ in range(3)]
             r = 0.25 + 0.1 * rng.next_double()
-            gs.append(E.Geometry(3, N, np.array([c]), np.array([r]), False, 4, name=f"sphere-{N}"))
-    dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+            gs.append((N, c, r))
+    if args.batch_dim == 2:
+        dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+    else:  # 3-D: the moment tables generated on the device (the host generator takes seconds per geometry)
+        dgs = [P.eb_geometry_spheres(N, [c], [r], moment_degree=4) for N, c, r in gs]
+        gs = [types.SimpleNamespace(N=G.n[0], ncell=G.n[0] ** 3, cut_cells=range(G.n_cut)) for G in dgs]
     torch.cuda.synchronize()
 
     def sequential():
