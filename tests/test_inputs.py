@@ -157,3 +157,18 @@ def test_multi_sphere_clearance_and_volume():
             assert np.linalg.norm(c[i] - c[j]) - r[i] - r[j] >= 2 * h - 1e-15
     vol = (g.flag == 1).sum() * h ** 3 + g.vol_mom[:, 0].sum() * h ** 3
     assert abs(vol - (1 - sum(4 / 3 * math.pi * x ** 3 for x in r))) <= 1e-12
+
+
+def test_level_set_modes():
+    """The shape-gradient workload's 16 modes: integer wave numbers in 1..4 per component (0 beyond the
+    dimension), phases in [0, 2 pi), drawn four numbers per mode from SplitMix64(5)."""
+    m = E.level_set_modes(16, seed=5)
+    assert m.shape == (16, 4)
+    k = m[:, :3]
+    assert np.all(k == np.round(k)) and np.all((k >= 1) & (k <= 4))
+    assert np.all((m[:, 3] >= 0) & (m[:, 3] < 2 * math.pi))
+    u = E.uniform(5, 4 * 16)
+    assert m[0, 3] == 2 * math.pi * u[3] and m[0, 0] == 1 + min(3, math.floor(4 * u[0]))
+    assert np.array_equal(E.level_set_modes(16, seed=5), m)
+    m2 = E.level_set_modes(3, seed=5, dim=2)
+    assert np.all(m2[:, 2] == 0) and np.array_equal(m2[:, :2], m[:3, :2])
