@@ -576,7 +576,7 @@ def run_sweep(args, P, torch):
         for N in ns:
             t0 = time.time()
             g = E.multi_circle_config(N)
-            man = E.Manufactured(g, E.sin_product("config2d"))
+            man = E.Manufactured(g, E.sin_product("sin2pix_cos3piy"))
             rho, Phi, geb, gw = man.lap_avg(), man.cell_avg(), man.eb_phi(), man.wall_phi_by_id()
             t_host = time.time() - t0
             dev = "cuda"
@@ -602,7 +602,7 @@ def run_sweep(args, P, torch):
             rows.append(row)
             prev = row
             del st
-    print(json.dumps({"mode": "sweep", "workload": "2-D unit square minus five circles (config 2), phi = "
+    print(json.dumps({"mode": "sweep", "workload": "2-D unit square minus five circles (r = 0.3 at (0.51, 0.49) and four seeded), phi = "
                       "sin(2 pi x) cos(3 pi y), refined solve to 1e-12", "data": "synthetic", "rows": rows}))
 
 

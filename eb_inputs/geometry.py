@@ -335,7 +335,7 @@ class Geometry:
                 "n_covered": int((self.flag == 0).sum()), "kappa_min": self.min_kappa()}
 
 
-# ---------------------------------------------------------------- configs
+# ---------------------------------------------------------------- seeded geometries
 
 def line_config(N: int, qmax: int = 4) -> Geometry:
     """1-D unit interval with N cells and no embedded boundary."""

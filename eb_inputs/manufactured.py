@@ -22,7 +22,7 @@ def sin_product(kind: str) -> ProductFn:
     ``paper2d``: sin(2 pi (x - sqrt2/2)) sin(2 pi (y - sqrt3/2)) -- the 2-D
     solution of Sec. 3.3 read with its second factor in y (as printed both
     factors are in x, which cannot be the intended 2-D test).
-    ``config2d``: sin(2 pi x) cos(3 pi y).
+    ``sin2pix_cos3piy``: sin(2 pi x) cos(3 pi y).
     ``paper3d``: sin(2 pi (x-x0)) sin(2 pi (y-y0)) sin(2 pi (z-z0)),
     x0 = sqrt2/2, y0 = sqrt3/2, z0 = 0.54321 (Sec. 3.5).
     ``paper2d_printed``: sin(2 pi (x - sqrt2/2)) sin(2 pi (x - sqrt3/2)) as printed.
@@ -30,7 +30,7 @@ def sin_product(kind: str) -> ProductFn:
     tp = 2 * math.pi
     if kind == "paper2d":
         return ProductFn((tp, tp, 0.0), (-tp * math.sqrt(2) / 2, -tp * math.sqrt(3) / 2, math.pi / 2))
-    if kind == "config2d":
+    if kind == "sin2pix_cos3piy":
         return ProductFn((tp, 3 * math.pi, 0.0), (0.0, math.pi / 2, math.pi / 2))
     if kind == "paper3d":
         return ProductFn((tp, tp, tp), (-tp * math.sqrt(2) / 2, -tp * math.sqrt(3) / 2, -tp * 0.54321))

@@ -47,7 +47,7 @@ def make(name):
     from oracle_pool import parallel_stencils
     mk, neumann = cases()[name]
     g = mk()
-    man = E.Manufactured(g, E.sin_product("paper3d" if g.dim == 3 else "config2d"))
+    man = E.Manufactured(g, E.sin_product("paper3d" if g.dim == 3 else "sin2pix_cos3piy"))
     bc = np.ones(len(g.cut_cells), np.uint8) if neumann else None
     p = Params(order=2 if name.endswith("_q2") else 4)
     t0 = time.time()

@@ -17,7 +17,7 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _problem(g):
-    man = E.Manufactured(g, E.sin_product("paper3d" if g.dim == 3 else "config2d"))
+    man = E.Manufactured(g, E.sin_product("paper3d" if g.dim == 3 else "sin2pix_cos3piy"))
     return to_dev(man.lap_avg()), to_dev(man.eb_phi()), to_dev(man.wall_phi_by_id())
 
 

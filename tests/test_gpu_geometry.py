@@ -16,9 +16,9 @@ from oracle.eb_moments import circle_moments
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "config1_n32": (32, [(0.51, 0.49)], [0.3], False),
+    "circle_r03_n32": (32, [(0.51, 0.49)], [0.3], False),
     "two_circles_n24": (24, [(0.31, 0.29), (0.69, 0.66)], [0.13, 0.17], False),
-    "five_circles_n128": None,   # config 2's geometry (the seeded multi-circle case)
+    "five_circles_n128": None,   # the seeded five-circle geometry (multi_circle_config)
     "inside_n32": (32, [(0.5, 0.5)], [0.45], True),
 }
 
@@ -49,7 +49,7 @@ def test_device_tables_match_generator(name):
         assert np.abs(G.table("face_mom", d) - g.face_mom[d]).max() <= 1e-13
 
 
-@pytest.mark.parametrize("name", ["config1_n32", "two_circles_n24"])
+@pytest.mark.parametrize("name", ["circle_r03_n32", "two_circles_n24"])
 def test_device_tables_match_moment_oracle(name):
     import paper_1411_4283_gb300 as P
     N, cen, rad, inside, g = _case(name)
@@ -71,10 +71,11 @@ def test_device_tables_match_moment_oracle(name):
 
 def test_stencils_from_device_tables():
     """The operator built on the device tables equals the one built on the host tables (FP64 apply,
-    kappa-weighted, 1e-9 normwise: see the module docstring) for config 1 and both orders."""
+    kappa-weighted, 1e-9 normwise: see the module docstring) for the circle r = 0.3 at (0.51, 0.49),
+    N = 32, and both orders."""
     import torch
     import paper_1411_4283_gb300 as P
-    N, cen, rad, inside, g = _case("config1_n32")
+    N, cen, rad, inside, g = _case("circle_r03_n32")
     G = P.eb_geometry_circles(N, cen, rad, moment_degree=4)
     phi = to_dev(E.seeded_field(21, g.ncell) * (g.flag > 0))
     for Q in (4, 2):

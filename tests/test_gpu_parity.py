@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def circle32():
     g = E.circle_config(32, center=(0.51, 0.49), r=0.3)
-    man = E.Manufactured(g, E.sin_product("config2d"))
+    man = E.Manufactured(g, E.sin_product("sin2pix_cos3piy"))
     ref = run_problem(g, man, Params(order=4))
     return g, man, ref
 
@@ -189,7 +189,7 @@ def test_apply_q2_2d():
     import torch
     import paper_1411_4283_gb300 as P
     g = E.circle_config(32, center=(0.51, 0.49), r=0.3)
-    man = E.Manufactured(g, E.sin_product("config2d"))
+    man = E.Manufactured(g, E.sin_product("sin2pix_cos3piy"))
     ref = run_problem(g, man, Params(order=2))
     st, _ = build_gpu(g, order=2)
     phi = E.seeded_field(12, g.ncell) * (g.flag > 0)

@@ -25,7 +25,7 @@ def _solve(N, Q):
     import torch
     import paper_1411_4283_gb300 as P
     g = E.multi_circle_config(N)
-    man = E.Manufactured(g, E.sin_product("config2d"))
+    man = E.Manufactured(g, E.sin_product("sin2pix_cos3piy"))
     st = P.eb_build_stencils(P.DeviceGeometry.from_geometry(g), order=Q)
     x = torch.zeros(g.ncell, dtype=torch.float64, device="cuda")
     info = P.eb_solve(st, to_dev(man.lap_avg()), to_dev(man.eb_phi()), to_dev(man.wall_phi_by_id()), x, tol=1e-12)

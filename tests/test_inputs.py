@@ -133,7 +133,7 @@ def test_multi_circle_clearance():
 
 def test_manufactured_full_cell_average():
     g = E.circle_config(16)
-    man = E.Manufactured(g, E.sin_product("config2d"))
+    man = E.Manufactured(g, E.sin_product("sin2pix_cos3piy"))
     avg = man.cell_avg()
     c = 0  # cell (0,0) is full
     x0, x1, h = 0.0, g.h, g.h
