@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--out", default=None)
     p.add_argument("--batch", type=int, default=256, help="geometries of --mode batch")
     p.add_argument("--batch-dim", type=int, default=2, choices=[2, 3], help="dimension of --mode batch")
+    p.add_argument("--batch-shapes", default="circles", choices=["circles", "mixed"],
+                   help="2-D batch bodies: circles, or every other geometry an axis-aligned ellipse")
     p.add_argument("--mode", default="step", choices=["step", "build", "apply", "batch", "sweep", "adjoint", "peak"],
                    help="build: one stencil build and exit; apply: build plus 3 FP32 applies (profiling cases); "
                         "sweep: the 2-D convergence sweep (five circles, 128^2..1024^2, Q = 2 and 4)")
@@ -650,7 +652,8 @@ def run_adjoint(args, P, torch):
 def run_batch(args, P, torch):
     """Many-instance batch.  2-D (--batch-dim 2): --batch seeded geometries, the unit square minus a
     circle (centre 0.5 + U[-0.1, 0.1)^2, radius U[0.2, 0.3), grid sizes 2^k with k ~ U{5..9}, i.e.
-    32^2..512^2); 3-D (--batch-dim 3): the unit cube minus a sphere (centre 0.5 + U[-0.05, 0.05)^3,
+    32^2..512^2; --batch-shapes mixed: every other one an axis-aligned ellipse with semi-axes r and
+    U[0.15, 0.3)); 3-D (--batch-dim 3): the unit cube minus a sphere (centre 0.5 + U[-0.05, 0.05)^3,
     radius U[0.25, 0.35), grids 64^3, 96^3 or 128^3); all from SplitMix64(11).  Build: one least-squares
     launch for the batch against one build per geometry (LS systems per second).  Solve: kappa L phi =
     kappa with homogeneous Dirichlet data to a relative residual of 1e-10, the batched refined solve
@@ -664,7 +667,11 @@ def run_batch(args, P, torch):
             k = 5 + int(rng.next_u64() % 5)
             cx, cy = 0.4 + 0.2 * rng.next_double(), 0.4 + 0.2 * rng.next_double()
             r = 0.2 + 0.1 * rng.next_double()
-            gs.append(E.circle_config(2 ** k, center=(cx, cy), r=r))
+            if args.batch_shapes == "mixed" and i % 2 == 1:  # an ellipse: semi-axes r and U[0.15, 0.3)
+                from eb_inputs.ellipse import ellipse_batch_config
+                gs.append(ellipse_batch_config(2 ** k, cx, cy, r, 0.15 + 0.15 * rng.next_double()))
+            else:
+                gs.append(E.circle_config(2 ** k, center=(cx, cy), r=r))
         else:
             N = (64, 96, 128)[int(rng.next_u64() % 3)]
             c = [0.45 + 0.1 * rng.next_double() for _ in range(3)]
