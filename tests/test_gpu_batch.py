@@ -82,3 +82,28 @@ def test_batch_failure_in_a_worker_reaches_the_caller():
     dgs[3] = P.DeviceGeometry.from_geometry(gs[3])
     batch = P.eb_build_stencils_batch(dgs, order=4)
     assert len(batch) == len(gs)
+
+
+def test_batch_with_an_ellipse_against_the_oracle():
+    """A batch of an ellipse (a = 0.31, b = 0.17, tables from eb_inputs/ellipse.py) and a circle: the
+    ellipse's stencils against the oracle's (sampled faces, 1e-10 of each face's largest coefficient),
+    and its batched refined solve equal to the single-geometry solve (1e-10 of max|phi|)."""
+    import torch
+    import paper_1411_4283_gb300 as P
+    from eb_inputs.ellipse import EllipseGeometry
+    ge = EllipseGeometry(48, [(0.503, 0.497)], [(0.31, 0.17)])
+    gs = [ge, E.circle_config(40)]
+    dgs = [P.DeviceGeometry.from_geometry(g) for g in gs]
+    batch = P.eb_build_stencils_batch(dgs, order=4)
+    o = Oracle(ge, Params(order=4))
+    compare_stencils(batch[0], o, sample_faces(o, 60, seed=13))
+    f64 = dict(dtype=torch.float64, device="cuda")
+    rho = [torch.ones(g.ncell, **f64) for g in gs]
+    geb = [torch.zeros(max(len(g.cut_cells), 1), **f64) for g in gs]
+    gw = [torch.zeros(max(len(P.eb_wall_faces(st)), 1), **f64) for st in batch]
+    phis = [torch.zeros(g.ncell, **f64) for g in gs]
+    P.BatchSolver(batch).solve(rho, geb, gw, phis, tol=1e-10)
+    for st, r_, e_, w_, x, g in zip(batch, rho, geb, gw, phis, gs):
+        y = torch.zeros(g.ncell, **f64)
+        P.eb_solve(st, r_, e_, w_, y, tol=1e-10)
+        assert (x - y).abs().max().item() <= 1e-10 * y.abs().max().item()
