@@ -457,7 +457,7 @@ def main():
                           "iterations; FP64 Householder for the systems the FP32 factor leaves)",
                 "bound": "alu", "achieved": lsq_tflops,
                 "peak": fp64_pk, "unit": "TFLOP/s", "frac": lsq_tflops / fp64_pk, "traffic": traffic,
-                "achieved_note": "the method's FP64 Householder flop count (2nK^2 - 2K^3/3 + 6nK + 2K^2 per system "
+                "achieved_note": "the method's FP64 Householder flop count (2nK^2 - 2K^3/3 + 4nK + K^2 per system "
                                  "solved) over the LS time; the factorisation runs on the FP32 pipe, so this "
                                  "equivalent rate can pass the FP64 peak",
                 "executed_fp64_tflops": ex64, "executed_fp64_frac": ex64 / fp64_pk,

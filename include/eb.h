@@ -119,8 +119,9 @@ typedef struct eb_build_info {
   int32_t max_rows;         /* largest LS system (rows) */
   int64_t n_irregular_rows; /* cells with their own operator row */
   int32_t n_row_classes;    /* shared operator rows (wall classes and template) */
-  int64_t lsq_flops;        /* FP64 flops of the LS solves by Householder QR + corrected semi-normal
-                               equations (the reference count of the method, whichever path ran) */
+  int64_t lsq_flops;        /* the method's flop count of the LS solves, 2nK^2 - 2K^3/3 + 4nK + K^2
+                               per system (Householder QR, triangular solve, application of Q),
+                               whichever path ran */
   double ms_classify, ms_gather, ms_lsq, ms_assemble; /* device time per phase */
   int64_t n_ls_fp64;        /* systems solved by the FP64 factorisation (all of them with
                                EB_LS_FP64; with EB_LS_MIXED those the FP32 factor could not carry) */

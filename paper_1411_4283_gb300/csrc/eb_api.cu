@@ -1660,8 +1660,9 @@ static eb_status build_post(BuildCtx& c) {
     for (int64_t i = 0; i < n_slots; ++i) {
       int64_t n = rp[i + 1] - rp[i];
       mx = std::max<int32_t>(mx, (int32_t)n);
-      // Householder QR of an n x K matrix plus the semi-normal solves and corrections
-      fl += 2.0 * n * K * K - 2.0 / 3.0 * K * K * K + 6.0 * n * K + 2.0 * K * K;
+      // the method's count per system: Householder QR of the n x K matrix, the triangular solve and the
+      // application of Q (2nK^2 - 2K^3/3 + 4nK + K^2)
+      fl += 2.0 * n * K * K - 2.0 / 3.0 * K * K * K + 4.0 * n * K + 1.0 * K * K;
     }
     info->max_rows = mx;
     info->lsq_flops = (int64_t)fl;
