@@ -1514,7 +1514,6 @@ static eb_status build_post(BuildCtx& c) {
       EB_TRY(tmp.get(&dfl, nc2));
       EB_CUDA(cudaMemcpyAsync(dcand, cand.data(), nc2 * 8, cudaMemcpyHostToDevice, s));
       std::vector<uint8_t> hfl(nc2);
-      int64_t off0 = 0;
       for (int d = 0; d < D; ++d) {
         // candidates of direction d are contiguous after sorting (global ids are direction-major)
         int64_t lo = std::lower_bound(cand.begin(), cand.end(), dm.face_base[d]) - cand.begin();
@@ -1530,9 +1529,7 @@ static eb_status build_post(BuildCtx& c) {
           EB_CUDA(cudaMemcpyAsync(hfl.data() + lo, dfl + lo, hi - lo, cudaMemcpyDeviceToHost, s));
           EB_CUDA(cudaStreamSynchronize(s));
         }
-        off0 = hi;
       }
-      (void)off0;
       st->wall_ids_host.clear();
       for (int64_t i = 0; i < nc2; ++i)
         if (hfl[i]) st->wall_ids_host.push_back(cand[i]);
@@ -2005,7 +2002,7 @@ eb_status eb_batch_solver_create(const eb_stencils* const* st, int32_t n, const 
     const eb_stencils* S = st[k];
     if (o.precond == 1 && (r = ensure_mg(S, s)) != EB_OK) return fail(r);
     BatchSys& y = b->sys[k];
-    memset(&y, 0, sizeof(y));
+    y = BatchSys();
     y.n = S->dm.ncell;
     y.A64 = apply_args<double>(S, 1);
     y.A32 = apply_args<float>(S, 1);

@@ -244,11 +244,7 @@ __device__ int gather_rows(const GatherArgs& a, int64_t s, uint32_t* out) {
   int base[3], lo_ok = 0, hi_ok = 0, dface = -1;
   int64_t vlo = -1, vhi = -1;
   int rng_lo[3], rng_hi[3];
-  if (gf >= dm.n_grid_faces) {
-    int64_t cut = gf - dm.n_grid_faces;
-    (void)cut;
-    return -1;  // EB slots are handled by the caller (base cell passed separately)
-  }
+  if (gf >= dm.n_grid_faces) return -1;  // EB slots are handled by the caller (base cell passed separately)
   for (int d = 0; d < dm.dim; ++d)
     if (gf >= dm.face_base[d]) dface = d;
   int64_t f = gf - dm.face_base[dface];
