@@ -158,6 +158,19 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
 
 
+def _vec64(t, n, what):
+    """Pointer to a device FP64 vector of at least n entries.  The C ABI takes raw pointers and reads or
+    writes n entries, so the type, the device, the layout and the length are checked here; n = 0 also
+    accepts None (the library then takes a null pointer)."""
+    import torch
+    if t is None and n == 0:
+        return ctypes.c_void_p(0)
+    if not (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+            and t.numel() >= n):
+        raise ValueError(f"{what}: a contiguous FP64 CUDA tensor of at least {n} entries is expected")
+    return _ptr(t)
+
+
 class DeviceGeometry:
     """Device copies of a geometry's moment tables, in the layout eb.h documents."""
 
@@ -358,6 +371,9 @@ class Stencils:
         self.h = geom.h
         self.ncell = int(np.prod(geom.n))
         self.n_cut = geom.n_cut
+        n = ctypes.c_int64()
+        _check(load().eb_wall_faces(handle, None, 0, ctypes.byref(n)))
+        self.n_wall = int(n.value)  # open wall faces (the length of g_wall)
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
@@ -413,7 +429,8 @@ def eb_wall_faces(st: Stencils) -> np.ndarray:
 
 
 def eb_bc_rhs(st: Stencils, g_eb, g_wall, Bg, kappa_weighted=True, stream=None):
-    _check(load().eb_bc_rhs(st.handle, _ptr(g_eb), _ptr(g_wall), _ptr(Bg), int(kappa_weighted), _stream(stream)))
+    _check(load().eb_bc_rhs(st.handle, _vec64(g_eb, st.n_cut, "g_eb"), _vec64(g_wall, st.n_wall, "g_wall"),
+                            _vec64(Bg, st.ncell, "Bg"), int(kappa_weighted), _stream(stream)))
     return Bg
 
 
@@ -424,7 +441,8 @@ def eb_solve(st: Stencils, rho, g_eb, g_wall, phi, tol=1e-12, mixed=True, inner_
     o = EbSolveOpts(int(mixed), inner_tol, max_inner, max_outer, max_iters, -1 if time_applies else 1,
                     {"jacobi": 0, "mg": 1}[precond])
     info = EbSolveInfo()
-    code = lib.eb_solve(st.handle, _ptr(rho), _ptr(g_eb), _ptr(g_wall), tol, ctypes.byref(o), _ptr(phi),
+    code = lib.eb_solve(st.handle, _vec64(rho, st.ncell, "rho"), _vec64(g_eb, st.n_cut, "g_eb"),
+                        _vec64(g_wall, st.n_wall, "g_wall"), tol, ctypes.byref(o), _vec64(phi, st.ncell, "phi"),
                         ctypes.byref(info), _stream(stream))
     if not (allow_not_converged and code == 4):
         _check(code)
@@ -457,10 +475,17 @@ class BatchSolver:
     def solve(self, rho, g_eb, g_wall, phi, tol=1e-12, stream=None, allow_not_converged=False) -> list:
         """rho, g_eb, g_wall, phi: lists of device FP64 tensors, one per system; phi in/out."""
         n = len(self.stencils)
-        arr = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
+        if not all(len(v) == n for v in (rho, g_eb, g_wall, phi)):
+            raise ValueError(f"BatchSolver.solve: one rho, g_eb, g_wall and phi per system ({n}) expected")
+
+        def arr(ts, size, what):
+            return (ctypes.c_void_p * n)(*[_vec64(t, size(st), f"{what}[{k}]")
+                                           for k, (t, st) in enumerate(zip(ts, self.stencils))])
+
         infos = (EbSolveInfo * n)()
-        code = load().eb_batch_solve(self.handle, arr(rho), arr(g_eb), arr(g_wall), tol, arr(phi), infos,
-                                     _stream(stream))
+        code = load().eb_batch_solve(self.handle, arr(rho, lambda st: st.ncell, "rho"),
+                                     arr(g_eb, lambda st: st.n_cut, "g_eb"), arr(g_wall, lambda st: st.n_wall, "g_wall"),
+                                     tol, arr(phi, lambda st: st.ncell, "phi"), infos, _stream(stream))
         if not (allow_not_converged and code == 4):
             _check(code)
         return [infos[k].as_dict() for k in range(n)]
@@ -473,7 +498,7 @@ class BatchSolver:
 
 def eb_norms(st: Stencils, err, stream=None) -> dict:
     out = (ctypes.c_double * 3)()
-    _check(load().eb_norms(st.handle, _ptr(err), out, _stream(stream)))
+    _check(load().eb_norms(st.handle, _vec64(err, st.ncell, "err"), out, _stream(stream)))
     return {"linf": out[0], "l1": out[1], "l2": out[2]}
 
 

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -86,3 +87,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(P._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         P.load()
+
+
+def test_binding_checks_vectors_before_the_call():
+    """The binding passes raw pointers, so it checks each vector's type, device, layout and length
+    first: a CPU tensor, a float32 tensor, a non-contiguous view or a short vector is refused on the
+    host, and an empty vector is accepted where the length is 0 (a geometry with no cut cells)."""
+    import torch
+    import paper_1411_4283_gb300 as P
+    for bad in (torch.zeros(8, dtype=torch.float64),  # host memory
+                torch.zeros(8, dtype=torch.float32),
+                torch.zeros(16, dtype=torch.float64)[::2],
+                np.zeros(8)):
+        with pytest.raises(ValueError):
+            P._vec64(bad, 8, "rho")
+    with pytest.raises(ValueError):
+        P._vec64(None, 3, "g_eb")
+    assert P._vec64(None, 0, "g_eb").value is None
