@@ -33,11 +33,13 @@ TUNED = os.path.join(HERE, "tuned_gb300.json")  # kernel shapes picked by tune.p
 
 
 def tuned_flags(path: str = TUNED) -> list:
-    """-D flags of the tuned kernel shapes (empty when no tuning record exists)."""
+    """-D flags of the tuned kernel shapes: the least-squares record's and the apply record's (empty when
+    no tuning record exists)."""
     if not os.path.exists(path):
         return []
     with open(path) as f:
-        best = json.load(f).get("best", {})
+        rec = json.load(f)
+    best = {**rec.get("best", {}), **rec.get("apply", {}).get("best", {})}
     return [f"-D{k}={int(v)}" for k, v in sorted(best.items())]
 
 
