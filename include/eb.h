@@ -214,8 +214,10 @@ eb_status eb_solve(const eb_stencils* st, const double* rho, const double* g_eb,
  * device-resident scalars: no host synchronisation inside the solve, the
  * systems' loops side by side.  Every loop stops at its iteration cap.
  *
- * eb_batch_solver_create: st[n] (host array of handles, which must outlive
- * the solver and are not used concurrently by other solves); opts as for
+ * eb_batch_solver_create: st[n] (host array of distinct handles, which must
+ * outlive the solver and are not used concurrently by other solves; a handle
+ * given twice is refused with EB_ERR_INVALID, since a stencil set's solver
+ * state serves one system at a time); opts as for
  * eb_solve (mixed must be 1; check_every is ignored); sets up each system's
  * preconditioner, its vectors (about 72 bytes per cell) and the graph.
  * eb_batch_solve: host arrays of device pointers rho[n], g_eb[n], g_wall[n]

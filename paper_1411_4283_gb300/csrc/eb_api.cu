@@ -1981,6 +1981,15 @@ eb_status eb_batch_solver_create(const eb_stencils* const* st, int32_t n, const 
   }
   for (int32_t k = 0; k < n; ++k)
     if (!st[k]) { set_error("eb_batch_solver_create: null stencils"); return EB_ERR_INVALID; }
+  {
+    // a stencil set's multigrid vectors and apply scratch serve one system of the graph at a time
+    std::vector<const eb_stencils*> seen(st, st + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+      set_error("eb_batch_solver_create: a stencil set appears twice in the batch");
+      return EB_ERR_INVALID;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   eb_batch_solver* b = new eb_batch_solver();
   b->o = o;

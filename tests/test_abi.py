@@ -76,6 +76,11 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert P._LIB.eb_adjoint_radii(None, None, None, ctypes.byref(J), None, None) == 1
     nb = ctypes.c_int64()
     assert P._LIB.eb_geometry_shape_table(None, 0, 0, None, 2, 0, None, 0, ctypes.byref(nb)) == 1
+    # one stencil set twice in a batch (refused before any handle is read)
+    opts1 = P.EbSolveOpts(1, 1e-5, 100, 10, 1000, 1, 1)
+    assert P._LIB.eb_batch_solver_create((ctypes.c_void_p * 3)(8, 16, 8), 3, ctypes.byref(opts1), ctypes.byref(sv),
+                                         None) == 1
+    assert "twice" in P._LIB.eb_last_error_message().decode()
     opts = P.EbSolveOpts(0, 1e-5, 100, 10, 1000, 1, 1)  # mixed = 0: the batch is the refinement only
     assert P._LIB.eb_batch_solver_create((ctypes.c_void_p * 1)(1), 1, ctypes.byref(opts), ctypes.byref(sv),
                                          None) == 1
