@@ -296,6 +296,39 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def fp64_apply_timing(P, torch, st, g, nfoot, fp64_pk, hbm_peak, pairs=4, rounds=3):
+    """The kappa-weighted FP64 apply (the refinement's operator) timed alone: phi ~ U[-1, 1] (SplitMix64
+    seed 3), `pairs` phi/y buffer pairs used in rotation so that no apply finds its vectors in L2, CUDA
+    events on the launching stream around each apply after one warm-up apply per pair, median of
+    rounds x pairs.  Reported against the FP64 ALU peak by the algorithmic count (one FMA per footprint
+    entry per volume, no folding counted) and against the copy bandwidth by the algorithmic bytes
+    (phi and y, the distinct non-template rows once, in FP64)."""
+    import eb_inputs as E
+    x0 = torch.tensor(E.seeded_field(3, g.ncell) * (g.flag > 0), dtype=torch.float64, device="cuda")
+    xs = [x0] + [x0 * (1.0 - 0.125 * k) for k in range(1, pairs)]
+    ys = [torch.empty_like(x0) for _ in range(pairs)]
+    for k in range(pairs):
+        P.eb_apply(st, xs[k], ys[k], kappa_weighted=True)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(rounds):
+        for k in range(pairs):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            P.eb_apply(st, xs[k], ys[k], kappa_weighted=True)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    t = float(np.median(ms))
+    alg_bytes = 2 * g.ncell * 8 + (st.info["n_irregular_rows"] + st.info["n_row_classes"]) * nfoot * 8
+    tflops = 2.0 * nfoot * int((g.flag > 0).sum()) / (t / 1e3) / 1e12
+    gbs = alg_bytes / (t / 1e3) / 1e9
+    return {"ms_median": t, "ms_all": ms, "tflops": tflops, "frac_fp64_peak": tflops / fp64_pk,
+            "gbs": gbs, "frac_hbm": gbs / hbm_peak, "alg_bytes": alg_bytes, "buffer_pairs": pairs,
+            "note": "algorithmic flops (637 products per volume) over the FP64 derived peak; the template pass "
+                    "runs the reflection-folded sum, so the executed flops are fewer"}
+
+
 def pick_tol(solve_err, e_star, cands=(1e-7, 1e-8, 1e-9, 1e-10, 1e-11)):
     """The loosest relative-residual target whose L_inf error is within 1.01 e* (else 1e-12)."""
     for cand in cands:
@@ -527,6 +560,10 @@ def main():
             runs[name] = {"ms_median": float(np.median(ms)), "ms_all": ms, "rel_residual_target": t_,
                           "error_linf": float(max(errs)), "iterations": int(np.median(its)),
                           "status": info_["status"]}
+        try:
+            line["apply_fp64"] = fp64_apply_timing(P, torch, st, g, nfoot, fp64_pk, hbm_peak)
+        except Exception as ex:  # reported in the line, never fatal to it
+            line["apply_fp64"] = {"error": f"{type(ex).__name__}: {ex}"}
         line["fp64_solve"] = {"e_star_linf": e_star, "mixed": runs["mixed"], "fp64": runs["fp64"],
                               "speedup_mixed_vs_fp64": runs["fp64"]["ms_median"] / runs["mixed"]["ms_median"],
                               "both_within_1.01_e_star": bool(runs["mixed"]["error_linf"] <= 1.01 * e_star and
