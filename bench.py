@@ -515,7 +515,8 @@ def main():
                    "n": args.n, "order": args.order, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (operator rows and stencil tables are GBs)",
                    "geometry_seconds_host": round(t_geom, 1), "geometry_seconds_device": round(t_geom_dev, 3),
-                   "geometry_device_same_cut_cells": geom_dev_ok},
+                   "geometry_device_same_cut_cells": geom_dev_ok,
+                   "seeds": {"sphere_centre_offset": 2, "apply_phi": 3, "generator": "SplitMix64"}},
         "systems_solved_per_s": n_solved * ws / (ms_step / 1e3),
         "components": {"build_ms": build_ms, "lsq_ms": lsq_ms, "ls_build_stencils_per_s": n_ls / (build_ms / 1e3),
                        "n_cut_face_systems": n_ls, "n_systems_solved": n_solved,
