@@ -50,3 +50,45 @@ def test_pick_tol_takes_the_loosest_target_within_the_error_bound():
     assert bench.pick_tol(err, 1.0) == 1e-9
     assert seen == [1e-7, 1e-8, 1e-9]          # stops at the first (loosest) target that qualifies
     assert bench.pick_tol(lambda c: 2.0, 1.0) == 1e-12
+
+
+def test_fp64_apply_timing_rotates_buffer_pairs_and_reports_rates():
+    """The FP64 apply block of the bench line, with a stand-in for the library and the CUDA events:
+    one warm-up apply per buffer pair, then rounds x pairs timed applies, each on its own pair in
+    rotation; the rates follow from the median time and the algorithmic counts."""
+    import types
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    import eb_inputs as E
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            pass
+
+        def record(self, s=None):
+            pass
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return 2.0
+
+    fake_torch = types.SimpleNamespace(tensor=lambda a, dtype=None, device=None: torch.tensor(a, dtype=dtype),
+                                       float64=torch.float64, empty_like=torch.empty_like,
+                                       cuda=types.SimpleNamespace(Event=Ev, current_stream=lambda: None))
+    calls = []
+    P = types.SimpleNamespace(eb_apply=lambda st, x, y, kappa_weighted=True: calls.append((x.data_ptr(),
+                                                                                           y.data_ptr())))
+    g = E.sphere_box_config(12)
+    st = types.SimpleNamespace(info={"n_irregular_rows": 100, "n_row_classes": 5})
+    r = bench.fp64_apply_timing(P, fake_torch, st, g, 637, 1.0, 1000.0, pairs=4, rounds=3)
+    assert len(calls) == 4 + 12
+    assert len(set(calls[:4])) == 4 and calls[4:8] == calls[:4] and calls[8:12] == calls[:4]
+    assert r["ms_median"] == 2.0 and r["buffer_pairs"] == 4
+    assert r["alg_bytes"] == 2 * g.ncell * 8 + 105 * 637 * 8
+    nvol = int((g.flag > 0).sum())
+    assert np.isclose(r["tflops"], 2 * 637 * nvol / 2e-3 / 1e12) and np.isclose(r["frac_fp64_peak"], r["tflops"])
+    assert np.isclose(r["gbs"], r["alg_bytes"] / 2e-3 / 1e9) and np.isclose(r["frac_hbm"], r["gbs"] / 1000.0)
