@@ -35,13 +35,15 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header(tmp_path):
     import paper_1411_4283_gb300 as P
     c = tmp_path / "sz.c"
-    c.write_text('#include <stdio.h>\n#include "%s"\nint main(){printf("%%zu %%zu %%zu %%zu %%zu\\n", sizeof(eb_geom), '
-                 'sizeof(eb_params), sizeof(eb_build_info), sizeof(eb_solve_opts), sizeof(eb_solve_info));}\n'
+    c.write_text('#include <stdio.h>\n#include "%s"\nint main(){printf("%%zu %%zu %%zu %%zu %%zu %%zu\\n", sizeof(eb_geom), '
+                 'sizeof(eb_params), sizeof(eb_build_info), sizeof(eb_solve_opts), sizeof(eb_solve_info), '
+                 'sizeof(eb_adjoint_info));}\n'
                  % os.path.join(ROOT, "include", "eb.h"))
     exe = tmp_path / "sz"
     subprocess.run(["gcc", str(c), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    want = [ctypes.sizeof(t) for t in (P.EbGeom, P.EbParams, P.EbBuildInfo, P.EbSolveOpts, P.EbSolveInfo)]
+    want = [ctypes.sizeof(t) for t in (P.EbGeom, P.EbParams, P.EbBuildInfo, P.EbSolveOpts, P.EbSolveInfo,
+                                       P.EbAdjointInfo)]
     assert got == want
 
 
@@ -109,3 +111,46 @@ def test_binding_checks_vectors_before_the_call():
     with pytest.raises(ValueError):
         P._vec64(None, 3, "g_eb")
     assert P._vec64(None, 0, "g_eb").value is None
+
+
+def test_plain_c_program_links_every_entry_point(tmp_path, lib):
+    """The boundary is consumable from C alone: a C99 program that includes eb.h (warnings as errors,
+    pedantic), takes the address of every declared entry point, links against the built library and
+    calls the entry points that need no GPU."""
+    from paper_1411_4283_gb300 import build
+    libdir = os.path.dirname(build.build())
+    refs = "\n".join(f"  fn = (void (*)(void))&{n}; (void)fn;" for n in _declared())
+    src = tmp_path / "use.c"
+    src.write_text('#include <stdio.h>\n#include "eb.h"\nint main(void) {\n  void (*fn)(void);\n' + refs +
+                   '\n  printf("%d %s\\n", (int)eb_abi_version(), eb_status_string(EB_ERR_RANK_DEFICIENT));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "use"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        str(src), "-I", os.path.join(ROOT, "include"), "-L", libdir, "-leb_gb300",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    ver, msg = out.stdout.split(" ", 1)
+    assert int(ver) == 3 and msg.strip()
+
+
+def test_struct_field_offsets_match_header(tmp_path):
+    """Every field of the binding's structures sits at the header's offset (sizes alone would not
+    catch two fields swapped)."""
+    import paper_1411_4283_gb300 as P
+    structs = {"eb_geom": P.EbGeom, "eb_params": P.EbParams, "eb_build_info": P.EbBuildInfo,
+               "eb_solve_opts": P.EbSolveOpts, "eb_solve_info": P.EbSolveInfo, "eb_adjoint_info": P.EbAdjointInfo}
+    lines, want = [], []
+    for cname, ct in structs.items():
+        for f in ct._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            want.append(getattr(ct, f[0]).offset)
+    c = tmp_path / "off.c"
+    c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "%s"\nint main(void) {\n%s\n  return 0;\n}\n'
+                 % (os.path.join(ROOT, "include", "eb.h"), "\n".join(lines)))
+    exe = tmp_path / "off"
+    r = subprocess.run(["gcc", str(c), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == want
