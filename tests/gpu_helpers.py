@@ -1,8 +1,7 @@
 """Shared helpers of the GPU parity tests: oracle references and device marshalling."""
 import numpy as np
 
-import eb_inputs as E
-from oracle.eb_oracle import Oracle, Params
+from oracle.eb_oracle import Oracle
 
 
 def to_dev(a, dtype=None):

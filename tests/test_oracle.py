@@ -5,7 +5,6 @@ import os
 
 import numpy as np
 import pytest
-import scipy.linalg as sl
 import scipy.sparse.linalg as spla
 
 import eb_inputs as E
