@@ -1,6 +1,6 @@
 """Writes sphere_n32.json: the FP64 oracle's solution errors for the 3-D sphere of Sec. 3.6
 (inside the sphere (0.5,0.5,0.5), r = 0.45, Q = 4, N = 32).  Calls only oracle/ and eb_inputs/;
-takes ~20 minutes on 8 cores (each 3-D face is ~0.2 s in the oracle).
+takes about two minutes on 8 cores.
 
     python tests/golden/make_sphere_golden.py
 """
